@@ -1,0 +1,492 @@
+"""Pins for the FP64 oracle against facts fixed outside it: library routines
+(scipy cKDTree, numpy eigh, scipy expm, scipy cdist), closed forms,
+finite differences, invariances and exact recovery of a known transform.
+
+Each test states the passage of the paper it follows.  None of these needs a
+GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+from scipy.spatial import cKDTree
+from scipy.spatial.distance import cdist
+from scipy.spatial.transform import Rotation
+
+from paper_2606_10019_gb300 import datagen as D
+
+
+def _rand_rot(rng, deg):
+    return Rotation.from_rotvec(math.radians(deg) * D.random_unit(rng)).as_matrix()
+
+
+def _small_problem(O, n_t=60, n_s=50, seed=3, aniso=True, feat_dim=1):
+    rng = np.random.default_rng(seed)
+    tgt = rng.uniform(-0.3, 0.3, size=(n_t, 3))
+    src = rng.uniform(-0.3, 0.3, size=(n_s, 3))
+    tf = rng.uniform(0.2, 1.0, size=(n_t, feat_dim))
+    sf = rng.uniform(0.2, 1.0, size=(n_s, feat_dim))
+    tc = sc = None
+    if aniso:
+        def rand_cov(n):
+            out = np.zeros((n, 6))
+            for k in range(n):
+                Q = _rand_rot(rng, rng.uniform(0, 180))
+                L = np.diag(rng.uniform(0.005, 0.05, size=3))
+                S = Q @ L @ Q.T
+                out[k] = [S[0, 0], S[0, 1], S[0, 2], S[1, 1], S[1, 2], S[2, 2]]
+            return out
+        tc, sc = rand_cov(n_t), rand_cov(n_s)
+    return O.Problem.make(tgt, tc, tf, src, sc, sf)
+
+
+def _sym(m):
+    return np.array([m[0, 0], m[0, 1], m[0, 2], m[1, 1], m[1, 2], m[2, 2]])
+
+
+def _mat(s):
+    return np.array([[s[0], s[1], s[2]], [s[1], s[3], s[4]], [s[2], s[4], s[5]]])
+
+
+def _frozen_problem(O, prob, T_ref, T_new):
+    """The same problem with source covariances re-expressed so that the
+    combined Sigma_ij of Eq. (7c) evaluated at T_new equals its value at
+    T_ref (the frozen-Sigma convention of Remark 2)."""
+    R0, R1 = T_ref[:3, :3], T_new[:3, :3]
+    Q = R1 @ R0.T
+    sc = np.array([_sym(Q @ _mat(s) @ Q.T) for s in prob.src_cov])
+    return O.Problem(prob.tgt, prob.tgt_cov, prob.tgt_feat, prob.src, sc, prob.src_feat)
+
+
+# --------------------------------------------------------------------------
+# Covariances, Eq. (7b) and the Remark after Eq. (7)
+# --------------------------------------------------------------------------
+
+def test_knn_sets_match_ckdtree(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(400, 3))
+    _, nbr, kth = O.knn_cov(x, 10)
+    d, idx = cKDTree(x).query(x, k=11)
+    ok = 0
+    for i in range(len(x)):
+        if d[i, 10] - d[i, 9] < 1e-9:      # near-tie at the boundary: skip
+            continue
+        assert set(nbr[i]) == set(idx[i, :10]), i
+        assert abs(kth[i, 0] - d[i, 9] ** 2) < 1e-12
+        ok += 1
+    assert ok > 390
+
+
+def test_knn_cov_line_closed_form(oracle_mod):
+    """Points k*d*e, k = 0..N-1, on a line: for the end point, N_n = the first
+    n points, so Sigma = d^2 n (2n - 1) / 6 e e^T (rank one)."""
+    O = oracle_mod
+    e = np.array([1.0, 2.0, -2.0]) / 3.0
+    d, n = 0.05, 10
+    x = np.arange(40)[:, None] * d * e[None, :] + np.array([0.3, -0.1, 2.0])
+    cov, _, _ = O.knn_cov(x, n)
+    expect = d * d * n * (2 * n - 1) / 6.0 * np.outer(e, e)
+    assert np.allclose(_mat(cov[0]), expect, rtol=1e-12, atol=1e-15)
+
+
+def test_knn_cov_plane_normal(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(1)
+    R = _rand_rot(rng, 40)
+    uv = rng.uniform(-1, 1, size=(300, 2))
+    x = np.c_[uv, np.zeros(300)] @ R.T
+    cov, _, _ = O.knn_cov(x, 10)
+    for s in cov[:50]:
+        lam, V = np.linalg.eigh(_mat(s))
+        assert lam[0] < 1e-14
+        assert abs(abs(V[:, 0] @ R[:, 2]) - 1.0) < 1e-9
+
+
+def test_knn_cov_rigid_equivariance(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(300, 3))
+    R = _rand_rot(rng, 70)
+    t = rng.normal(size=3)
+    c0, _, _ = O.knn_cov(x, 10)
+    c1, _, _ = O.knn_cov(x @ R.T + t, 10)
+    for a, b in zip(c0, c1):
+        assert np.allclose(R @ _mat(a) @ R.T, _mat(b), atol=1e-12)
+
+
+def test_sym3_eig_vs_numpy(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        A = rng.normal(size=(3, 3))
+        A = A @ A.T
+        lam, V = O.sym3_eig(_sym(A))
+        lam_ref = np.linalg.eigvalsh(A)
+        assert np.allclose(np.sort(lam), lam_ref, rtol=1e-12, atol=1e-13)
+        assert np.allclose(V @ np.diag(lam) @ V.T, A, atol=1e-12)
+        assert np.allclose(V.T @ V, np.eye(3), atol=1e-12)
+
+
+def test_eig_clamp(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(5)
+    covs = []
+    for _ in range(30):
+        Q = _rand_rot(rng, 120)
+        covs.append(_sym(Q @ np.diag(10 ** rng.uniform(-6, 0, size=3)) @ Q.T))
+    covs = np.array(covs)
+    out = O.eig_clamp(covs, 0.01, 100.0)
+    for a, b in zip(covs, out):
+        la, Va = np.linalg.eigh(_mat(a))
+        lb = np.linalg.eigvalsh(_mat(b))
+        assert np.allclose(lb, np.clip(la, 1e-4, 0.01), rtol=1e-10)
+        # eigenvectors are kept: the clamped matrix commutes with the original
+        assert np.allclose(_mat(a) @ _mat(b), _mat(b) @ _mat(a), atol=1e-12)
+    inside = O.eig_clamp(np.array([_sym(np.diag([0.001, 0.002, 0.005]))]), 0.01, 100.0)
+    assert np.allclose(inside[0], _sym(np.diag([0.001, 0.002, 0.005])))
+
+
+# --------------------------------------------------------------------------
+# Lie-group pieces: exp (Sec. 2.1) and the connection (Eq. 3, 4, 12)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scale", [0.0, 1e-9, 1e-5, 1e-2, 0.5, 2.5])
+def test_exp_matches_expm(oracle_mod, scale):
+    O = oracle_mod
+    rng = np.random.default_rng(int(scale * 1e6) % 1000)
+    xi = rng.normal(size=6) * scale
+    xi[3:] = rng.normal(size=3)
+    assert np.allclose(O.exp_se3(xi), expm(O.hat6(xi)), atol=1e-13, rtol=1e-12)
+    assert np.allclose(O.exp_se3_series(xi, 40), expm(O.hat6(xi)), atol=1e-12)
+
+
+def test_gamma_is_levi_civita(oracle_mod):
+    """For left-invariant fields the Levi-Civita connection of Eq. (3) is
+    torsion free (Gamma(U,V) - Gamma(V,U) = [U,V], the 4x4 matrix
+    commutator) and compatible with the metric of Eq. (2)."""
+    O = oracle_mod
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        U, V, W = rng.normal(size=(3, 6))
+        C = O.hat6(U) @ O.hat6(V) - O.hat6(V) @ O.hat6(U)
+        br = np.r_[C[2, 1], C[0, 2], C[1, 0], C[:3, 3]]
+        assert np.allclose(O.gamma_vec(U, V) - O.gamma_vec(V, U), br, atol=1e-12)
+        assert abs(O.gamma_vec(U, V) @ W + V @ O.gamma_vec(U, W)) < 1e-12
+
+
+def test_gamma_closed_form_eq12(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(7)
+    g = rng.normal(size=6)
+    G = O.gamma_matrix(g)
+    ref = np.zeros((6, 6))
+    ref[:3, :3] = -0.5 * O.hat3(g[:3])
+    ref[3:, :3] = -O.hat3(g[3:])
+    assert np.allclose(G, ref, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Objective (Eq. 5, 7) and derivatives (Lemma 1, Eq. 10-11)
+# --------------------------------------------------------------------------
+
+def test_isotropic_objective_vs_cdist(oracle_mod):
+    """Remark 3: with Sigma_ij = ell^2 I the objective is a plain Gaussian
+    kernel sum weighted by <l_i, l_j>."""
+    O = oracle_mod
+    prob = _small_problem(O, aniso=False, feat_dim=3)
+    rng = np.random.default_rng(8)
+    T = D.rigid(_rand_rot(rng, 20), rng.normal(size=3) * 0.1)
+    for cutoff in (0.0, 3.0):
+        kp = O.KernelParams(kernel_mode=1, sigma2=1.7, cutoff=cutoff, iso_ell=0.15)
+        res = O.evaluate(prob, T, kp)
+        p = (prob.src - T[:3, 3]) @ T[:3, :3]
+        d2 = cdist(prob.tgt, p, "sqeuclidean") / 0.15 ** 2
+        K = 1.7 * np.exp(-0.5 * d2) * (prob.tgt_feat @ prob.src_feat.T)
+        if cutoff > 0:
+            K = K * (d2 <= 9.0)
+        assert res.f == pytest.approx(K.sum(), rel=1e-12)
+
+
+def test_aniso_reduces_to_isotropic(oracle_mod):
+    """Eq. (7c) with Sigma_x = Sigma_z = ell^2/2 I gives Sigma_ij = ell^2 I."""
+    O = oracle_mod
+    prob = _small_problem(O, aniso=False)
+    ell = 0.2
+    half = np.tile(_sym(np.eye(3) * ell * ell / 2), (len(prob.tgt), 1))
+    halfz = np.tile(_sym(np.eye(3) * ell * ell / 2), (len(prob.src), 1))
+    pa = O.Problem(prob.tgt, half, prob.tgt_feat, prob.src, halfz, prob.src_feat)
+    rng = np.random.default_rng(9)
+    T = D.rigid(_rand_rot(rng, 30), rng.normal(size=3) * 0.1)
+    r_iso = O.evaluate(prob, T, O.KernelParams(kernel_mode=1, cutoff=0, iso_ell=ell))
+    r_an = O.evaluate(pa, T, O.KernelParams(kernel_mode=0, cutoff=0))
+    assert r_an.f == pytest.approx(r_iso.f, rel=1e-12)
+    assert np.allclose(r_an.g, r_iso.g, rtol=1e-10, atol=1e-12)
+    assert np.allclose(r_an.M, r_iso.M, rtol=1e-10, atol=1e-12)
+
+
+def test_rigid_invariance(oracle_mod):
+    """f is unchanged when both clouds move by a common G, with
+    T' = G T G^-1 and covariances recomputed by kNN on the moved clouds."""
+    O = oracle_mod
+    pair = D.make_corner_pair(n_src=300, n_tgt=300)
+    rng = np.random.default_rng(10)
+    G = D.rigid(_rand_rot(rng, 50), rng.normal(size=3))
+    kp = O.KernelParams(cutoff=3.0)
+    tc = O.covariances(pair.tgt_xyz, 10, 0.01, 100)
+    sc = O.covariances(pair.src_xyz, 10, 0.01, 100)
+    p0 = O.Problem.make(pair.tgt_xyz, tc, pair.tgt_feat, pair.src_xyz, sc, pair.src_feat)
+    tg, sg = D.apply(G, pair.tgt_xyz.astype(np.float64)), D.apply(G, pair.src_xyz.astype(np.float64))
+    p1 = O.Problem.make(tg, O.covariances(tg, 10, 0.01, 100), pair.tgt_feat,
+                        sg, O.covariances(sg, 10, 0.01, 100), pair.src_feat)
+    T = D.rigid(_rand_rot(rng, 3), rng.normal(size=3) * 0.05)
+    a = O.evaluate(p0, T, kp)
+    b = O.evaluate(p1, G @ T @ D.inv_rigid(G), kp)
+    assert b.f == pytest.approx(a.f, rel=1e-9)
+    assert a.n_kept == b.n_kept
+
+
+def test_permutation_invariance(oracle_mod):
+    O = oracle_mod
+    prob = _small_problem(O)
+    rng = np.random.default_rng(11)
+    pt, ps = rng.permutation(len(prob.tgt)), rng.permutation(len(prob.src))
+    q = O.Problem(prob.tgt[pt], prob.tgt_cov[pt], prob.tgt_feat[pt], prob.src[ps], prob.src_cov[ps],
+                  prob.src_feat[ps])
+    T = D.rigid(_rand_rot(rng, 10), rng.normal(size=3) * 0.05)
+    kp = O.KernelParams(cutoff=3.0)
+    a, b = O.evaluate(prob, T, kp), O.evaluate(q, T, kp)
+    assert b.f == pytest.approx(a.f, rel=1e-12)
+    assert np.allclose(a.g, b.g, rtol=1e-10, atol=1e-13)
+    assert np.allclose(a.M, b.M, rtol=1e-10, atol=1e-13)
+
+
+def _fd_grad(O, prob, T, kp, h=1e-6, frozen=True):
+    g = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        Tp, Tm = T @ O.exp_se3(e), T @ O.exp_se3(-e)
+        pp = _frozen_problem(O, prob, T, Tp) if frozen else prob
+        pm = _frozen_problem(O, prob, T, Tm) if frozen else prob
+        g[k] = (O.evaluate(pp, Tp, kp).f - O.evaluate(pm, Tm, kp).f) / (2 * h)
+    return g
+
+
+def test_gradient_matches_fd_frozen_sigma(oracle_mod):
+    """Lemma 1 is the gradient of the objective with Sigma_ij held at its
+    value for the current T (Remark 2); central differences of that frozen
+    objective along T exp(t e_k) must reproduce g."""
+    O = oracle_mod
+    prob = _small_problem(O)
+    rng = np.random.default_rng(12)
+    T = D.rigid(_rand_rot(rng, 15), rng.normal(size=3) * 0.05)
+    kp = O.KernelParams(cutoff=0.0, sigma2=1.3)
+    res = O.evaluate(prob, T, kp)
+    fd = _fd_grad(O, prob, T, kp)
+    assert np.allclose(res.g, fd, rtol=1e-6, atol=1e-7 * np.abs(res.g).max())
+
+
+def test_isotropic_gradient_is_true_gradient(oracle_mod):
+    O = oracle_mod
+    prob = _small_problem(O, aniso=False)
+    rng = np.random.default_rng(13)
+    T = D.rigid(_rand_rot(rng, 15), rng.normal(size=3) * 0.05)
+    kp = O.KernelParams(kernel_mode=1, cutoff=0.0, iso_ell=0.2)
+    res = O.evaluate(prob, T, kp)
+    fd = _fd_grad(O, prob, T, kp, frozen=False)
+    assert np.allclose(res.g, fd, rtol=1e-6, atol=1e-7 * np.abs(res.g).max())
+
+
+def test_gn_matrix_from_fd_of_gradient(oracle_mod):
+    """Eq. (10): with Sigma frozen, D(g)[xi] = -(T1 + T2 + M xi) where
+    T1 = sum J^T A r D(f_ij)[xi], T2 = sum f_ij D(J^T)[xi] A r.  The two
+    terms the Gauss-Newton matrix drops are written out here from their
+    definitions; the finite difference of g checks the oracle's M."""
+    O = oracle_mod
+    prob = _small_problem(O, n_t=25, n_s=20)
+    rng = np.random.default_rng(14)
+    T = D.rigid(_rand_rot(rng, 10), rng.normal(size=3) * 0.05)
+    kp = O.KernelParams(cutoff=0.0)
+    res = O.evaluate(prob, T, kp)
+    R, t = T[:3, :3], T[:3, 3]
+    for trial in range(3):
+        xi = rng.normal(size=6)
+        h = 1e-6
+        Tp, Tm = T @ O.exp_se3(h * xi), T @ O.exp_se3(-h * xi)
+        # gradient at the perturbed poses with Sigma_ij frozen at T
+        gp = O.evaluate(_frozen_problem(O, prob, T, Tp), Tp, kp).g
+        gm = O.evaluate(_frozen_problem(O, prob, T, Tm), Tm, kp).g
+        Dg = (gp - gm) / (2 * h)
+        T1 = np.zeros(6)
+        T2 = np.zeros(6)
+        for j in range(len(prob.src)):
+            p = R.T @ (prob.src[j] - t)
+            J = np.c_[-O.hat3(p), np.eye(3)]
+            Jxi = J @ xi
+            DJt = np.zeros((6, 3))
+            DJt[:3, :] = -O.hat3(Jxi)
+            for i in range(len(prob.tgt)):
+                Sig = _mat(prob.tgt_cov[i]) + R.T @ _mat(prob.src_cov[j]) @ R
+                A = np.linalg.inv(Sig)
+                r = prob.tgt[i] - p
+                fij = float(prob.tgt_feat[i] @ prob.src_feat[j]) * np.exp(-0.5 * r @ A @ r)
+                T1 += J.T @ A @ r * (-fij * r @ A @ Jxi)
+                T2 += fij * DJt @ A @ r
+        ref = -(T1 + T2 + res.M @ xi)
+        assert np.allclose(Dg, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+def test_gn_step_invariant_to_sigma2(oracle_mod):
+    """M, g and Gamma all scale with sigma^2 (and a common scale of c_ij), so
+    the step of Eq. (13) does not."""
+    O = oracle_mod
+    prob = _small_problem(O)
+    T = np.eye(4)
+    a = O.gn_step(O.evaluate(prob, T, O.KernelParams(sigma2=1.0)))
+    b = O.gn_step(O.evaluate(prob, T, O.KernelParams(sigma2=37.0)))
+    assert np.allclose(a, b, rtol=1e-10, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1: exact recovery where the frozen-Sigma bias vanishes
+# --------------------------------------------------------------------------
+
+def test_exact_recovery_isotropic(oracle_mod):
+    """With Z = G X (same points and features) and an isotropic kernel, the
+    RKHS inner product of Eq. (4) is maximal at T = G (Cauchy-Schwarz), and
+    G-CVO-2 must converge there."""
+    O = oracle_mod
+    pair = D.make_corner_pair(n_src=300, n_tgt=300, noise=0.0)
+    rng = np.random.default_rng(15)
+    G = D.rigid(_rand_rot(rng, 5), D.random_unit(rng) * 0.1)
+    tgt = pair.tgt_xyz.astype(np.float64)
+    src = D.apply(G, tgt)
+    prob = O.Problem.make(tgt, None, pair.tgt_feat, src, None, pair.tgt_feat)
+    kp = O.KernelParams(kernel_mode=1, cutoff=0.0, iso_ell=0.2)
+    out = O.register(prob, np.eye(4), kp, order=2, eps_tol=1e-12, k_max=100)
+    ang, dt = O.pose_error(out.T, G)
+    assert out.converged
+    assert ang < 1e-9 and dt < 1e-9
+
+
+def _spheres(rng, n_per=150):
+    pts, covs = [], []
+    for c, rad in (([0, 0, 0], 1.0), ([4, 0, 0], 1.4), ([0, 4, 1.5], 0.8)):
+        d = rng.normal(size=(n_per, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        pts.append(np.asarray(c) + rad * d)
+        for n in d:
+            covs.append(_sym(0.002 * np.outer(n, n) + 0.02 * (np.eye(3) - np.outer(n, n))))
+    return np.concatenate(pts), np.array(covs)
+
+
+def test_exact_recovery_spheres_anisotropic(oracle_mod):
+    """Points on spheres with covariances built from the exact normals: for a
+    pair on one sphere the reflection through their bisecting plane swaps the
+    two covariances, so r_ij is an eigenvector of Sigma_ij, the frozen-Sigma
+    gradient vanishes at the truth, and G-CVO-2 recovers G exactly."""
+    O = oracle_mod
+    rng = np.random.default_rng(16)
+    tgt, tc = _spheres(rng)
+    G = D.rigid(_rand_rot(rng, 3), D.random_unit(rng) * 0.08)
+    R = G[:3, :3]
+    src = D.apply(G, tgt)
+    sc = np.array([_sym(R @ _mat(s) @ R.T) for s in tc])
+    feat = np.ones((len(tgt), 1))
+    prob = O.Problem.make(tgt, tc, feat, src, sc, feat)
+    kp = O.KernelParams(cutoff=3.0)
+    assert np.abs(O.evaluate(prob, G, kp).g).max() < 1e-12 * O.evaluate(prob, G, kp).gabs.max()
+    out = O.register(prob, np.eye(4), kp, order=2, eps_tol=1e-12, k_max=100)
+    ang, dt = O.pose_error(out.T, G)
+    assert ang < 1e-9 and dt < 1e-9
+
+
+def test_loss_slices_single_maximum(oracle_mod):
+    """Appendix C: along 1-D slices of the pose around the truth, the
+    objective has one maximum, at the truth (isotropic identical-cloud case)."""
+    O = oracle_mod
+    pair = D.make_corner_pair(n_src=200, n_tgt=200, noise=0.0)
+    tgt = pair.tgt_xyz.astype(np.float64)
+    G = D.rigid(np.eye(3), np.zeros(3))
+    prob = O.Problem.make(tgt, None, pair.tgt_feat, tgt, None, pair.tgt_feat)
+    kp = O.KernelParams(kernel_mode=1, cutoff=0.0, iso_ell=0.15)
+    for axis in (1, 3, 5):
+        ts = np.linspace(-0.5, 0.5, 41) if axis < 3 else np.linspace(-1.0, 1.0, 41)
+        fs = []
+        for s in ts:
+            xi = np.zeros(6)
+            xi[axis] = s
+            fs.append(O.evaluate(prob, G @ O.exp_se3(xi), kp).f)
+        fs = np.array(fs)
+        k = int(np.argmax(fs))
+        assert k == 20
+        assert np.all(np.diff(fs[:k + 1]) > 0) and np.all(np.diff(fs[k:]) < 0)
+
+
+# --------------------------------------------------------------------------
+# G-CVO-1 line search (Eq. 9, Appendix B)
+# --------------------------------------------------------------------------
+
+def test_linesearch_polynomial_is_fourth_order(oracle_mod):
+    """sum_k c_k t^k must agree with G(t) = f(T exp(t xi)) (Sigma frozen) to
+    O(t^5): halving t divides the error by about 32.  The coefficients as
+    printed in Appendix B do not (their error is O(t^2))."""
+    O = oracle_mod
+    prob = _small_problem(O)
+    rng = np.random.default_rng(17)
+    T = D.rigid(_rand_rot(rng, 5), rng.normal(size=3) * 0.03)
+    kp = O.KernelParams(cutoff=0.0)
+    xi = rng.normal(size=6)
+    xi /= np.linalg.norm(xi)
+    c = O.linesearch_poly(prob, T, xi, kp)
+    c_lit = O.linesearch_poly(prob, T, xi, kp, literal=True)
+    res = O.evaluate(prob, T, kp)
+    assert c[0] == pytest.approx(res.f, rel=1e-12)
+    assert c[1] == pytest.approx(res.g @ xi, rel=1e-10)
+
+    def G(t):
+        Tt = T @ O.exp_se3(t * xi)
+        return O.evaluate(_frozen_problem(O, prob, T, Tt), Tt, kp).f
+
+    errs, errs_lit = [], []
+    for t in (0.02, 0.01, 0.005):
+        poly = sum(c[k] * t ** k for k in range(5))
+        poly_l = sum(c_lit[k] * t ** k for k in range(5))
+        errs.append(abs(G(t) - poly))
+        errs_lit.append(abs(G(t) - poly_l))
+    assert 20 < errs[0] / errs[1] < 45 and 20 < errs[1] / errs[2] < 45
+    assert errs_lit[1] > 100 * errs[1]
+
+
+def test_linesearch_root_rule(oracle_mod):
+    O = oracle_mod
+    # G'(t) = 1 - t^2 (c1 = 1, c3 = -1/3): smallest positive root 1
+    assert O.linesearch_step(np.array([0, 1.0, 0, -1.0 / 3.0, 0]), 1e-4) == pytest.approx(1.0)
+    # G'(t) = 1 + t^2 > 0: no real root, fall back to mu0
+    assert O.linesearch_step(np.array([0, 1.0, 0, 1.0 / 3.0, 0]), 1e-4) == 1e-4
+    # G'(t) = (t - 2)(t - 3)(t + 1): smallest positive root 2
+    d = np.poly1d([1, -4, 1, 6])
+    c = np.array([0, d.c[3], d.c[2] / 2, d.c[1] / 3, d.c[0] / 4])
+    assert O.linesearch_step(c, 1e-4) == pytest.approx(2.0)
+
+
+@pytest.mark.slow
+def test_second_order_needs_fewer_iterations(oracle_mod):
+    """Sec. 5.4: G-CVO-2 converges in tens of iterations where G-CVO-1 needs
+    many more."""
+    O = oracle_mod
+    pair = D.make_corner_pair(n_src=250, n_tgt=250, noise=0.0)
+    tgt = pair.tgt_xyz.astype(np.float64)
+    rng = np.random.default_rng(18)
+    G = D.rigid(_rand_rot(rng, 5), D.random_unit(rng) * 0.1)
+    prob = O.Problem.make(tgt, None, pair.tgt_feat, D.apply(G, tgt), None, pair.tgt_feat)
+    kp = O.KernelParams(kernel_mode=1, cutoff=0.0, iso_ell=0.2)
+    o2 = O.register(prob, np.eye(4), kp, order=2, eps_tol=1e-7, k_max=200)
+    o1 = O.register(prob, np.eye(4), kp, order=1, eps_tol=1e-7, k_max=200, mu0=1e-4)
+    e2 = O.pose_error(o2.T, G)
+    e1 = O.pose_error(o1.T, G)
+    assert o2.converged and len(o2.log) < 50
+    assert len(o1.log) > 3 * len(o2.log)
+    assert sum(e2) < 1e-6 and sum(e1) < 1e-5
