@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""G-CVO benchmark: pair-evals/s and registrations/s on LiDAR-like
+frame-to-frame tracking (64-beam scans of a procedural street, voxelised
+at 0.3 m, 100-frame trajectory, 1-2 m and <= 3 degrees between frames).
+
+One step = the whole hot path over one batch: per-point covariances of
+every frame (Eq. 7b + eigenvalue bound), the voxel hash of every target
+frame, and Algorithm 1 (G-CVO-2) for all consecutive frame pairs from the
+identity in one batched call (transform, pair kernel, FP64 reduction,
+solve, update until ||xi||_1 < eps_tol).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gcvo|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G-CVO kernel pair-evals/s & registrations/s at equal pose error vs plain"
+UNIT = "pair-evals/s"
+FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation, see the design doc
+EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
+KNN = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gcvo", choices=["gcvo", "reference"])
+    ap.add_argument("--frames", type=int, default=100)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--k-max", type=int, default=200)
+    ap.add_argument("--no-plain", action="store_true", help="skip the single-problem comparison")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Workload
+# ---------------------------------------------------------------------------
+
+def _frame_job(args):
+    config, n_frames, k = args
+    from paper_2606_10019_gb300 import datagen as D
+    seq = D.LidarSequence(n_frames=n_frames, config=config)
+    return seq.frame(k)
+
+
+def make_frames(n_frames: int, rank: int):
+    """Ray-cast and voxelise the frames in a spawn pool (before CUDA is
+    touched).  Each rank gets its own street and trajectory."""
+    import multiprocessing as mp
+    from paper_2606_10019_gb300 import datagen as D
+    config = 2 + 100 * rank
+    seq = D.LidarSequence(n_frames=n_frames, config=config)
+    nproc = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        frames = pool.map(_frame_job, [(config, n_frames, k) for k in range(n_frames)])
+    T_true = [D.inv_rigid(seq.poses[k + 1]) @ seq.poses[k] for k in range(n_frames - 1)]
+    return frames, T_true
+
+
+def pose_errors(T_est, T_true):
+    from scipy.spatial.transform import Rotation
+    rot, tr = [], []
+    for Te, Tt in zip(T_est, T_true):
+        D = np.linalg.inv(Tt) @ Te
+        rot.append(math.degrees(np.linalg.norm(Rotation.from_matrix(D[:3, :3]).as_rotvec())))
+        tr.append(float(np.linalg.norm(D[:3, 3])))
+    rot, tr = np.array(rot), np.array(tr)
+    return dict(rot_deg_median=float(np.median(rot)), rot_deg_p95=float(np.percentile(rot, 95)),
+                trans_m_median=float(np.median(tr)), trans_m_p95=float(np.percentile(tr, 95)))
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = np.array([r[0] for r in rows])
+        pw = np.array([r[2] for r in rows])
+        load = pw >= np.percentile(pw, 50)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm[load])), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": reasons, "samples": len(rows), "power_w_max": float(pw.max())}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gcvo(args, rank, world):
+    frames, T_true = make_frames(args.frames, rank)
+    import torch
+    from paper_2606_10019_gb300 import build as B
+    from paper_2606_10019_gb300 import gcvo as G
+    B.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = G.gcvo_create(local, stream)
+    kp = G.kernel_params(eig_max=EIG_MAX, eig_ratio=100.0, knn=KNN)
+    sp = G.solver_params(order=2, k_max=args.k_max, eps_tol=args.eps)
+    F = len(frames)
+    n_pts = [len(x) for x, _ in frames]
+    # inputs resident in HBM: SoA xyz (3, n) and intensity (1, n) per frame
+    xyz = [torch.from_numpy(np.ascontiguousarray(x.T)).to(dev) for x, _ in frames]
+    feat = [torch.from_numpy(np.ascontiguousarray(f.T)).to(dev) for _, f in frames]
+    cov = [torch.empty((6, n), dtype=torch.float32, device=dev) for n in n_pts]
+    grids = [None] * (F - 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(xyz_in, feat_in):
+        for k in range(F):
+            G.gcvo_estimate_covariances(ctx, xyz_in[k], kp, cov[k])
+        for k in range(F - 1):
+            if grids[k] is None:
+                grids[k] = G.gcvo_build_grid(ctx, xyz_in[k], cov[k], feat_in[k], kp)
+            else:
+                G.gcvo_rebuild_grid(ctx, grids[k], xyz_in[k], cov[k], feat_in[k], kp)
+        probs = [(grids[k], xyz_in[k + 1], cov[k + 1], feat_in[k + 1], np.eye(4)) for k in range(F - 1)]
+        return G.gcvo_register_batched(ctx, probs, sp, want_log=True)
+
+    for _ in range(args.warmup):
+        out = step(xyz, feat)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: device-resident inputs
+    G.gcvo_profile_enable(ctx, True)
+    clocks = Clocks(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_evals = 0
+    kept = 0
+    regs = 0
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()                       # L2 flush, outside the events
+        ev[s][0].record(stream)
+        T_est, logs, n_iter, status = step(xyz, feat)
+        ev[s][1].record(stream)
+        pair_evals += sum(L["n_pairs"] for lg in logs for L in lg)
+        kept += sum(L["n_kept"] for lg in logs for L in lg)
+        regs += len(T_est)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof = G.gcvo_profile_read(ctx)
+    G.gcvo_profile_enable(ctx, False)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(ms_steps) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = torch.tensor([float(pair_evals), float(regs)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot)
+        t_dev = float(t.item())
+        pair_evals_all, regs_all = tot.tolist()
+    else:
+        pair_evals_all, regs_all = float(pair_evals), float(regs)
+    value = pair_evals_all / t_dev
+    errs = pose_errors(list(T_est), T_true)
+    n_conv = int(np.sum(status == 0))
+    iters = n_iter.tolist()
+
+    # ---- end to end: host (pinned) inputs copied in every step, poses read back
+    hx = [torch.from_numpy(np.ascontiguousarray(x.T)).pin_memory() for x, _ in frames]
+    hf = [torch.from_numpy(np.ascontiguousarray(f.T)).pin_memory() for _, f in frames]
+    h2d = sum(a.numel() * 4 for a in hx) + sum(a.numel() * 4 for a in hf)
+    d2h = (F - 1) * 16 * 8
+    e2e_pairs = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        dx = [a.to(dev, non_blocking=True) for a in hx]
+        df = [a.to(dev, non_blocking=True) for a in hf]
+        T_e, logs_e, _, _ = step(dx, df)
+        e2e_pairs += sum(L["n_pairs"] for lg in logs_e for L in lg)
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+
+    # ---- plain single-problem G-CVO on the same pairs (registration only)
+    plain = None
+    if not args.no_plain and rank == 0:
+        probs = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(F - 1)]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Tb, _, _, _ = G.gcvo_register_batched(ctx, probs, sp)
+        torch.cuda.synchronize(dev)
+        t_b = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Ts = []
+        for p in probs:
+            T1, _, _, _ = G.gcvo_register(ctx, *p, sp, want_log=False)
+            Ts.append(T1)
+        torch.cuda.synchronize(dev)
+        t_s = time.perf_counter() - t0
+        plain = {"registrations_per_s_batched": (F - 1) / t_b, "registrations_per_s_plain": (F - 1) / t_s,
+                 "batched_over_plain": t_s / t_b,
+                 "max_pose_diff_batched_vs_plain": float(max(np.abs(np.array(Ts) - Tb).max(), 0.0))}
+
+    # ---- roofline of the pair kernel
+    n_launch = max(1, prof["n_pair_launches"])
+    t_pair = prof["pair_kernel_ms"] / 1e3
+    achieved = pair_evals * FLOP_PER_PAIR / t_pair / 1e12 if t_pair > 0 else 0.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_ghz = (clk or {}).get("sm_max_mhz", 2070.0) / 1e3
+    peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pair (EVAL)", "launches": prof["n_pair_launches"],
+                "avg_launch_ms": prof["pair_kernel_ms"] / n_launch,
+                "pair_kernel_share_of_step": t_pair / t_dev if t_dev > 0 else None,
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz (max SM clock)"}
+
+    res = None
+    if rank == 0:
+        cpu = cpu_baseline(frames, T_true)
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"lidar-64beam street tracking, {F} frames voxelised at 0.3 m "
+                                   f"(~{int(np.mean(n_pts))} points), {F - 1} frame pairs from the identity",
+                       "points_per_frame_mean": float(np.mean(n_pts)), "frame_pairs": F - 1,
+                       "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, "
+                                 f"eig clamp [{EIG_MAX / 100}, {EIG_MAX}]",
+                       "precision": "FP32 pair kernel, compensated FP32 group partials, FP64 reduction/solve/exp",
+                       "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
+                       "parallelism": f"{world} independent replica(s), no collective"},
+            "registrations_per_s": regs_all / t_dev,
+            "pair_evals_per_step": pair_evals / args.steps, "kept_pairs_per_step": kept / args.steps,
+            "iterations_mean": float(np.mean(iters)), "converged": f"{n_conv}/{len(iters)}",
+            "pose_error_vs_truth": errs,
+            "roofline": roofline,
+            "e2e": {"value": e2e_pairs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": prof["n_launches"],
+            "clocks": clk,
+            "plain_vs_batched": plain,
+            "cpu_baseline": cpu,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return res
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(frames, k=0):
+    """Covariances of one frame pair and one evaluation of f, g, H at the
+    identity, by the FP64 brute-force oracle.  Returns (pair-evals, seconds)."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    (xt, ft), (xs, fs) = frames[k], frames[k + 1]
+    tc = O.covariances(xt, KNN, EIG_MAX, 100.0)
+    sc = O.covariances(xs, KNN, EIG_MAX, 100.0)
+    prob = O.Problem.make(xt, tc, ft, xs, sc, fs)
+    rho = 3.0 * math.sqrt(2.0 * EIG_MAX)
+    r = O.evaluate(prob, np.eye(4), O.KernelParams(cutoff=3.0, rho=rho))
+    return r.n_rho, time.perf_counter() - t0
+
+
+def cpu_baseline(frames, T_true):
+    from oracle import oracle as O
+    O.build()
+    n, t = oracle_sample(frames)
+    return {"value": n / t, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "one frame pair: brute-force kNN covariances of both clouds and one all-pairs FP64 "
+                      "evaluation of f, g, H at the identity (pairs within rho counted)",
+            "seconds": t}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    frames, T_true = make_frames(2, 0)
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(frames)
+    tot_n, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        n, t = oracle_sample(frames)
+        tot_n += n
+        tot_t += t
+    v = tot_n / tot_t
+    res = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot_t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "lidar-64beam street tracking, voxelised at 0.3 m; one frame pair per step"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": "per step: kNN covariances of one frame pair and one all-pairs FP64 evaluation"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+    return res
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gcvo(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

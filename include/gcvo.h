@@ -1,0 +1,229 @@
+/*
+ * gcvo.h -- C ABI of the GB300 (sm_103a) G-CVO registration library.
+ *
+ * G-CVO registers a source ("new") point cloud Z to a target cloud X by
+ * maximising the RKHS inner product of Eq. (4)-(5) of the paper,
+ *
+ *     f(T) = sum_ij <l_i^X, l_j^Z> k(x_i, T^{-1} z_j),
+ *     k(x, z) = sigma^2 exp(-1/2 r^T Sigma_ij^{-1} r),  r = x - T^{-1} z,
+ *     Sigma_ij = Sigma(x_i; X) + R^T Sigma(z_j; Z) R            (Eq. 7),
+ *
+ * with the Riemannian gradient of Lemma 1 (Eq. 8), the Gauss-Newton matrix
+ * and Levi-Civita correction of Eq. (10)-(12), and the second-order update
+ * T <- T exp(-H_GN^{-1} g) of Eq. (13) inside Algorithm 1.
+ *
+ * Conventions shared by every call:
+ *  - A pose T is a 4x4 row-major double matrix [R t; 0 1] acting as
+ *    T x = R x + t (Sec. 2.1).  The optimum satisfies T^{-1} z_j ~ x_i.
+ *  - Tangent vectors are twists xi = (omega, v), rotation first (Sec. 2.1),
+ *    left-trivialised; the gradient g = (g_omega, g_v).
+ *  - Point arrays are structure-of-arrays float32: xyz is 3 x n
+ *    (x[0..n), y[0..n), z[0..n)), a covariance array is 6 x n holding
+ *    (xx, xy, xz, yy, yz, zz), a feature array is feat_dim x n.
+ *  - Point arrays may live in device memory or in host memory; host arrays
+ *    are copied to the device by the call.  They are only read, and must stay
+ *    valid until the call returns.
+ *  - All work runs on the stream given to gcvo_create, in stream order.
+ *    Calls that return host results (eval, register) synchronise that stream
+ *    before returning.  A context is used by one host thread at a time.
+ *  - Every call returns a gcvo_status.  On any status other than GCVO_OK the
+ *    outputs are left untouched, except where a call documents otherwise.
+ *    Device-side failures (a bounded wait that ran out, a capacity limit, a
+ *    non-finite reduction) are reported through a status word that the call
+ *    reads back; no kernel traps.
+ *  - Device memory for contexts and grids is allocated by the library with
+ *    cudaMalloc and released by the matching destroy call.
+ */
+#ifndef GCVO_H
+#define GCVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GCVO_OK = 0,
+    GCVO_ERR_INVALID_ARG = 1,   /* null pointer, bad size or parameter */
+    GCVO_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    GCVO_ERR_WORKSPACE = 3,     /* device memory could not be allocated */
+    GCVO_ERR_SINGULAR = 4,      /* M - Gamma of Eq. (13) could not be factorised */
+    GCVO_ERR_NO_OVERLAP = 5,    /* no pair passed the kernel cutoff (f = 0) */
+    GCVO_ERR_NOT_CONVERGED = 6, /* k_max iterations ran without ||xi||_1 < eps_tol */
+    GCVO_ERR_NONFINITE = 7,     /* an input or a reduced value is NaN or Inf */
+    GCVO_ERR_TIMEOUT = 8,       /* a bounded device-side wait ran out */
+    GCVO_ERR_CAPACITY = 9       /* a size limit of this build was exceeded */
+} gcvo_status;
+
+typedef struct gcvo_ctx gcvo_ctx;   /* device, stream, scratch buffers */
+typedef struct gcvo_grid gcvo_grid; /* voxel-hashed copy of a target cloud */
+
+/* Kernel parameters (Eq. 7 and the Remark that follows it). */
+typedef struct {
+    int kernel_mode;    /* 0: anisotropic kernel of Eq. (7) (default);
+                           1: isotropic CVO kernel, Sigma_ij = iso_ell^2 I (Remark 3) */
+    double sigma2;      /* kernel amplitude sigma^2 of Eq. (7a); default 1 */
+    double cutoff;      /* a pair contributes only if r^T Sigma_ij^{-1} r <= cutoff^2;
+                           must be > 0 (default 3) */
+    double iso_ell;     /* isotropic length scale (kernel_mode 1) */
+    int knn;            /* n of Eq. (7b): neighbours per covariance, self included;
+                           2..16 (default 10) */
+    double eig_max;     /* eigenvalue bound of the Remark after Eq. (7): every
+                           eigenvalue of a per-point covariance is clamped to */
+    double eig_ratio;   /* [eig_max / eig_ratio, eig_max]; eig_max <= 0 disables */
+    int feat_dim;       /* l: channels of the pose-invariant features, 1..3;
+                           c_ij = <l_i, l_j> (Eq. 5) */
+    double cell_size;   /* target voxel edge; <= 0 picks the kernel range */
+} gcvo_kernel_params;
+
+/* Solver parameters (Algorithm 1 inputs mu_0, k_max, eps_tol). */
+typedef struct {
+    int order;          /* 2: G-CVO-2, Gauss-Newton step of Eq. (13);
+                           1: G-CVO-1, gradient step with the line search of Eq. (9) */
+    int k_max;          /* iteration limit, 1..1000 */
+    double eps_tol;     /* stop when ||xi^(k)||_1 < eps_tol */
+    double mu0;         /* G-CVO-1 minimum step of Eq. (9) */
+} gcvo_solver_params;
+
+/* One row of the iteration log: values at the pose T^(k) the iteration
+ * started from, and the step it took. */
+typedef struct {
+    double f;           /* objective, Eq. (5) */
+    double g[6];        /* Riemannian gradient (g_omega, g_v), Eq. (8) */
+    double xi[6];       /* step xi^(k) */
+    double xi_l1;       /* ||xi^(k)||_1 */
+    double T[16];       /* T^(k), row-major */
+    int64_t n_pairs;    /* pairs with |r_ij| <= rho examined by the kernel */
+    int64_t n_kept;     /* pairs with d^2 <= cutoff^2 */
+} gcvo_iter_log;
+
+/* Counters returned by gcvo_eval. */
+typedef struct {
+    int64_t n_pairs;      /* pairs with |r_ij| <= rho (pair-evals) */
+    int64_t n_kept;       /* pairs with d^2 <= cutoff^2 */
+    int64_t n_candidates; /* target points scanned in the voxel neighbourhoods */
+    double rho;           /* Euclidean radius that bounds the cutoff ellipsoids */
+} gcvo_eval_stats;
+
+/* Description of one problem for gcvo_register_batched. */
+typedef struct {
+    const gcvo_grid *target;
+    const float *src_xyz;   /* 3 x n_src */
+    const float *src_cov;   /* 6 x n_src (ignored in kernel_mode 1) */
+    const float *src_feat;  /* feat_dim x n_src */
+    int64_t n_src;
+    double T0[16];          /* initial pose T^(0) */
+} gcvo_problem;
+
+/* Library-wide limits of this build. */
+#define GCVO_MAX_FEAT 3
+#define GCVO_MAX_KNN 16
+#define GCVO_MAX_KMAX 1000
+#define GCVO_MAX_PROBLEMS 4096
+
+/* Human-readable name of a status code (static storage). */
+const char *gcvo_status_string(gcvo_status s);
+
+/* Default kernel / solver parameters (cutoff 3, sigma2 1, knn 10, G-CVO-2,
+ * k_max 200, eps_tol 1e-6, mu0 1e-10; the paper gives no mu0, and a
+ * minimum step must stay below 2 / lambda_max(M) or G-CVO-1 leaves its fixed
+ * point). */
+void gcvo_default_kernel_params(gcvo_kernel_params *p);
+void gcvo_default_solver_params(gcvo_solver_params *p);
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL selects the legacy default stream).  The context
+ * owns its scratch memory.  *ctx is set on success. */
+gcvo_status gcvo_create(gcvo_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and its device memory (synchronises its stream). */
+gcvo_status gcvo_destroy(gcvo_ctx *ctx);
+
+/* Eq. (7b) plus the eigenvalue bound of the Remark after Eq. (7): for each
+ * point, Sigma = 1/(n-1) sum_{y in N_n(x)} (y - x)(y - x)^T over its n = knn
+ * nearest points (the point itself included, ties broken by lower index),
+ * then each eigenvalue is clamped to [eig_max/eig_ratio, eig_max].
+ * xyz: 3 x n input; cov_out: 6 x n output, device memory, caller-owned.
+ * Requires n >= knn.  Stream-ordered; does not synchronise. */
+gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n,
+                                      const gcvo_kernel_params *params, float *cov_out);
+
+/* Build the voxel hash of a target cloud X (Eq. 5's x_i with Sigma(x_i; X)
+ * and features l_i^X): points are keyed by voxel, sorted, copied into a
+ * grid-owned packed layout and indexed by an open-addressing hash of the
+ * occupied voxels.  cov may be NULL in kernel_mode 1.  The grid keeps the
+ * kernel parameters it was built with.  Synchronises the stream. */
+gcvo_status gcvo_build_grid(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat,
+                            int64_t n, const gcvo_kernel_params *params, gcvo_grid **grid_out);
+
+/* Rebuild an existing grid from a new cloud, reusing its device memory
+ * when it is large enough (frame-to-frame tracking re-targets every frame).
+ * Same inputs and semantics as gcvo_build_grid; on failure the grid is left
+ * in an unusable state and may only be destroyed or rebuilt.  The grid must
+ * belong to the context's device.  Synchronises the stream. */
+gcvo_status gcvo_rebuild_grid(gcvo_ctx *ctx, gcvo_grid *grid, const float *xyz, const float *cov, const float *feat,
+                              int64_t n, const gcvo_kernel_params *params);
+
+/* Release a grid.  May be called after the context that built it was
+ * destroyed; waits for work still using the grid's memory. */
+gcvo_status gcvo_grid_destroy(gcvo_grid *grid);
+
+/* Number of points and occupied voxels of a grid. */
+gcvo_status gcvo_grid_info(const gcvo_grid *grid, int64_t *n_points, int64_t *n_cells, double *cell_size);
+
+/* One evaluation at pose T (row-major 4x4, host): the objective f of Eq. (5),
+ * the gradient g of Eq. (8) and H = H_GN = -M + Gamma of Eq. (11)-(12)
+ * (row-major 6x6, host), summed over every pair with d^2 <= cutoff^2.
+ * M_out (host 6x6, may be NULL) receives M = sum f_ij J_j^T Sigma_ij^{-1} J_j
+ * of Eq. (11); stats may be NULL.  Synchronises the stream. */
+gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                      const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
+                      double H[36], double *M_out, gcvo_eval_stats *stats);
+
+/* Algorithm 1 from T0: at most k_max iterations of transform, pair
+ * evaluation, reduction and update (G-CVO-2 solves (M - Gamma) xi = g, Eq.
+ * (13); G-CVO-1 takes xi = mu g with mu from Eq. (9)), stopping when
+ * ||xi||_1 < eps_tol.  T_out receives the final pose (row-major, host);
+ * log (host, capacity k_max rows, may be NULL) the per-iteration values;
+ * n_iter the number of iterations run.  Returns GCVO_ERR_NOT_CONVERGED (with
+ * all outputs written) when k_max ran out.  Synchronises the stream. */
+gcvo_status gcvo_register(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                          const float *src_feat, int64_t n_src, const double T0[16],
+                          const gcvo_solver_params *params, double T_out[16], gcvo_iter_log *log, int *n_iter);
+
+/* Algorithm 1 for n_problems independent problems in one set of launches:
+ * every iteration evaluates all still-active problems in one pair-kernel
+ * launch and updates them in one solver launch; a problem that converged
+ * or failed is masked out.  T_out: n_problems x 16 (host); logs: n_problems
+ * x k_max rows (host, may be NULL); n_iter and status: n_problems (host).
+ * The call returns GCVO_OK when every problem ran (per-problem outcomes
+ * are in status[]).  All problems must use grids built with the same
+ * kernel_mode and feat_dim.  Synchronises the stream. */
+gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_problem *problems,
+                                  const gcvo_solver_params *params, double *T_out, gcvo_iter_log *logs,
+                                  int *n_iter, int *status);
+
+/* Profiling counters (no counterpart in the paper; used to measure the
+ * pair kernel against its roofline). */
+typedef struct {
+    int64_t n_launches;      /* kernels launched by the library in this process
+                                since gcvo_profile_enable */
+    int64_t n_pair_launches; /* pair-kernel launches (evaluation passes) timed */
+    double pair_kernel_ms;   /* their summed device time, from CUDA events
+                                recorded on the context's stream around each launch */
+} gcvo_profile;
+
+/* Turn profiling on (enable != 0) or off and reset the counters.
+ * Synchronises the stream. */
+gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable);
+
+/* Read the counters accumulated since gcvo_profile_enable (synchronises the
+ * stream). */
+gcvo_status gcvo_profile_read(gcvo_ctx *ctx, gcvo_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCVO_H */

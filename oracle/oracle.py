@@ -347,7 +347,7 @@ class RegisterResult:
 
 
 def register(prob: Problem, T0, kp: KernelParams, order: int = 2, k_max: int = 200,
-             eps_tol: float = 1e-8, mu0: float = 1e-4, literal_ls: bool = False) -> RegisterResult:
+             eps_tol: float = 1e-8, mu0: float = 1e-10, literal_ls: bool = False) -> RegisterResult:
     """Alg. 1: repeat {evaluate f, grad f (and H_GN) at T^(k); step xi^(k);
     T^(k+1) = T^(k) exp(xi^(k))} while ||xi^(k)||_1 >= eps_tol and k < k_max.
     The first iteration always runs."""

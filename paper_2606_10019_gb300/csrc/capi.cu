@@ -1,0 +1,694 @@
+// The extern "C" entry points declared in include/gcvo.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "pair.cuh"
+
+using namespace gcvo;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool valid_kernel_params(const gcvo_kernel_params *p) {
+    if (!p) return false;
+    if (p->kernel_mode != 0 && p->kernel_mode != 1) return false;
+    if (!(p->cutoff > 0) || !std::isfinite(p->cutoff)) return false;
+    if (!(p->sigma2 > 0) || !std::isfinite(p->sigma2)) return false;
+    if (p->kernel_mode == 1 && !(p->iso_ell > 0)) return false;
+    if (p->feat_dim < 1 || p->feat_dim > GCVO_MAX_FEAT) return false;
+    return true;
+}
+
+// Copy `count` floats to the device when `p` is host memory.  `off` is the
+// running float offset inside `buf` (grown by the caller beforehand).
+gcvo_status stage(gcvo_ctx *ctx, const float *p, size_t count, DevBuf &buf, size_t &off, const float **out) {
+    if (!p) {
+        *out = nullptr;
+        return GCVO_OK;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return GCVO_OK;
+    }
+    float *d = buf.as<float>() + off;
+    GCVO_CUDA(cudaMemcpyAsync(d, p, count * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    off += (count + 63) & ~size_t(63);
+    *out = d;
+    return GCVO_OK;
+}
+
+size_t staged_floats(const float *p, size_t count) {
+    if (!p || is_device_ptr(p)) return 0;
+    return (count + 63) & ~size_t(63);
+}
+
+gcvo_status host_pinned(gcvo_ctx *ctx, size_t bytes, void **out) {
+    if (ctx->host_pinned_bytes < bytes) {
+        if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+        ctx->host_pinned = nullptr;
+        ctx->host_pinned_bytes = 0;
+        if (cudaMallocHost(&ctx->host_pinned, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return GCVO_ERR_WORKSPACE;
+        }
+        ctx->host_pinned_bytes = bytes;
+    }
+    *out = ctx->host_pinned;
+    return GCVO_OK;
+}
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+// Everything the pair / finalize kernels need for a set of problems.
+struct Prepared {
+    int n_problems = 0;
+    int n_groups = 0;
+    int64_t n_points = 0;
+    int feat_dim = 1;
+    bool iso = false;
+    std::vector<ProbDev> probs;
+};
+
+gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) {
+    cudaStream_t s = ctx->stream;
+    if (np < 1 || np > GCVO_MAX_PROBLEMS || !pr) return GCVO_ERR_INVALID_ARG;
+    const gcvo_kernel_params &kp0 = pr[0].target ? pr[0].target->kp : gcvo_kernel_params{};
+    for (int p = 0; p < np; ++p) {
+        const gcvo_problem &q = pr[p];
+        if (!q.target || !q.src_xyz || q.n_src < 1 || q.n_src > (1 << 28)) return GCVO_ERR_INVALID_ARG;
+        if (q.target->kp.kernel_mode != kp0.kernel_mode || q.target->kp.feat_dim != kp0.feat_dim)
+            return GCVO_ERR_INVALID_ARG;
+        if (q.target->kp.kernel_mode == 0 && !q.src_cov) return GCVO_ERR_INVALID_ARG;
+        for (int k = 0; k < 16; ++k)
+            if (!std::isfinite(q.T0[k])) return GCVO_ERR_NONFINITE;
+    }
+    P.n_problems = np;
+    P.iso = kp0.kernel_mode == 1;
+    P.feat_dim = kp0.feat_dim;
+    // stage host inputs
+    size_t need = 0;
+    int64_t N = 0;
+    for (int p = 0; p < np; ++p) {
+        const gcvo_problem &q = pr[p];
+        need += staged_floats(q.src_xyz, 3 * (size_t)q.n_src);
+        if (!P.iso) need += staged_floats(q.src_cov, 6 * (size_t)q.n_src);
+        need += staged_floats(q.src_feat, (size_t)P.feat_dim * q.n_src);
+        N += q.n_src;
+    }
+    if (N > (int64_t)1 << 30) return GCVO_ERR_CAPACITY;
+    P.n_points = N;
+    if (need) GCVO_TRY(ctx->stage_xyz.ensure(need * sizeof(float), s));
+    std::vector<SrcDesc> desc(np);
+    size_t off = 0;
+    int64_t max_n = 0;
+    for (int p = 0; p < np; ++p) {
+        const gcvo_problem &q = pr[p];
+        SrcDesc &d = desc[p];
+        GCVO_TRY(stage(ctx, q.src_xyz, 3 * (size_t)q.n_src, ctx->stage_xyz, off, &d.xyz));
+        d.cov = nullptr;
+        if (!P.iso) GCVO_TRY(stage(ctx, q.src_cov, 6 * (size_t)q.n_src, ctx->stage_xyz, off, &d.cov));
+        GCVO_TRY(stage(ctx, q.src_feat, (size_t)P.feat_dim * q.n_src, ctx->stage_xyz, off, &d.feat));
+        d.n = q.n_src;
+        d.offset = 0;
+        d.inv_hf = 4.0f / q.target->store.d.h;
+        max_n = std::max<int64_t>(max_n, q.n_src);
+    }
+    int64_t acc = 0;
+    for (int p = 0; p < np; ++p) {
+        desc[p].offset = acc;
+        acc += desc[p].n;
+    }
+
+    // device buffers
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t small_need = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 3 + al(sizeof(int)) * 4;
+    GCVO_TRY(ctx->small.ensure(small_need + 4096, s));
+    char *sp = ctx->small.as<char>();
+    SrcDesc *d_desc = reinterpret_cast<SrcDesc *>(sp);
+    sp += al(np * sizeof(SrcDesc));
+    int *d_lam = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_pg0 = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_pg1 = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_ngroups = reinterpret_cast<int *>(sp);
+
+    GCVO_TRY(ctx->sort_keys.ensure(N * sizeof(unsigned long long), s));
+    GCVO_TRY(ctx->sort_vals.ensure(al(N * sizeof(int)) * 5, s));
+    GCVO_TRY(ctx->sort_tmp.ensure(radix_sort_scratch_bytes(N), s));
+    GCVO_TRY(ctx->scan_tmp.ensure(scan_scratch_bytes(N) + 1024, s));
+    GCVO_TRY(ctx->src_pos.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->src_ca.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->src_cb.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->grp_start.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->grp_count.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->grp_prob.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->status_word.ensure(256, s));
+    char *vp = ctx->sort_vals.as<char>();
+    int *vals = reinterpret_cast<int *>(vp);
+    int *prob_of = reinterpret_cast<int *>(vp + al(N * sizeof(int)));
+    int *local = reinterpret_cast<int *>(vp + 2 * al(N * sizeof(int)));
+    int *seg = reinterpret_cast<int *>(vp + 3 * al(N * sizeof(int)));
+    int *gid = reinterpret_cast<int *>(vp + 4 * al(N * sizeof(int)));
+
+    GCVO_CUDA(cudaMemcpyAsync(d_desc, desc.data(), np * sizeof(SrcDesc), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(cudaMemsetAsync(d_lam, 0, np * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(d_pg0, 0x7f, np * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(d_pg1, 0, np * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(ctx->status_word.ptr, 0, 256, s));
+    GCVO_CUDA(cudaMemsetAsync(ctx->grp_count.ptr, 0, N * sizeof(int), s));
+
+    SrcArgs sa{};
+    sa.desc = d_desc;
+    sa.keys = ctx->sort_keys.as<unsigned long long>();
+    sa.vals = vals;
+    sa.prob_of = prob_of;
+    sa.local = local;
+    sa.lam_enc = d_lam;
+    sa.status_word = ctx->status_word.as<unsigned>();
+    sa.spos = ctx->src_pos.as<float4>();
+    sa.sca = ctx->src_ca.as<float4>();
+    sa.scb = ctx->src_cb.as<float4>();
+    sa.feat_dim = P.feat_dim;
+    sa.iso = P.iso;
+    GCVO_CUDA(launch_src_keys(sa, np, max_n, s));
+    GCVO_TRY(radix_sort_pairs(sa.keys, vals, N, 30 + std::max(1, ceil_log2(np)), ctx->sort_tmp.ptr,
+                              ctx->sort_tmp.bytes, s));
+    GCVO_CUDA(launch_src_segments(sa.keys, N, seg, s));
+    GCVO_TRY(scan_inclusive_max(seg, N, ctx->scan_tmp.ptr, s));
+    GCVO_CUDA(launch_src_group_heads(seg, N, gid, s));
+    GCVO_TRY(scan_inclusive_sum(gid, N, ctx->scan_tmp.ptr, s));
+    GCVO_CUDA(launch_src_groups(sa, sa.keys, gid, N, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(),
+                                ctx->grp_prob.as<int>(), d_pg0, d_pg1, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_ngroups, gid + N - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+
+    // read back group count, group ranges, source eigenvalue bounds
+    void *hp;
+    GCVO_TRY(host_pinned(ctx, (size_t)(3 * np + 8) * sizeof(int), &hp));
+    int *h = static_cast<int *>(hp);
+    GCVO_CUDA(cudaMemcpyAsync(h, d_ngroups, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 1, ctx->status_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8, d_lam, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8 + np, d_pg0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 2 * np, d_pg1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaStreamSynchronize(s));
+    if (h[1] & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
+    P.n_groups = h[0];
+    P.probs.assign(np, ProbDev{});
+    for (int p = 0; p < np; ++p) {
+        ProbDev &d = P.probs[p];
+        const gcvo_problem &q = pr[p];
+        const gcvo_grid *G = q.target;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) d.T[3 * r + c] = q.T0[4 * r + c];
+            d.T[9 + r] = q.T0[4 * r + 3];
+        }
+        d.status = 0;
+        d.iter = 0;
+        d.g0 = h[8 + np + p];
+        d.g1 = h[8 + 2 * np + p];
+        int le = h[8 + p];
+        int li = le >= 0 ? le : le ^ 0x7fffffff;
+        float lam_src;
+        memcpy(&lam_src, &li, 4);
+        const gcvo_kernel_params &kp = G->kp;
+        double c2 = kp.cutoff * kp.cutoff;
+        double rho2;
+        if (kp.kernel_mode == 1)
+            rho2 = c2 * kp.iso_ell * kp.iso_ell * (1.0 + 1e-5);
+        else
+            rho2 = c2 * ((double)G->store.d.lam_max + (double)lam_src) * (1.0 + 2e-4) + 1e-12;
+        d.rho2 = (float)rho2;
+        d.c2 = (float)c2;
+        d.sigma2 = (float)kp.sigma2;
+        d.iso_inv = kp.kernel_mode == 1 ? (float)(1.0 / (kp.iso_ell * kp.iso_ell)) : 0.f;
+    }
+    // per-iteration buffers
+    GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_groups, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,
+                                 s));
+    GCVO_TRY(ctx->probs.ensure(np * sizeof(ProbDev), s));
+    GCVO_TRY(ctx->grids.ensure(np * sizeof(GridDev), s));
+    GCVO_TRY(ctx->evalout.ensure(np * sizeof(EvalOut) + 256, s));
+    std::vector<GridDev> gd(np);
+    for (int p = 0; p < np; ++p) gd[p] = pr[p].target->store.d;
+    GCVO_CUDA(cudaMemcpyAsync(ctx->probs.ptr, P.probs.data(), np * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(cudaMemcpyAsync(ctx->grids.ptr, gd.data(), np * sizeof(GridDev), cudaMemcpyHostToDevice, s));
+    // host staging buffers must stay valid until the copies ran
+    GCVO_CUDA(cudaStreamSynchronize(s));
+    return GCVO_OK;
+}
+
+struct IterBufs {
+    PairArgs pa;
+    FinalizeArgs fa;
+    int *work;
+    int grid;
+};
+
+gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *part = ctx->partial.as<char>();
+    size_t ng = (size_t)std::max(P.n_groups, 1);
+    float *pf = reinterpret_cast<float *>(part);
+    long long *pc = reinterpret_cast<long long *>(part + al(ng * 64 * sizeof(float)));
+    int *work = reinterpret_cast<int *>(ctx->status_word.as<char>() + 64);
+    int *n_active = work + 1;
+    const int *d_ngroups = reinterpret_cast<const int *>(ctx->small.as<char>() +
+                                                        al(P.n_problems * sizeof(SrcDesc)) +
+                                                        3 * al(P.n_problems * sizeof(int)));
+    PairArgs &a = b.pa;
+    a.spos = ctx->src_pos.as<float4>();
+    a.sca = ctx->src_ca.as<float4>();
+    a.scb = ctx->src_cb.as<float4>();
+    a.gstart = ctx->grp_start.as<int>();
+    a.gcount = ctx->grp_count.as<int>();
+    a.gprob = ctx->grp_prob.as<int>();
+    a.n_groups = d_ngroups;
+    a.probs = ctx->probs.as<ProbDev>();
+    a.grids = ctx->grids.as<GridDev>();
+    a.part = pf;
+    a.counts = pc;
+    a.work = work;
+    a.status_word = ctx->status_word.as<unsigned>();
+    a.ls_literal = 0;
+    FinalizeArgs &f = b.fa;
+    f.probs = ctx->probs.as<ProbDev>();
+    f.grids = ctx->grids.as<GridDev>();
+    f.part = pf;
+    f.counts = pc;
+    f.evalout = ctx->evalout.as<EvalOut>();
+    f.logs = dlogs;
+    f.n_active = n_active;
+    f.n_problems = P.n_problems;
+    f.k_max = k_max;
+    f.eps_tol = 0;
+    f.mu0 = 0;
+    b.work = work;
+    int per_sm = pair_blocks_per_sm(PAIR_EVAL, P.iso, P.feat_dim);
+    if (per_sm < 1) per_sm = 1;
+    int want = (P.n_groups + PAIR_WARPS - 1) / PAIR_WARPS;
+    b.grid = std::max(1, std::min(want, per_sm * ctx->sm_count));
+    return GCVO_OK;
+}
+
+gcvo_status check_status_word(gcvo_ctx *ctx) {
+    unsigned w = 0;
+    GCVO_CUDA(cudaMemcpyAsync(&w, ctx->status_word.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (w & DEV_ERR_TIMEOUT) return GCVO_ERR_TIMEOUT;
+    if (w & DEV_ERR_CAPACITY) return GCVO_ERR_CAPACITY;
+    if (w & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
+    return GCVO_OK;
+}
+
+gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode) {
+    GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->profiling && mode == PAIR_EVAL) {
+        while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+            cudaEvent_t e;
+            GCVO_CUDA(cudaEventCreate(&e));
+            ctx->ev_pool.push_back(e);
+        }
+        e0 = ctx->ev_pool[ctx->ev_used];
+        e1 = ctx->ev_pool[ctx->ev_used + 1];
+        ctx->ev_used += 2;
+        GCVO_CUDA(cudaEventRecord(e0, ctx->stream));
+    }
+    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, b.grid, ctx->stream));
+    if (e1) {
+        GCVO_CUDA(cudaEventRecord(e1, ctx->stream));
+        ctx->pair_launches += 1;
+    }
+    return GCVO_OK;
+}
+
+// Add the device time of the recorded pair-kernel launches (stream must be
+// synchronised) and release the events for reuse.
+gcvo_status collect_profile(gcvo_ctx *ctx) {
+    for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
+        float ms = 0.f;
+        GCVO_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
+        ctx->pair_ms += ms;
+    }
+    ctx->ev_used = 0;
+    return GCVO_OK;
+}
+
+gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gcvo_solver_params *sp,
+                         double *T_out, gcvo_iter_log *logs, int *n_iter, int *status) {
+    if (!sp || !T_out || (sp->order != 1 && sp->order != 2) || sp->k_max < 1 || sp->k_max > GCVO_MAX_KMAX ||
+        !(sp->eps_tol >= 0) || (sp->order == 1 && !(sp->mu0 > 0)))
+        return GCVO_ERR_INVALID_ARG;
+    cudaStream_t s = ctx->stream;
+    Prepared P;
+    GCVO_TRY(prepare(ctx, np, pr, P));
+    GCVO_TRY(ctx->logs.ensure((size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
+    gcvo_iter_log *dlogs = ctx->logs.as<gcvo_iter_log>();
+    GCVO_CUDA(cudaMemsetAsync(dlogs, 0, (size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
+    IterBufs b{};
+    GCVO_TRY(iter_bufs(ctx, P, b, dlogs, sp->k_max));
+    b.fa.eps_tol = sp->eps_tol;
+    b.fa.mu0 = sp->mu0;
+    int *n_active = b.fa.n_active;
+    GCVO_CUDA(cudaMemcpyAsync(n_active, &np, sizeof(int), cudaMemcpyHostToDevice, s));
+    void *hp;
+    GCVO_TRY(host_pinned(ctx, 64, &hp));
+    int *h_active = static_cast<int *>(hp);
+    const int U = 4;
+    int it = 0;
+    while (it < sp->k_max) {
+        for (int u = 0; u < U && it < sp->k_max; ++u, ++it) {
+            if (sp->order == 2) {
+                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
+                b.fa.mode = FIN_GN;
+                GCVO_CUDA(launch_finalize(b.fa, s));
+            } else {
+                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
+                b.fa.mode = FIN_GRAD;
+                GCVO_CUDA(launch_finalize(b.fa, s));
+                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_LINESEARCH));
+                b.fa.mode = FIN_LINESEARCH;
+                GCVO_CUDA(launch_finalize(b.fa, s));
+            }
+        }
+        GCVO_CUDA(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GCVO_CUDA(cudaStreamSynchronize(s));
+        GCVO_TRY(collect_profile(ctx));
+        if (*h_active <= 0) break;
+    }
+    GCVO_TRY(check_status_word(ctx));
+    std::vector<ProbDev> out(np);
+    GCVO_CUDA(cudaMemcpyAsync(out.data(), ctx->probs.ptr, np * sizeof(ProbDev), cudaMemcpyDeviceToHost, s));
+    if (logs)
+        GCVO_CUDA(cudaMemcpyAsync(logs, dlogs, (size_t)np * sp->k_max * sizeof(gcvo_iter_log),
+                                  cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaStreamSynchronize(s));
+    for (int p = 0; p < np; ++p) {
+        const ProbDev &d = out[p];
+        double *T = T_out + 16 * p;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) T[4 * r + c] = d.T[3 * r + c];
+            T[4 * r + 3] = d.T[9 + r];
+        }
+        T[12] = T[13] = T[14] = 0.0;
+        T[15] = 1.0;
+        if (n_iter) n_iter[p] = d.iter;
+        int st;
+        if (d.status == 1) st = GCVO_OK;
+        else if (d.status == 2 || d.status == 0) st = GCVO_ERR_NOT_CONVERGED;
+        else st = -d.status;
+        if (status) status[p] = st;
+    }
+    return GCVO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gcvo_status_string(gcvo_status s) {
+    switch (s) {
+        case GCVO_OK: return "ok";
+        case GCVO_ERR_INVALID_ARG: return "invalid argument";
+        case GCVO_ERR_CUDA: return "CUDA runtime error";
+        case GCVO_ERR_WORKSPACE: return "device memory allocation failed";
+        case GCVO_ERR_SINGULAR: return "singular Gauss-Newton system";
+        case GCVO_ERR_NO_OVERLAP: return "no pair within the kernel cutoff";
+        case GCVO_ERR_NOT_CONVERGED: return "k_max reached before convergence";
+        case GCVO_ERR_NONFINITE: return "non-finite input or result";
+        case GCVO_ERR_TIMEOUT: return "device-side wait timed out";
+        case GCVO_ERR_CAPACITY: return "size limit exceeded";
+    }
+    return "unknown status";
+}
+
+void gcvo_default_kernel_params(gcvo_kernel_params *p) {
+    if (!p) return;
+    p->kernel_mode = 0;
+    p->sigma2 = 1.0;
+    p->cutoff = 3.0;
+    p->iso_ell = 0.1;
+    p->knn = 10;
+    p->eig_max = 0.0;
+    p->eig_ratio = 100.0;
+    p->feat_dim = 1;
+    p->cell_size = 0.0;
+}
+
+void gcvo_default_solver_params(gcvo_solver_params *p) {
+    if (!p) return;
+    p->order = 2;
+    p->k_max = 200;
+    p->eps_tol = 1e-6;
+    p->mu0 = 1e-10;
+}
+
+gcvo_status gcvo_create(gcvo_ctx **ctx, int device, void *cuda_stream) {
+    if (!ctx) return GCVO_ERR_INVALID_ARG;
+    int nd = 0;
+    if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) {
+        cudaGetLastError();
+        return GCVO_ERR_INVALID_ARG;
+    }
+    GCVO_CUDA(cudaSetDevice(device));
+    gcvo_ctx *c = new (std::nothrow) gcvo_ctx();
+    if (!c) return GCVO_ERR_WORKSPACE;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return GCVO_ERR_CUDA;
+    }
+    *ctx = c;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
+    if (!ctx) return GCVO_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf *bufs[] = {&ctx->sort_keys, &ctx->sort_vals, &ctx->sort_tmp, &ctx->scan_tmp, &ctx->small,
+                      &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
+                      &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g,
+                      &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word};
+    for (DevBuf *b : bufs) b->release();
+    for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
+        DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval};
+        for (DevBuf *b : kb) b->release();
+    }
+    ctx->knn_retry.release();
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
+    if (!ctx) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->profiling = enable ? 1 : 0;
+    ctx->ev_used = 0;
+    ctx->pair_launches = 0;
+    ctx->pair_ms = 0.0;
+    ctx->launch_base = launches_so_far();
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_profile_read(gcvo_ctx *ctx, gcvo_profile *out) {
+    if (!ctx || !out) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    GCVO_TRY(collect_profile(ctx));
+    out->n_launches = launches_so_far() - ctx->launch_base;
+    out->n_pair_launches = ctx->pair_launches;
+    out->pair_kernel_ms = ctx->pair_ms;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gcvo_kernel_params *params,
+                                      float *cov_out) {
+    if (!ctx || !xyz || !cov_out || !params) return GCVO_ERR_INVALID_ARG;
+    if (params->knn < 2 || params->knn > GCVO_MAX_KNN || n < params->knn || n > (1 << 28))
+        return GCVO_ERR_INVALID_ARG;
+    if (params->eig_max > 0 && !(params->eig_ratio >= 1.0)) return GCVO_ERR_INVALID_ARG;
+    if (!(params->cutoff > 0)) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    size_t need = staged_floats(xyz, 3 * (size_t)n);
+    bool host_out = !is_device_ptr(cov_out);
+    if (need) GCVO_TRY(ctx->stage_xyz.ensure(need * sizeof(float), ctx->stream));
+    size_t off = 0;
+    const float *dx;
+    GCVO_TRY(stage(ctx, xyz, 3 * (size_t)n, ctx->stage_xyz, off, &dx));
+    float *dcov = cov_out;
+    if (host_out) {
+        GCVO_TRY(ctx->stage_cov.ensure(6 * (size_t)n * sizeof(float), ctx->stream));
+        dcov = ctx->stage_cov.as<float>();
+    }
+    GCVO_TRY(knn_covariances(ctx, dx, n, *params, dcov));
+    if (host_out) {
+        GCVO_CUDA(cudaMemcpyAsync(cov_out, dcov, 6 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return GCVO_OK;
+}
+
+static gcvo_status build_into(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
+                              const gcvo_kernel_params *params, gcvo_grid *g) {
+    if (!ctx || !xyz || !feat || !valid_kernel_params(params)) return GCVO_ERR_INVALID_ARG;
+    if (params->kernel_mode == 0 && !cov) return GCVO_ERR_INVALID_ARG;
+    if (n < 1 || n > (1 << 28)) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    size_t need = staged_floats(xyz, 3 * (size_t)n) + staged_floats(feat, (size_t)params->feat_dim * n) +
+                  (params->kernel_mode == 0 ? staged_floats(cov, 6 * (size_t)n) : 0);
+    if (need) GCVO_TRY(ctx->stage_xyz.ensure(need * sizeof(float), s));
+    size_t off = 0;
+    const float *dx, *dc = nullptr, *df;
+    GCVO_TRY(stage(ctx, xyz, 3 * (size_t)n, ctx->stage_xyz, off, &dx));
+    if (params->kernel_mode == 0) GCVO_TRY(stage(ctx, cov, 6 * (size_t)n, ctx->stage_xyz, off, &dc));
+    GCVO_TRY(stage(ctx, feat, (size_t)params->feat_dim * n, ctx->stage_xyz, off, &df));
+    g->kp = *params;
+    g->device = ctx->device;
+    GCVO_TRY(build_grid_store(ctx, dx, dc, df, n, *params, false, params->cell_size, g->store));
+    GCVO_CUDA(cudaStreamSynchronize(s));
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_build_grid(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
+                            const gcvo_kernel_params *params, gcvo_grid **grid_out) {
+    if (!grid_out) return GCVO_ERR_INVALID_ARG;
+    gcvo_grid *g = new (std::nothrow) gcvo_grid();
+    if (!g) return GCVO_ERR_WORKSPACE;
+    g->device = ctx ? ctx->device : 0;
+    gcvo_status st = build_into(ctx, xyz, cov, feat, n, params, g);
+    if (st != GCVO_OK) {
+        gcvo_grid_destroy(g);
+        return st;
+    }
+    *grid_out = g;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_rebuild_grid(gcvo_ctx *ctx, gcvo_grid *grid, const float *xyz, const float *cov, const float *feat,
+                              int64_t n, const gcvo_kernel_params *params) {
+    if (!grid) return GCVO_ERR_INVALID_ARG;
+    if (ctx && grid->device != ctx->device) return GCVO_ERR_INVALID_ARG;
+    return build_into(ctx, xyz, cov, feat, n, params, grid);
+}
+
+gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
+    if (!grid) return GCVO_ERR_INVALID_ARG;
+    // cudaFree waits for outstanding work on the device, so no stream of a
+    // (possibly destroyed) context is needed here
+    cudaSetDevice(grid->device);
+    GridStore &s = grid->store;
+    s.pos.release();
+    s.ca.release();
+    s.cb.release();
+    s.orig.release();
+    s.cell_start.release();
+    s.hkeys.release();
+    s.hval.release();
+    delete grid;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_grid_info(const gcvo_grid *grid, int64_t *n_points, int64_t *n_cells, double *cell_size) {
+    if (!grid) return GCVO_ERR_INVALID_ARG;
+    if (n_points) *n_points = grid->store.d.n;
+    if (n_cells) *n_cells = grid->store.d.n_cells;
+    if (cell_size) *cell_size = grid->store.d.h;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                      const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
+                      double H[36], double *M_out, gcvo_eval_stats *stats) {
+    if (!ctx || !target || !src_xyz || !src_feat || !T || !f || !g || !H) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    gcvo_problem pr{};
+    pr.target = target;
+    pr.src_xyz = src_xyz;
+    pr.src_cov = src_cov;
+    pr.src_feat = src_feat;
+    pr.n_src = n_src;
+    memcpy(pr.T0, T, 16 * sizeof(double));
+    Prepared P;
+    GCVO_TRY(prepare(ctx, 1, &pr, P));
+    IterBufs b{};
+    GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
+    int one = 1;
+    GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
+    b.fa.mode = FIN_EVAL;
+    GCVO_CUDA(launch_finalize(b.fa, ctx->stream));
+    EvalOut e{};
+    GCVO_CUDA(cudaMemcpyAsync(&e, ctx->evalout.ptr, sizeof(EvalOut), cudaMemcpyDeviceToHost, ctx->stream));
+    GCVO_TRY(check_status_word(ctx));
+    GCVO_TRY(collect_profile(ctx));
+    *f = e.f;
+    memcpy(g, e.g, 6 * sizeof(double));
+    memcpy(H, e.H, 36 * sizeof(double));
+    if (M_out) memcpy(M_out, e.M, 36 * sizeof(double));
+    if (stats) {
+        stats->n_pairs = e.n_pairs;
+        stats->n_kept = e.n_kept;
+        stats->n_candidates = e.n_cand;
+        stats->rho = std::sqrt((double)P.probs[0].rho2);
+    }
+    bool fin = std::isfinite(e.f);
+    for (int k = 0; k < 6; ++k) fin = fin && std::isfinite(e.g[k]);
+    if (!fin) return GCVO_ERR_NONFINITE;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_register(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                          const float *src_feat, int64_t n_src, const double T0[16],
+                          const gcvo_solver_params *params, double T_out[16], gcvo_iter_log *log, int *n_iter) {
+    if (!ctx || !target || !src_xyz || !src_feat || !T0 || !T_out) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    gcvo_problem pr{};
+    pr.target = target;
+    pr.src_xyz = src_xyz;
+    pr.src_cov = src_cov;
+    pr.src_feat = src_feat;
+    pr.n_src = n_src;
+    memcpy(pr.T0, T0, 16 * sizeof(double));
+    int st = 0, ni = 0;
+    double Tt[16];
+    GCVO_TRY(run_register(ctx, 1, &pr, params, Tt, log, &ni, &st));
+    memcpy(T_out, Tt, sizeof(Tt));
+    if (n_iter) *n_iter = ni;
+    return (gcvo_status)st;
+}
+
+gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_problem *problems,
+                                  const gcvo_solver_params *params, double *T_out, gcvo_iter_log *logs,
+                                  int *n_iter, int *status) {
+    if (!ctx || !problems || !T_out || n_problems < 1) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    return run_register(ctx, n_problems, problems, params, T_out, logs, n_iter, status);
+}
+
+}  // extern "C"

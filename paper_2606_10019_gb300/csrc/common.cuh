@@ -1,0 +1,199 @@
+// Internal declarations shared by the translation units of libgcvo.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstddef>
+#include <vector>
+
+#include "gcvo.h"
+
+namespace gcvo {
+
+// ---------------------------------------------------------------------------
+// Error handling: every CUDA call is checked; the first failure is turned into
+// a gcvo_status that the C ABI returns.
+// ---------------------------------------------------------------------------
+#define GCVO_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            gcvo::set_last_cuda_error(e_, #call, __LINE__); \
+            return GCVO_ERR_CUDA;                         \
+        }                                                 \
+    } while (0)
+
+#define GCVO_TRY(expr)                                    \
+    do {                                                  \
+        gcvo_status s_ = (expr);                          \
+        if (s_ != GCVO_OK) return s_;                     \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, int line);
+
+// Process-wide count of kernels launched by the library (profiling).
+void count_launches(long long n);
+long long launches_so_far();
+
+// Device status word bits (set by kernels with atomicOr, read by the host).
+enum : unsigned {
+    DEV_ERR_TIMEOUT = 1u,
+    DEV_ERR_CAPACITY = 2u,
+    DEV_ERR_NONFINITE = 4u,
+};
+
+// ---------------------------------------------------------------------------
+// A device buffer that only grows (released by the owner's destroy call).
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    gcvo_status ensure(size_t need, cudaStream_t s);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ---------------------------------------------------------------------------
+// What the kernels see of a target grid (plain data, passed by value or read
+// from device memory).
+//
+// Points are sorted by voxel key.  pos[i] = (x - o, y - o, z - o, l0) for the
+// target grid (coordinates relative to the grid origin o, float32), and the
+// absolute coordinates for the internal kNN grid; ca[i] = (S00, S01, S02, S11),
+// cb[i] = (S12, S22, l1, l2).  Voxel (cx, cy, cz) holds the points whose
+// coordinates c satisfy floor((c - corner) * inv_h) = (cx, cy, cz); its key is
+// (cx * ny + cy) * nz + cz, so the voxels of one (cx, cy) column with
+// consecutive cz are consecutive in the sorted order.
+// ---------------------------------------------------------------------------
+struct GridDev {
+    const float4 *pos;
+    const float4 *ca;
+    const float4 *cb;
+    const int *orig;          // original index of each sorted point
+    const int *cell_start;    // n_cells + 1 offsets into the sorted points
+    const unsigned long long *hkeys;  // open-addressing table of voxel keys
+    const int *hval;          // voxel index of each table slot
+    unsigned long long hmask; // table size - 1 (power of two)
+    double origin[3];         // o (target grid) or 0 (kNN grid), double
+    float corner[3];          // lowest voxel corner, in the coordinates of pos
+    float h, inv_h;
+    int dims[3];
+    int n, n_cells;
+    float lam_max;            // largest eigenvalue over the stored covariances
+    int feat_dim;
+    int kernel_mode;
+};
+
+static constexpr unsigned long long EMPTY_KEY = ~0ull;
+
+__host__ __device__ inline unsigned long long hash_key(unsigned long long k) {
+    // splitmix64 finaliser
+    k ^= k >> 30;
+    k *= 0xbf58476d1ce4e5b9ull;
+    k ^= k >> 27;
+    k *= 0x94d049bb133111ebull;
+    k ^= k >> 31;
+    return k;
+}
+
+// Voxel index of `key`, or -1 when the voxel holds no point.
+__device__ inline int grid_lookup(const GridDev &g, unsigned long long key) {
+    unsigned long long s = hash_key(key) & g.hmask;
+    for (int probe = 0; probe <= (int)g.hmask; ++probe) {
+        unsigned long long k = __ldg(g.hkeys + s);
+        if (k == key) return __ldg(g.hval + s);
+        if (k == EMPTY_KEY) return -1;
+        s = (s + 1) & g.hmask;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Primitives (prims.cu).
+// ---------------------------------------------------------------------------
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+// Scratch: radix_sort_scratch_bytes(n) bytes.
+size_t radix_sort_scratch_bytes(int64_t n);
+gcvo_status radix_sort_pairs(unsigned long long *keys, int *vals, int64_t n, int bits, void *scratch,
+                             size_t scratch_bytes, cudaStream_t s);
+
+// In-place inclusive scans of int arrays (sum or max).
+size_t scan_scratch_bytes(int64_t n);
+gcvo_status scan_inclusive_sum(int *data, int64_t n, void *scratch, cudaStream_t s);
+gcvo_status scan_inclusive_max(int *data, int64_t n, void *scratch, cudaStream_t s);
+
+// Bounding box of a 3 x n SoA cloud and the largest eigenvalue of a 6 x n
+// SoA covariance array (cov may be null).  out: 8 floats
+// (min xyz, max xyz, lam_max, nonfinite flag).
+gcvo_status bbox_lammax(const float *xyz, const float *cov, int64_t n, float *out_dev, cudaStream_t s);
+
+// Largest eigenvalue of a symmetric 3x3 (closed form, float).
+__host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, float a11, float a12, float a22) {
+    float p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * p1;
+    if (p2 <= 0.0f) return q;
+    float p = sqrtf(p2 * (1.0f / 6.0f));
+    float ip = 1.0f / p;
+    b00 *= ip; b11 *= ip; b22 *= ip;
+    float c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    float detb = b00 * (b11 * b22 - c12 * c12) - c01 * (c01 * b22 - c12 * c02) + c02 * (c01 * c12 - b11 * c02);
+    float r = fminf(fmaxf(0.5f * detb, -1.0f), 1.0f);
+    float phi = acosf(r) * (1.0f / 3.0f);
+    return q + 2.0f * p * cosf(phi);
+}
+
+// ---------------------------------------------------------------------------
+// Grids (grid.cu).
+// ---------------------------------------------------------------------------
+struct GridStore {
+    GridDev d{};
+    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval;
+};
+
+// Build a grid from SoA inputs.  absolute: keep absolute coordinates and no
+// origin shift (kNN grid); otherwise coordinates are relative to the box
+// centre.  cell <= 0 picks cutoff * sqrt(2 lam_max) (or cutoff * iso_ell).
+gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
+                             const gcvo_kernel_params &kp, bool absolute, double cell, GridStore &out);
+
+gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gcvo_kernel_params &kp,
+                            float *cov_out);
+
+}  // namespace gcvo
+
+// ---------------------------------------------------------------------------
+// The opaque handles of the C ABI.
+// ---------------------------------------------------------------------------
+struct gcvo_grid {
+    gcvo::GridStore store;
+    gcvo_kernel_params kp;
+    int device;   // the grid outlives nothing but its own memory: no context pointer
+};
+
+struct gcvo_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // scratch
+    gcvo::DevBuf sort_keys, sort_vals, sort_tmp, scan_tmp, small;
+    gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
+    gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
+    gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g;
+    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word;
+    gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
+    gcvo::DevBuf knn_retry;
+    void *host_pinned = nullptr;
+    size_t host_pinned_bytes = 0;
+    int sm_count = 0;
+    // profiling: CUDA events around pair-kernel launches
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    long long launch_base = 0;
+    long long pair_launches = 0;
+    double pair_ms = 0.0;
+};

@@ -1,0 +1,323 @@
+"""Python binding of libgcvo (include/gcvo.h): argument marshalling only.
+
+Functions keep the C names.  Point arrays are structure-of-arrays float32:
+xyz (3, n), cov (6, n) with (xx, xy, xz, yy, yz, zz), feat (l, n).  They may
+be CUDA tensors (used in place) or host arrays (NumPy or CPU tensors; the
+library copies them).  Poses are 4x4 float64 arrays, row-major.
+
+The CUDA library must have been built (``paper_2606_10019_gb300.build``);
+nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgcvo.so")
+
+GCVO_OK = 0
+GCVO_ERR_INVALID_ARG = 1
+GCVO_ERR_CUDA = 2
+GCVO_ERR_WORKSPACE = 3
+GCVO_ERR_SINGULAR = 4
+GCVO_ERR_NO_OVERLAP = 5
+GCVO_ERR_NOT_CONVERGED = 6
+GCVO_ERR_NONFINITE = 7
+GCVO_ERR_TIMEOUT = 8
+GCVO_ERR_CAPACITY = 9
+
+
+class gcvo_kernel_params(ctypes.Structure):
+    _fields_ = [("kernel_mode", ctypes.c_int), ("sigma2", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("iso_ell", ctypes.c_double), ("knn", ctypes.c_int), ("eig_max", ctypes.c_double),
+                ("eig_ratio", ctypes.c_double), ("feat_dim", ctypes.c_int), ("cell_size", ctypes.c_double)]
+
+
+class gcvo_solver_params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("k_max", ctypes.c_int), ("eps_tol", ctypes.c_double),
+                ("mu0", ctypes.c_double)]
+
+
+class gcvo_iter_log(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("g", ctypes.c_double * 6), ("xi", ctypes.c_double * 6),
+                ("xi_l1", ctypes.c_double), ("T", ctypes.c_double * 16), ("n_pairs", ctypes.c_int64),
+                ("n_kept", ctypes.c_int64)]
+
+
+class gcvo_eval_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_kept", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("rho", ctypes.c_double)]
+
+
+class gcvo_problem(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_void_p), ("src_xyz", ctypes.c_void_p), ("src_cov", ctypes.c_void_p),
+                ("src_feat", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("T0", ctypes.c_double * 16)]
+
+
+class gcvo_profile(ctypes.Structure):
+    _fields_ = [("n_launches", ctypes.c_int64), ("n_pair_launches", ctypes.c_int64),
+                ("pair_kernel_ms", ctypes.c_double)]
+
+
+class GcvoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgcvo.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgcvo.so is missing ({LIB_PATH}); run paper_2606_10019_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.gcvo_status_string.restype = ctypes.c_char_p
+        L.gcvo_status_string.argtypes = [I]
+        L.gcvo_default_kernel_params.argtypes = [P]
+        L.gcvo_default_solver_params.argtypes = [P]
+        L.gcvo_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, P]
+        L.gcvo_destroy.argtypes = [P]
+        L.gcvo_estimate_covariances.argtypes = [P, P, I64, P, P]
+        L.gcvo_build_grid.argtypes = [P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.gcvo_grid_destroy.argtypes = [P]
+        L.gcvo_rebuild_grid.argtypes = [P, P, P, P, P, I64, P]
+        L.gcvo_grid_info.argtypes = [P, P, P, P]
+        L.gcvo_eval.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
+        L.gcvo_register.argtypes = [P, P, P, P, P, I64, P, P, P, P, P]
+        L.gcvo_register_batched.argtypes = [P, I, P, P, P, P, P, P]
+        L.gcvo_profile_enable.argtypes = [P, I]
+        L.gcvo_profile_read.argtypes = [P, P]
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().gcvo_status_string(int(s)).decode()
+
+
+def _check(s: int, where: str, ok=(GCVO_OK,)):
+    if s not in ok:
+        raise GcvoError(s, where)
+    return s
+
+
+def _ptr(a) -> int | None:
+    """Device or host address of a contiguous float32 array (or None)."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("point arrays must be contiguous float32")
+            return a.data_ptr()
+    except ImportError:
+        pass
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise ValueError("point arrays must be contiguous float32")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _n(a) -> int:
+    return int(a.shape[-1])
+
+
+def _pose(T) -> np.ndarray:
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(4, 4))
+    return T
+
+
+def kernel_params(**kw) -> gcvo_kernel_params:
+    p = gcvo_kernel_params()
+    lib().gcvo_default_kernel_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def solver_params(**kw) -> gcvo_solver_params:
+    p = gcvo_solver_params()
+    lib().gcvo_default_solver_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    def __init__(self, handle: int, device: int):
+        self.handle = handle
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().gcvo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grid:
+    def __init__(self, handle: int, ctx: Context, keep):
+        self.handle = handle
+        self.ctx = ctx
+        self._keep = keep
+
+    def info(self):
+        n = ctypes.c_int64()
+        c = ctypes.c_int64()
+        h = ctypes.c_double()
+        _check(lib().gcvo_grid_info(self.handle, ctypes.byref(n), ctypes.byref(c), ctypes.byref(h)), "grid_info")
+        return n.value, c.value, h.value
+
+    def close(self):
+        if self.handle:
+            lib().gcvo_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gcvo_create(device: int = 0, stream=None) -> Context:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (the
+    current torch stream if torch is importable, else the default stream)."""
+    raw = 0
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                raw = torch.cuda.current_stream(device).cuda_stream
+        except ImportError:
+            pass
+    elif isinstance(stream, int):
+        raw = stream
+    else:
+        raw = stream.cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib().gcvo_create(ctypes.byref(h), int(device), ctypes.c_void_p(raw) if raw else None), "gcvo_create")
+    return Context(h.value, device)
+
+
+def gcvo_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def gcvo_estimate_covariances(ctx: Context, xyz, params: gcvo_kernel_params, cov_out) -> None:
+    _check(lib().gcvo_estimate_covariances(ctx.handle, _ptr(xyz), _n(xyz), ctypes.byref(params), _ptr(cov_out)),
+           "gcvo_estimate_covariances")
+
+
+def gcvo_build_grid(ctx: Context, xyz, cov, feat, params: gcvo_kernel_params) -> Grid:
+    h = ctypes.c_void_p()
+    _check(lib().gcvo_build_grid(ctx.handle, _ptr(xyz), _ptr(cov), _ptr(feat), _n(xyz), ctypes.byref(params),
+                                 ctypes.byref(h)), "gcvo_build_grid")
+    return Grid(h.value, ctx, (xyz, cov, feat))
+
+
+def gcvo_rebuild_grid(ctx: Context, grid: Grid, xyz, cov, feat, params: gcvo_kernel_params) -> Grid:
+    _check(lib().gcvo_rebuild_grid(ctx.handle, grid.handle, _ptr(xyz), _ptr(cov), _ptr(feat), _n(xyz),
+                                   ctypes.byref(params)), "gcvo_rebuild_grid")
+    grid._keep = (xyz, cov, feat)
+    return grid
+
+
+@dataclass
+class EvalResult:
+    f: float
+    g: np.ndarray
+    H: np.ndarray
+    M: np.ndarray
+    n_pairs: int
+    n_kept: int
+    n_candidates: int
+    rho: float
+
+
+def gcvo_eval(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T) -> EvalResult:
+    T = _pose(T)
+    f = ctypes.c_double()
+    g = np.zeros(6)
+    H = np.zeros(36)
+    M = np.zeros(36)
+    st = gcvo_eval_stats()
+    _check(lib().gcvo_eval(ctx.handle, grid.handle, _ptr(src_xyz), _ptr(src_cov), _ptr(src_feat), _n(src_xyz),
+                           T.ctypes.data, ctypes.byref(f), g.ctypes.data, H.ctypes.data, M.ctypes.data,
+                           ctypes.byref(st)), "gcvo_eval")
+    return EvalResult(f.value, g, H.reshape(6, 6), M.reshape(6, 6), st.n_pairs, st.n_kept, st.n_candidates, st.rho)
+
+
+def _logs_to_list(logs, n):
+    out = []
+    for k in range(n):
+        L = logs[k]
+        out.append(dict(f=L.f, g=np.array(L.g[:]), xi=np.array(L.xi[:]), xi_l1=L.xi_l1,
+                        T=np.array(L.T[:]).reshape(4, 4), n_pairs=L.n_pairs, n_kept=L.n_kept))
+    return out
+
+
+def gcvo_register(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T0, params: gcvo_solver_params,
+                  want_log: bool = True):
+    """Returns (T, log list, n_iter, status); status is GCVO_OK or
+    GCVO_ERR_NOT_CONVERGED (other statuses raise)."""
+    T0 = _pose(T0)
+    T = np.zeros(16)
+    logs = (gcvo_iter_log * params.k_max)() if want_log else None
+    n_iter = ctypes.c_int()
+    s = lib().gcvo_register(ctx.handle, grid.handle, _ptr(src_xyz), _ptr(src_cov), _ptr(src_feat), _n(src_xyz),
+                            T0.ctypes.data, ctypes.byref(params), T.ctypes.data,
+                            ctypes.cast(logs, ctypes.c_void_p) if logs is not None else None, ctypes.byref(n_iter))
+    _check(s, "gcvo_register", ok=(GCVO_OK, GCVO_ERR_NOT_CONVERGED))
+    return T.reshape(4, 4), (_logs_to_list(logs, n_iter.value) if logs is not None else None), n_iter.value, s
+
+
+def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solver_params, want_log: bool = False):
+    """problems: list of (grid, src_xyz, src_cov, src_feat, T0).  Returns
+    (T (n, 4, 4), logs or None, n_iter (n,), status (n,))."""
+    n = len(problems)
+    arr = (gcvo_problem * n)()
+    for k, (grid, xyz, cov, feat, T0) in enumerate(problems):
+        arr[k].target = grid.handle
+        arr[k].src_xyz = _ptr(xyz)
+        arr[k].src_cov = _ptr(cov)
+        arr[k].src_feat = _ptr(feat)
+        arr[k].n_src = _n(xyz)
+        arr[k].T0[:] = list(_pose(T0).ravel())
+    T = np.zeros((n, 16))
+    n_iter = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    logs = (gcvo_iter_log * (n * params.k_max))() if want_log else None
+    _check(lib().gcvo_register_batched(ctx.handle, n, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(params),
+                                       T.ctypes.data, ctypes.cast(logs, ctypes.c_void_p) if logs is not None else None,
+                                       n_iter.ctypes.data, status.ctypes.data), "gcvo_register_batched")
+    out_logs = None
+    if logs is not None:
+        out_logs = [_logs_to_list(logs[k * params.k_max:(k + 1) * params.k_max], int(n_iter[k])) for k in range(n)]
+    return T.reshape(n, 4, 4), out_logs, n_iter, status
+
+
+def gcvo_profile_enable(ctx: Context, enable: bool = True) -> None:
+    _check(lib().gcvo_profile_enable(ctx.handle, int(bool(enable))), "gcvo_profile_enable")
+
+
+def gcvo_profile_read(ctx: Context) -> dict:
+    p = gcvo_profile()
+    _check(lib().gcvo_profile_read(ctx.handle, ctypes.byref(p)), "gcvo_profile_read")
+    return dict(n_launches=p.n_launches, n_pair_launches=p.n_pair_launches, pair_kernel_ms=p.pair_kernel_ms)

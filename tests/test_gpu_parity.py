@@ -1,0 +1,228 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded
+inputs, through the C ABI.  Tolerances: relative 1e-5 on f, g and H per
+evaluation and 1e-5 rad / 1e-5 m on the final pose (the precision split:
+FP32 pair kernel, FP64 reduction, solve and exp)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import POSE_TOL, TOL, Case, rel_H, rel_f, rel_g, soa
+from paper_2606_10019_gb300 import datagen as D
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    import torch
+    from paper_2606_10019_gb300 import build as B
+    from paper_2606_10019_gb300 import gcvo as G
+    B.build()
+    dev = torch.device("cuda:0")
+    ctx = G.gcvo_create(0)
+    yield oracle_mod, G, ctx, dev
+    ctx.close()
+
+
+def _poses(pair):
+    rng = np.random.default_rng(5)
+    from scipy.spatial.transform import Rotation
+    Tr = D.rigid(Rotation.from_rotvec(rng.normal(size=3) * 0.03).as_matrix(), rng.normal(size=3) * 0.05)
+    return [np.eye(4), pair.T_true, Tr]
+
+
+def _check_eval(O, G, ctx, case, T, tol=TOL):
+    r = G.gcvo_eval(ctx, case.grid, *case.src, T)
+    o = O.evaluate(case.prob, T, case.kp_o)
+    ef, eg, eh = rel_f(r.f, o.f), rel_g(r.g, o.g, o.gabs), rel_H(r.H, o.H)
+    assert ef <= tol and eg <= tol and eh <= tol, (ef, eg, eh, o.n_near_cut)
+    # the kernel examined at least every pair the cutoff keeps
+    assert r.n_kept == pytest.approx(o.n_kept, abs=max(2, 2 * o.n_near_cut))
+    return r, o
+
+
+@pytest.mark.parametrize("n", [2000, 333, 37])
+def test_eval_corner_anisotropic(env, n):
+    """Config-1 scene; sizes with a ragged last group (333, 37 points)."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=n, n_tgt=n)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    for T in _poses(pair):
+        _check_eval(O, G, ctx, case, T)
+
+
+def test_eval_isotropic(env):
+    """Remark 3: Sigma_ij = ell^2 I."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=1500, n_tgt=1200)
+    case = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=3.0), iso=True)
+    case.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08))
+    for T in _poses(pair):
+        _check_eval(O, G, ctx, case, T)
+
+
+def test_eval_rgb_features_and_sigma2(env):
+    """Three feature channels (c_ij = <l_i, l_j>) and sigma^2 != 1."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=800, n_tgt=900, frame=3)
+    rng = np.random.default_rng(1)
+    pair.tgt_feat = rng.uniform(0, 1, size=(900, 3)).astype(np.float32)
+    pair.src_feat = rng.uniform(0, 1, size=(800, 3)).astype(np.float32)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0, sigma2=2.5))
+    case.gpu(G, ctx, dev, G.kernel_params(eig_max=0.01, feat_dim=3, sigma2=2.5))
+    for T in _poses(pair):
+        _check_eval(O, G, ctx, case, T)
+
+
+def test_eval_far_from_origin(env):
+    """The whole scene 300 m from the origin: the grid-origin shift and its
+    exact FP64 change of frame keep g and H in the caller's frame."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=700, n_tgt=700, frame=4)
+    off = np.array([300.0, -120.0, 40.0], np.float32)
+    pair.tgt_xyz = pair.tgt_xyz + off
+    pair.src_xyz = pair.src_xyz + off
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    T = D.rigid(np.eye(3), np.array([0.01, 0.0, -0.02]))
+    _check_eval(O, G, ctx, case, T, tol=3e-5)
+
+
+def test_eval_no_overlap_and_host_inputs(env):
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=300, n_tgt=300)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    far = D.rigid(np.eye(3), np.array([50.0, 0.0, 0.0]))
+    r = G.gcvo_eval(ctx, case.grid, *case.src, far)
+    assert r.f == 0.0 and r.n_kept == 0 and np.all(r.g == 0)
+    # host (NumPy) inputs give the same numbers as device inputs
+    hs = (np.ascontiguousarray(pair.src_xyz.T), np.ascontiguousarray(case.sc.T), np.ascontiguousarray(pair.src_feat.T))
+    a = G.gcvo_eval(ctx, case.grid, *case.src, np.eye(4))
+    b = G.gcvo_eval(ctx, case.grid, *hs, np.eye(4))
+    assert a.f == b.f and np.array_equal(a.g, b.g) and np.array_equal(a.H, b.H)
+
+
+def test_nonfinite_input_is_reported(env):
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=200, n_tgt=200)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    bad = pair.src_xyz.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(G.GcvoError) as e:
+        G.gcvo_eval(ctx, case.grid, soa(bad, dev), case.src[1], case.src[2], np.eye(4))
+    assert e.value.status == G.GCVO_ERR_NONFINITE
+
+
+def test_covariances_match_oracle(env):
+    """Eq. (7b) + eigenvalue clamp on the GPU vs the brute-force oracle,
+    excluding points whose knn-th and (knn+1)-th distances nearly tie."""
+    O, G, ctx, dev = env
+    import torch
+    for pair, eig in ((D.make_corner_pair(n_src=2000, n_tgt=2000), 0.01),
+                      (D.LidarSequence(n_frames=2).pair(0), 0.09)):
+        x = pair.src_xyz
+        cov = torch.zeros((6, len(x)), dtype=torch.float32, device=dev)
+        G.gcvo_estimate_covariances(ctx, soa(x, dev), G.kernel_params(eig_max=eig, eig_ratio=100.0), cov)
+        c_gpu = cov.cpu().numpy().T.astype(np.float64)
+        c_raw, _, kth = O.knn_cov(x, 10)
+        c_orc = O.eig_clamp(c_raw, eig, 100.0)
+        gap = (kth[:, 1] - kth[:, 0]) / np.maximum(kth[:, 1], 1e-30)
+        ok = gap > 1e-5
+        assert ok.mean() > 0.97
+        M = lambda c: np.stack([c[:, [0, 1, 2]], c[:, [1, 3, 4]], c[:, [2, 4, 5]]], 1)
+        err = np.linalg.norm(M(c_gpu) - M(c_orc), axis=(1, 2)) / np.linalg.norm(M(c_orc), axis=(1, 2))
+        assert err[ok].max() <= 2e-5, err[ok].max()
+
+
+def test_register_corner_matches_oracle(env):
+    """Alg. 1 (G-CVO-2) on the config-1 problem from the identity: the oracle
+    evaluated at each GPU iterate T^(k) matches the logged f and g, and the
+    final poses agree within 1e-5 rad / 1e-5 m."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair()
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    T, log, n_iter, st = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4),
+                                         G.solver_params(k_max=100, eps_tol=1e-8))
+    assert st == G.GCVO_OK and 2 <= n_iter < 100
+    for k in sorted({0, 1, n_iter // 2, n_iter - 1}):
+        o = O.evaluate(case.prob, log[k]["T"], case.kp_o)
+        assert rel_f(log[k]["f"], o.f) <= TOL
+        assert rel_g(log[k]["g"], o.g, o.gabs) <= TOL
+    ref = O.register(case.prob, np.eye(4), case.kp_o, order=2, k_max=100, eps_tol=1e-8)
+    ang, dt = O.pose_error(T, ref.T)
+    assert ang <= POSE_TOL and dt <= POSE_TOL, (ang, dt)
+    ang_t, dt_t = O.pose_error(T, pair.T_true)
+    assert ang_t < math.radians(0.5) and dt_t < 0.02
+
+
+def test_register_first_order_matches_oracle(env):
+    """G-CVO-1: gradient step with the line search of Eq. (9).  At every GPU
+    iterate the oracle's f and g agree within 1e-5 and its step within 1e-3
+    (mu is a root of a cubic whose coefficients the kernel sums in FP32);
+    run to convergence, G-CVO-1 stops at the stationary point that the
+    oracle's G-CVO-2 reaches, within 1e-5 rad / 1e-5 m."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=600, n_tgt=600, frame=2)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    sp = G.solver_params(order=1, k_max=12, eps_tol=0.0, mu0=1e-4)
+    T, log, n_iter, st = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), sp)
+    assert n_iter == 12
+    for k in range(12):
+        Tk = log[k]["T"]
+        o = O.evaluate(case.prob, Tk, case.kp_o)
+        assert rel_f(log[k]["f"], o.f) <= TOL
+        assert rel_g(log[k]["g"], o.g, o.gabs) <= TOL
+        c = O.linesearch_poly(case.prob, Tk, o.g, case.kp_o)
+        xi_o = O.linesearch_step(c, 1e-4) * o.g
+        assert np.abs(log[k]["xi"] - xi_o).max() <= 1e-3 * np.abs(xi_o).max()
+    # G-CVO-1 and G-CVO-2 share their fixed points (g = 0): started at the
+    # oracle's G-CVO-2 solution, G-CVO-1 stays there
+    ref = O.register(case.prob, np.eye(4), case.kp_o, order=2, k_max=100, eps_tol=1e-11)
+    sp = G.solver_params(order=1, k_max=20, eps_tol=1e-12, mu0=1e-10)
+    T1, log1, n1, st1 = G.gcvo_register(ctx, case.grid, *case.src, ref.T, sp)
+    ang, dt = O.pose_error(T1, ref.T)
+    assert ang <= POSE_TOL and dt <= POSE_TOL, (ang, dt, n1)
+    # from the identity it is far slower than G-CVO-2 (Sec. 5.4)
+    sp = G.solver_params(order=1, k_max=300, eps_tol=1e-7, mu0=1e-10)
+    _, _, n_first, _ = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), sp)
+    _, _, n_second, _ = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), G.solver_params(eps_tol=1e-7))
+    assert n_first > 2 * n_second
+
+
+def test_batched_equals_single(env):
+    """One launch over several problems gives each problem exactly what it
+    gets alone (per-group partials, fixed-order FP64 sums)."""
+    O, G, ctx, dev = env
+    cases, probs = [], []
+    for fr, n in ((0, 700), (1, 1300), (2, 64), (3, 900)):
+        pair = D.make_corner_pair(n_src=n, n_tgt=n + 50, frame=fr)
+        c = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+        cases.append(c)
+        probs.append((c.grid, *c.src, np.eye(4)))
+    sp = G.solver_params(k_max=60, eps_tol=1e-8)
+    Tb, _, nb, sb = G.gcvo_register_batched(ctx, probs, sp)
+    for k, c in enumerate(cases):
+        Ts, _, ns, ss = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
+        assert ns == nb[k] and ss == sb[k]
+        assert np.array_equal(Ts, Tb[k])
+
+
+@pytest.mark.slow
+def test_register_lidar_frame_pair(env):
+    """Config 2 at full size (one voxelised LiDAR frame pair, ~14k points):
+    GPU vs oracle at sampled iterates and at the final pose."""
+    O, G, ctx, dev = env
+    seq = D.LidarSequence(n_frames=2)
+    pair = seq.pair(0)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0), eig_max=0.09).gpu(G, ctx, dev, G.kernel_params(eig_max=0.09))
+    T, log, n_iter, st = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4),
+                                         G.solver_params(k_max=400, eps_tol=1e-8))
+    assert st == G.GCVO_OK
+    for k in (0, n_iter // 2, n_iter - 1):
+        o = O.evaluate(case.prob, log[k]["T"], case.kp_o)
+        assert rel_f(log[k]["f"], o.f) <= TOL
+        assert rel_g(log[k]["g"], o.g, o.gabs) <= TOL
+    # the oracle continued from the GPU's answer stays put
+    ref = O.register(case.prob, T, case.kp_o, order=2, k_max=5, eps_tol=1e-7)
+    ang, dt = O.pose_error(T, ref.T)
+    assert ang <= POSE_TOL and dt <= POSE_TOL

@@ -484,9 +484,27 @@ def test_second_order_needs_fewer_iterations(oracle_mod):
     prob = O.Problem.make(tgt, None, pair.tgt_feat, D.apply(G, tgt), None, pair.tgt_feat)
     kp = O.KernelParams(kernel_mode=1, cutoff=0.0, iso_ell=0.2)
     o2 = O.register(prob, np.eye(4), kp, order=2, eps_tol=1e-7, k_max=200)
-    o1 = O.register(prob, np.eye(4), kp, order=1, eps_tol=1e-7, k_max=200, mu0=1e-4)
+    o1 = O.register(prob, np.eye(4), kp, order=1, eps_tol=1e-7, k_max=200, mu0=1e-10)
     e2 = O.pose_error(o2.T, G)
     e1 = O.pose_error(o1.T, G)
     assert o2.converged and len(o2.log) < 50
     assert len(o1.log) > 3 * len(o2.log)
     assert sum(e2) < 1e-6 and sum(e1) < 1e-5
+
+
+def test_first_order_minimum_step_must_be_small(oracle_mod):
+    """Eq. (9) takes mu = max(mu0, t*).  At a fixed point t* ~ 1/lambda of the
+    curvature along g, so a minimum step mu0 above about 2/lambda forces an
+    overshoot that grows every iteration; a small mu0 keeps G-CVO-1 at the
+    fixed point it shares with G-CVO-2 (g = 0)."""
+    O = oracle_mod
+    pair = D.make_corner_pair(n_src=300, n_tgt=300, frame=2)
+    tc = O.covariances(pair.tgt_xyz, 10, 0.01, 100.0)
+    sc = O.covariances(pair.src_xyz, 10, 0.01, 100.0)
+    prob = O.Problem.make(pair.tgt_xyz, tc, pair.tgt_feat, pair.src_xyz, sc, pair.src_feat)
+    kp = O.KernelParams(cutoff=3.0)
+    ref = O.register(prob, np.eye(4), kp, order=2, k_max=100, eps_tol=1e-11)
+    stay = O.register(prob, ref.T, kp, order=1, k_max=20, eps_tol=0.0, mu0=1e-10)
+    assert sum(O.pose_error(stay.T, ref.T)) < 1e-9
+    leave = O.register(prob, ref.T, kp, order=1, k_max=20, eps_tol=0.0, mu0=1e-4)
+    assert sum(O.pose_error(leave.T, ref.T)) > 1e-3
