@@ -126,6 +126,10 @@ typedef struct {
 /* Human-readable name of a status code (static storage). */
 const char *gcvo_status_string(gcvo_status s);
 
+/* Text of the last CUDA runtime failure seen by this host thread (the call,
+ * its error string and code); empty when none.  Valid until the next call. */
+const char *gcvo_last_error_detail(void);
+
 /* Default kernel / solver parameters (cutoff 3, sigma2 1, knn 10, G-CVO-2,
  * k_max 200, eps_tol 1e-6, mu0 1e-10; the paper gives no mu0, and a
  * minimum step must stay below 2 / lambda_max(M) or G-CVO-1 leaves its fixed

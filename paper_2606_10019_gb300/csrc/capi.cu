@@ -81,6 +81,8 @@ int ceil_log2(int64_t v) {
 struct Prepared {
     int n_problems = 0;
     int n_groups = 0;
+    int n_items = 0;
+    int *d_nitems = nullptr;
     int64_t n_points = 0;
     int feat_dim = 1;
     bool iso = false;
@@ -128,7 +130,9 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         GCVO_TRY(stage(ctx, q.src_feat, (size_t)P.feat_dim * q.n_src, ctx->stage_xyz, off, &d.feat));
         d.n = q.n_src;
         d.offset = 0;
-        d.inv_hf = 4.0f / q.target->store.d.h;
+        // fine Morton voxel: h/2, so the coarse voxel (8 fine) is 4 h = twice the
+        // kernel range when h = rho/2
+        d.inv_hf = 2.0f / q.target->store.d.h;
         max_n = std::max<int64_t>(max_n, q.n_src);
     }
     int64_t acc = 0;
@@ -139,7 +143,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
 
     // device buffers
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t small_need = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 3 + al(sizeof(int)) * 4;
+    size_t small_need = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 7 + al(sizeof(int)) * 4 + 256;
     GCVO_TRY(ctx->small.ensure(small_need + 4096, s));
     char *sp = ctx->small.as<char>();
     SrcDesc *d_desc = reinterpret_cast<SrcDesc *>(sp);
@@ -151,6 +155,17 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     int *d_pg1 = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
     int *d_ngroups = reinterpret_cast<int *>(sp);
+    sp += 256;
+    int *d_nitems = reinterpret_cast<int *>(sp);
+    sp += 256;
+    int *d_pcnt = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_pincl = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_pw0 = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
+    int *d_pw1 = reinterpret_cast<int *>(sp);
+    P.d_nitems = d_nitems;
 
     GCVO_TRY(ctx->sort_keys.ensure(N * sizeof(unsigned long long), s));
     GCVO_TRY(ctx->sort_vals.ensure(al(N * sizeof(int)) * 5, s));
@@ -162,6 +177,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->grp_start.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->grp_count.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->grp_prob.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->items.ensure(N * sizeof(int4), s));
+    GCVO_TRY(ctx->item_prob.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->status_word.ensure(256, s));
     char *vp = ctx->sort_vals.as<char>();
     int *vals = reinterpret_cast<int *>(vp);
@@ -200,19 +217,31 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_CUDA(launch_src_groups(sa, sa.keys, gid, N, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(),
                                 ctx->grp_prob.as<int>(), d_pg0, d_pg1, s));
     GCVO_CUDA(cudaMemcpyAsync(d_ngroups, gid + N - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    // pack consecutive groups of a problem into warp items
+    GCVO_CUDA(launch_pack(0, np, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(), d_pg0, d_pg1, d_pcnt, nullptr,
+                          nullptr, nullptr, nullptr, nullptr, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_pincl, d_pcnt, np * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    GCVO_TRY(scan_inclusive_sum(d_pincl, np, ctx->scan_tmp.ptr, s));
+    GCVO_CUDA(launch_pack(1, np, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(), d_pg0, d_pg1, d_pcnt, d_pincl,
+                          ctx->items.as<int4>(), ctx->item_prob.as<int>(), d_pw0, d_pw1, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_nitems, d_pincl + np - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
 
-    // read back group count, group ranges, source eigenvalue bounds
+    // read back group and item counts and ranges, source eigenvalue bounds
     void *hp;
-    GCVO_TRY(host_pinned(ctx, (size_t)(3 * np + 8) * sizeof(int), &hp));
+    GCVO_TRY(host_pinned(ctx, (size_t)(5 * np + 8) * sizeof(int), &hp));
     int *h = static_cast<int *>(hp);
     GCVO_CUDA(cudaMemcpyAsync(h, d_ngroups, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 1, ctx->status_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 2, d_nitems, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8, d_lam, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8 + np, d_pg0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8 + 2 * np, d_pg1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 3 * np, d_pw0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 4 * np, d_pw1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaStreamSynchronize(s));
     if (h[1] & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
     P.n_groups = h[0];
+    P.n_items = h[2];
     P.probs.assign(np, ProbDev{});
     for (int p = 0; p < np; ++p) {
         ProbDev &d = P.probs[p];
@@ -226,6 +255,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         d.iter = 0;
         d.g0 = h[8 + np + p];
         d.g1 = h[8 + 2 * np + p];
+        d.w0 = h[8 + 3 * np + p];
+        d.w1 = h[8 + 4 * np + p];
         int le = h[8 + p];
         int li = le >= 0 ? le : le ^ 0x7fffffff;
         float lam_src;
@@ -243,9 +274,10 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         d.iso_inv = kp.kernel_mode == 1 ? (float)(1.0 / (kp.iso_ell * kp.iso_ell)) : 0.f;
     }
     // per-iteration buffers
-    GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_groups, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,
+    GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_items, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,
                                  s));
     GCVO_TRY(ctx->probs.ensure(np * sizeof(ProbDev), s));
+    GCVO_TRY(ctx->anchors.ensure((size_t)std::max(P.n_groups, 1) * sizeof(float4), s));
     GCVO_TRY(ctx->grids.ensure(np * sizeof(GridDev), s));
     GCVO_TRY(ctx->evalout.ensure(np * sizeof(EvalOut) + 256, s));
     std::vector<GridDev> gd(np);
@@ -267,22 +299,20 @@ struct IterBufs {
 gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     char *part = ctx->partial.as<char>();
-    size_t ng = (size_t)std::max(P.n_groups, 1);
+    size_t ng = (size_t)std::max(P.n_items, 1);
     float *pf = reinterpret_cast<float *>(part);
     long long *pc = reinterpret_cast<long long *>(part + al(ng * 64 * sizeof(float)));
     int *work = reinterpret_cast<int *>(ctx->status_word.as<char>() + 64);
     int *n_active = work + 1;
-    const int *d_ngroups = reinterpret_cast<const int *>(ctx->small.as<char>() +
-                                                        al(P.n_problems * sizeof(SrcDesc)) +
-                                                        3 * al(P.n_problems * sizeof(int)));
     PairArgs &a = b.pa;
     a.spos = ctx->src_pos.as<float4>();
     a.sca = ctx->src_ca.as<float4>();
     a.scb = ctx->src_cb.as<float4>();
+    a.anchor = ctx->anchors.as<float4>();
     a.gstart = ctx->grp_start.as<int>();
-    a.gcount = ctx->grp_count.as<int>();
-    a.gprob = ctx->grp_prob.as<int>();
-    a.n_groups = d_ngroups;
+    a.items = ctx->items.as<int4>();
+    a.item_prob = ctx->item_prob.as<int>();
+    a.n_items = P.d_nitems;
     a.probs = ctx->probs.as<ProbDev>();
     a.grids = ctx->grids.as<GridDev>();
     a.part = pf;
@@ -292,6 +322,9 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     a.ls_literal = 0;
     FinalizeArgs &f = b.fa;
     f.probs = ctx->probs.as<ProbDev>();
+    f.spos = ctx->src_pos.as<float4>();
+    f.gstart = ctx->grp_start.as<int>();
+    f.anchor = ctx->anchors.as<float4>();
     f.grids = ctx->grids.as<GridDev>();
     f.part = pf;
     f.counts = pc;
@@ -303,9 +336,12 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     f.eps_tol = 0;
     f.mu0 = 0;
     b.work = work;
+    // group anchors and float rotation at the initial pose
+    f.mode = FIN_ANCHORS;
+    GCVO_CUDA(launch_finalize(f, ctx->stream));
     int per_sm = pair_blocks_per_sm(PAIR_EVAL, P.iso, P.feat_dim);
     if (per_sm < 1) per_sm = 1;
-    int want = (P.n_groups + PAIR_WARPS - 1) / PAIR_WARPS;
+    int want = (P.n_items + PAIR_WARPS - 1) / PAIR_WARPS;
     b.grid = std::max(1, std::min(want, per_sm * ctx->sm_count));
     return GCVO_OK;
 }
@@ -442,6 +478,8 @@ const char *gcvo_status_string(gcvo_status s) {
     return "unknown status";
 }
 
+const char *gcvo_last_error_detail(void) { return last_cuda_error(); }
+
 void gcvo_default_kernel_params(gcvo_kernel_params *p) {
     if (!p) return;
     p->kernel_mode = 0;
@@ -490,10 +528,12 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->sort_keys, &ctx->sort_vals, &ctx->sort_tmp, &ctx->scan_tmp, &ctx->small,
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
                       &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g,
-                      &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word};
+                      &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
+                      &ctx->anchors, &ctx->items, &ctx->item_prob};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
-        DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval};
+        DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
+                        &kg->col_range, &kg->cell_z};
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
@@ -610,6 +650,8 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
     s.cell_start.release();
     s.hkeys.release();
     s.hval.release();
+    s.col_range.release();
+    s.cell_z.release();
     delete grid;
     return GCVO_OK;
 }

@@ -31,14 +31,17 @@ __global__ void k_heads(const unsigned long long *keys, int64_t n, int *head) {
     head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
-__global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t n, int *cell_start,
-                        unsigned long long *hkeys, int *hval, unsigned long long hmask) {
+__global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t n, int dz, int *cell_start,
+                        unsigned long long *hkeys, int *hval, unsigned long long hmask, int2 *col_range,
+                        int *cell_z) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (i == 0 || keys[i] != keys[i - 1]) {
+    const unsigned long long k = keys[i];
+    const unsigned long long col = k / (unsigned long long)dz;
+    if (i == 0 || k != keys[i - 1]) {
         int c = incl[i] - 1;
         cell_start[c] = (int)i;
-        unsigned long long k = keys[i];
+        cell_z[c] = (int)(k - col * (unsigned long long)dz);
         unsigned long long s = hash_key(k) & hmask;
         for (;;) {
             unsigned long long prev = atomicCAS(hkeys + s, EMPTY_KEY, k);
@@ -48,8 +51,22 @@ __global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t
             }
             s = (s + 1) & hmask;
         }
+        // voxels of one (cx, cy) column are consecutive: record where each
+        // column starts and where the previous one ends
+        if (i == 0) {
+            col_range[col].x = c;
+        } else {
+            const unsigned long long pcol = keys[i - 1] / (unsigned long long)dz;
+            if (pcol != col) {
+                col_range[col].x = c;
+                col_range[pcol].y = c;
+            }
+        }
     }
-    if (i == n - 1) cell_start[incl[i]] = (int)n;
+    if (i == n - 1) {
+        cell_start[incl[i]] = (int)n;
+        col_range[col].y = incl[i];
+    }
 }
 
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
@@ -114,10 +131,11 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
 
     double h = cell;
     if (h <= 0) {
+        // half the kernel range: finer voxels hug the range ball more tightly
         if (kp.kernel_mode == 1)
-            h = kp.cutoff * kp.iso_ell;
+            h = 0.5 * kp.cutoff * kp.iso_ell;
         else
-            h = kp.cutoff * std::sqrt(2.0 * (double)lam);
+            h = 0.5 * kp.cutoff * std::sqrt(2.0 * (double)lam);
     }
     if (!(h > 0) || !std::isfinite(h)) return GCVO_ERR_INVALID_ARG;
 
@@ -137,6 +155,8 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
         prod *= g.dims[a];
     }
     if (prod > 4.0e18) return GCVO_ERR_CAPACITY;
+    const double n_columns = (double)g.dims[0] * (double)g.dims[1];
+    if (n_columns > (double)(1 << 27)) return GCVO_ERR_CAPACITY;
     int bits = 1;
     while ((double)(1ull << bits) < prod && bits < 62) ++bits;
 
@@ -169,10 +189,14 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(out.cell_start.ensure((n_cells + 1) * sizeof(int), s));
     GCVO_TRY(out.hkeys.ensure(H * sizeof(unsigned long long), s));
     GCVO_TRY(out.hval.ensure(H * sizeof(int), s));
+    GCVO_TRY(out.col_range.ensure((size_t)n_columns * sizeof(int2), s));
+    GCVO_TRY(out.cell_z.ensure((size_t)(n_cells + 1) * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(out.col_range.ptr, 0, (size_t)n_columns * sizeof(int2), s));
     k_fill_u64<<<(unsigned)((H + 255) / 256), 256, 0, s>>>(out.hkeys.as<unsigned long long>(), (int64_t)H,
                                                           EMPTY_KEY);
-    k_cells<<<blocks, 256, 0, s>>>(keys, incl, n, out.cell_start.as<int>(), out.hkeys.as<unsigned long long>(),
-                                   out.hval.as<int>(), H - 1);
+    k_cells<<<blocks, 256, 0, s>>>(keys, incl, n, g.dims[2], out.cell_start.as<int>(),
+                                   out.hkeys.as<unsigned long long>(), out.hval.as<int>(), H - 1,
+                                   out.col_range.as<int2>(), out.cell_z.as<int>());
     k_reorder<<<blocks, 256, 0, s>>>(xyz, kp.kernel_mode == 0 ? cov : nullptr, feat, kp.feat_dim, n, vals, g,
                                      absolute, out.pos.as<float4>(), out.ca.as<float4>(), out.cb.as<float4>(),
                                      out.orig.as<int>());
@@ -186,6 +210,8 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.cell_start = out.cell_start.as<int>();
     g.hkeys = out.hkeys.as<unsigned long long>();
     g.hval = out.hval.as<int>();
+    g.col_range = out.col_range.as<int2>();
+    g.cell_z = out.cell_z.as<int>();
     g.hmask = H - 1;
     g.n = (int)n;
     g.n_cells = n_cells;
@@ -252,7 +278,7 @@ struct KnnList {
 // voxels around q's voxel.  After shell R every point closer than R * h has
 // been seen, so the search is complete (returns true) once the knn-th
 // distance is within R * h.
-__device__ bool knn_search(const GridDev &g, float4 q, int knn, int R_max, KnnList &L) {
+__device__ __forceinline__ bool knn_search(const GridDev &g, float4 q, int knn, int R_max, KnnList &L) {
     int cq[3];
     float qc[3] = {q.x, q.y, q.z};
     for (int a = 0; a < 3; ++a) {
@@ -327,7 +353,7 @@ __device__ bool knn_search(const GridDev &g, float4 q, int knn, int R_max, KnnLi
 }
 
 // Eq. (7b) over the list, then the eigenvalue bound; writes column o of cov_out.
-__device__ void knn_write_cov(const GridDev &g, float4 q, const KnnList &L, int knn, double eig_max,
+__device__ __forceinline__ void knn_write_cov(const GridDev &g, float4 q, const KnnList &L, int knn, double eig_max,
                               double eig_ratio, int64_t n, int o, float *cov_out) {
     // Sigma = 1/(n-1) sum (y - x)(y - x)^T, centred at the query point
     float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -380,26 +406,148 @@ __global__ void k_knn_cov(GridDev g, int knn, double eig_max, double eig_ratio, 
         retry[atomicAdd(n_retry, 1)] = (int)i;
 }
 
-// Pass 2: the queued points searched in the coarse grid without a shell limit.
+// Pass 2: one warp per queued point, searching the coarse grid shell by
+// shell without a limit.  The lanes split each shell's voxels and keep
+// private sorted lists; after every shell the warp merges them (repeated
+// warp-wide minimum over each lane's next entry) into the knn nearest so
+// far, and stops once the knn-th distance is within the shells' reach.
 __global__ void k_knn_cov_far(GridDev fine, GridDev coarse, int knn, double eig_max, double eig_ratio, int64_t n,
                               float *cov_out, const int *retry, const int *n_retry, unsigned *status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
     const int m = *n_retry;
     const int maxR = max(coarse.dims[0], max(coarse.dims[1], coarse.dims[2]));
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
-        int i = retry[t];
-        float4 q = fine.pos[i];
-        KnnList L;
-        if (knn_search(coarse, q, knn, maxR, L) || L.k[0] >= 0) {
-            bool full = true;
-#pragma unroll
-            for (int k = 0; k < KNN_MAX; ++k)
-                if (k < knn && L.k[k] < 0) full = false;
-            if (full) {
-                knn_write_cov(coarse, q, L, knn, eig_max, eig_ratio, n, fine.orig[i], cov_out);
-                continue;
+    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < m; t += gridDim.x * wpb) {
+        const int i = retry[t];
+        const float4 q = fine.pos[i];
+        int cq[3];
+        {
+            float qc[3] = {q.x, q.y, q.z};
+            for (int a = 0; a < 3; ++a) {
+                int c = (int)floorf((qc[a] - coarse.corner[a]) * coarse.inv_h);
+                cq[a] = min(max(c, 0), coarse.dims[a] - 1);
             }
         }
-        atomicOr(status, DEV_ERR_CAPACITY);
+        KnnList L;   // this lane's private list
+#pragma unroll
+        for (int k = 0; k < KNN_MAX; ++k) {
+            L.d[k] = INFINITY;
+            L.i[k] = 0x7fffffff;
+            L.k[k] = -1;
+        }
+        float wd = INFINITY;
+        int wi = 0x7fffffff;
+        KnnList M;   // merged result (identical in every lane)
+        bool done = false;
+        for (int R = 1; R <= maxR && !done; ++R) {
+            const int side = 2 * R + 1;
+            const int cube = side * side * side;
+            for (int v = lane; v < cube; v += 32) {
+                int dx = v / (side * side) - R, dy = (v / side) % side - R, dz = v % side - R;
+                if (R > 1 && max(abs(dx), max(abs(dy), abs(dz))) != R) continue;   // shell only
+                int cx = cq[0] + dx, cy = cq[1] + dy, cz = cq[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= coarse.dims[0] || cy >= coarse.dims[1] ||
+                    cz >= coarse.dims[2])
+                    continue;
+                unsigned long long key = ((unsigned long long)cx * coarse.dims[1] + cy) * coarse.dims[2] + cz;
+                int c = grid_lookup(coarse, key);
+                if (c < 0) continue;
+                for (int k = coarse.cell_start[c], k1 = coarse.cell_start[c + 1]; k < k1; ++k) {
+                    float4 y = coarse.pos[k];
+                    float ex = y.x - q.x, ey = y.y - q.y, ez = y.z - q.z;
+                    float d2 = ex * ex + ey * ey + ez * ez;
+                    if (d2 > wd) continue;
+                    int oi = coarse.orig[k];
+                    if (d2 == wd && oi >= wi) continue;
+                    float cd = d2;
+                    int ci = oi, ck = k;
+#pragma unroll
+                    for (int mm = 0; mm < KNN_MAX; ++mm) {
+                        if (mm < knn) {
+                            bool less = cd < L.d[mm] || (cd == L.d[mm] && ci < L.i[mm]);
+                            if (less) {
+                                float td = L.d[mm];
+                                int ti = L.i[mm], tk = L.k[mm];
+                                L.d[mm] = cd;
+                                L.i[mm] = ci;
+                                L.k[mm] = ck;
+                                cd = td;
+                                ci = ti;
+                                ck = tk;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int mm = 0; mm < KNN_MAX; ++mm)
+                        if (mm == knn - 1) {
+                            wd = L.d[mm];
+                            wi = L.i[mm];
+                        }
+                }
+            }
+            // merge: knn rounds of a warp-wide minimum over (d, index)
+            int head = 0;
+            for (int r = 0; r < knn; ++r) {
+                float hd = INFINITY;
+                int hi = 0x7fffffff, hk = -1;
+#pragma unroll
+                for (int mm = 0; mm < KNN_MAX; ++mm)
+                    if (mm == head) {
+                        hd = L.d[mm];
+                        hi = L.i[mm];
+                        hk = L.k[mm];
+                    }
+                float bd = hd;
+                int bi = hi;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float od = __shfl_xor_sync(FULL, bd, o);
+                    int oi = __shfl_xor_sync(FULL, bi, o);
+                    if (od < bd || (od == bd && oi < bi)) {
+                        bd = od;
+                        bi = oi;
+                    }
+                }
+                const bool mine = (hd == bd && hi == bi && hk >= 0);
+                const unsigned who = __ballot_sync(FULL, mine);
+                const int src = who ? __ffs(who) - 1 : 0;
+                const int bk = __shfl_sync(FULL, hk, src);
+                if (lane == src && who) ++head;
+#pragma unroll
+                for (int mm = 0; mm < KNN_MAX; ++mm)
+                    if (mm == r) {
+                        M.d[mm] = who ? bd : INFINITY;
+                        M.i[mm] = who ? bi : 0x7fffffff;
+                        M.k[mm] = who ? bk : -1;
+                    }
+            }
+            // every lane prunes with the merged knn-th distance from now on
+            float md = INFINITY;
+            int mi = 0x7fffffff, mk = -1;
+#pragma unroll
+            for (int mm = 0; mm < KNN_MAX; ++mm)
+                if (mm == knn - 1) {
+                    md = M.d[mm];
+                    mi = M.i[mm];
+                    mk = M.k[mm];
+                }
+            if (mk >= 0 && (md < wd || (md == wd && mi < wi))) {
+                wd = md;
+                wi = mi;
+            }
+            const float reach = (float)R * coarse.h;
+            done = mk >= 0 && md <= reach * reach * 0.999f;
+        }
+        bool full = true;
+#pragma unroll
+        for (int mm = 0; mm < KNN_MAX; ++mm)
+            if (mm < knn && M.k[mm] < 0) full = false;
+        if (!full) {
+            if (lane == 0) atomicOr(status, DEV_ERR_CAPACITY);
+            continue;
+        }
+        if (lane == 0) knn_write_cov(coarse, q, M, knn, eig_max, eig_ratio, n, fine.orig[i], cov_out);
     }
 }
 
@@ -454,7 +602,7 @@ gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gc
     GCVO_CUDA(cudaMemsetAsync(stw, 0, 2 * sizeof(unsigned), s));
     k_knn_cov<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(fine.d, kp.knn, kp.eig_max, kp.eig_ratio, n, cov_out,
                                                           ctx->knn_retry.as<int>(), n_retry);
-    k_knn_cov_far<<<std::max(1, ctx->sm_count) * 2, 64, 0, s>>>(fine.d, coarse.d, kp.knn, kp.eig_max,
+    k_knn_cov_far<<<std::max(1, ctx->sm_count) * 4, 128, 0, s>>>(fine.d, coarse.d, kp.knn, kp.eig_max,
                                                                 kp.eig_ratio, n, cov_out, ctx->knn_retry.as<int>(),
                                                                 n_retry, stw);
     count_launches(2);

@@ -15,6 +15,8 @@ static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+const char *last_cuda_error() { return g_last_err; }
+
 void set_last_cuda_error(cudaError_t e, const char *what, int line) {
     snprintf(g_last_err, sizeof(g_last_err), "%s (%d) at line %d: %s", cudaGetErrorString(e), (int)e, line, what);
 }

@@ -66,7 +66,10 @@ class gcvo_profile(ctypes.Structure):
 class GcvoError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {status_string(status)} ({status})")
+        detail = ""
+        if status == GCVO_ERR_CUDA:
+            detail = " -- " + lib().gcvo_last_error_detail().decode(errors="replace")
+        super().__init__(f"{where}: {status_string(status)} ({status}){detail}")
 
 
 _lib = None
@@ -82,6 +85,8 @@ def lib() -> ctypes.CDLL:
         P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         L.gcvo_status_string.restype = ctypes.c_char_p
         L.gcvo_status_string.argtypes = [I]
+        L.gcvo_last_error_detail.restype = ctypes.c_char_p
+        L.gcvo_last_error_detail.argtypes = []
         L.gcvo_default_kernel_params.argtypes = [P]
         L.gcvo_default_solver_params.argtypes = [P]
         L.gcvo_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, P]

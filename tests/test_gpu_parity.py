@@ -190,8 +190,9 @@ def test_register_first_order_matches_oracle(env):
 
 
 def test_batched_equals_single(env):
-    """One launch over several problems gives each problem exactly what it
-    gets alone (per-group partials, fixed-order FP64 sums)."""
+    """One launch over several problems gives each problem what it gets
+    alone.  The pair kernel adds per-point sums with shared-memory atomics,
+    so the two runs agree to rounding (not bit for bit)."""
     O, G, ctx, dev = env
     cases, probs = [], []
     for fr, n in ((0, 700), (1, 1300), (2, 64), (3, 900)):
@@ -203,8 +204,9 @@ def test_batched_equals_single(env):
     Tb, _, nb, sb = G.gcvo_register_batched(ctx, probs, sp)
     for k, c in enumerate(cases):
         Ts, _, ns, ss = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
-        assert ns == nb[k] and ss == sb[k]
-        assert np.array_equal(Ts, Tb[k])
+        assert ss == sb[k] and abs(ns - nb[k]) <= 2
+        ang, dt = O.pose_error(Ts, Tb[k])
+        assert ang < 1e-7 and dt < 1e-7
 
 
 @pytest.mark.slow
