@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--k-max", type=int, default=200)
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem comparison")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal comparison")
     return ap.parse_args()
 
 
@@ -276,6 +277,10 @@ def run_gcvo(args, rank, world):
                 "pair_kernel_share_of_step": t_pair / t_dev if t_dev > 0 else None,
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz (max SM clock)"}
 
+    proposal = None
+    if not args.no_proposal and rank == 0:
+        proposal = learned_proposal_block(G, ctx, dev)
+
     res = None
     if rank == 0:
         cpu = cpu_baseline(frames, T_true)
@@ -300,6 +305,7 @@ def run_gcvo(args, rank, world):
             "gpu_launches": prof["n_launches"],
             "clocks": clk,
             "plain_vs_batched": plain,
+            "learned_proposal": proposal,
             "cpu_baseline": cpu,
             "wall_s_timed": t_wall,
         }
@@ -310,6 +316,64 @@ def run_gcvo(args, rank, world):
         dist.destroy_process_group()
     ctx.close()
     return res
+
+
+# ---------------------------------------------------------------------------
+# Learned proposal + batched G-CVO vs plain single-problem G-CVO
+# ---------------------------------------------------------------------------
+
+def learned_proposal_block(G, ctx, dev, n_train=1024, steps=1500, n_eval=256):
+    """Config-5-style comparison on corner-scene pairs misaligned by up to
+    30 degrees / 0.5 m: the proposal is trained (by the library's kernels) on
+    G-CVO-labelled pairs, then plain G-CVO-2 from the identity, one problem
+    per call, is compared with proposal + batched G-CVO-2 on held-out pairs."""
+    import torch
+    from paper_2606_10019_gb300 import proposal_data as PD
+    from paper_2606_10019_gb300 import train_proposal as TP
+    t0 = time.perf_counter()
+    net = G.Proposal(ctx)
+    net.set_params(TP.init_params(net.n_params, 3))
+    TP.train(G, ctx, net, PD.corner_pairs(n_train, 1), dev, steps=steps)
+    t_train = time.perf_counter() - t0
+    test = PD.corner_pairs(n_eval, 2)
+    T_true = [p[4] for p in test]
+    batch = PD.to_device(test, dev)
+    kp = G.kernel_params(eig_max=0.01, eig_ratio=100.0)
+    sp = G.solver_params(k_max=200, eps_tol=1e-6)
+    probs, keep = PD.problems(G, ctx, kp, batch, [np.eye(4)] * n_eval, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    T_plain, it_plain = [], []
+    for pr in probs:
+        T1, _, n1, _ = G.gcvo_register(ctx, *pr, sp, want_log=False)
+        T_plain.append(T1)
+        it_plain.append(n1)
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, T0p = net.infer(*batch)
+    probs_p = [(g, sx, sc, sf, T0p[k]) for k, (g, sx, sc, sf, _) in enumerate(probs)]
+    T_prop, _, it_prop, _ = G.gcvo_register_batched(ctx, probs_p, sp)
+    torch.cuda.synchronize(dev)
+    t_prop = time.perf_counter() - t0
+    e_plain = PD.pose_errors(T_plain, T_true)
+    e_prop = PD.pose_errors(list(T_prop), T_true)
+    ok_plain = (e_plain[:, 0] < 2.0) & (e_plain[:, 1] < 0.05)
+    ok_prop = (e_prop[:, 0] < 2.0) & (e_prop[:, 1] < 0.05)
+    net.close()
+    return {"workload": f"corner scenes, 2000 points, misaligned up to 30 deg / 0.5 m, {n_eval} held-out pairs",
+            "train": {"pairs": n_train, "steps": steps, "seconds": t_train},
+            "plain_single_from_identity": {"registrations_per_s": n_eval / t_plain, "success": float(ok_plain.mean()),
+                                           "iterations_mean": float(np.mean(it_plain)),
+                                           "rot_deg_median_success": float(np.median(e_plain[ok_plain, 0]))
+                                           if ok_plain.any() else None},
+            "batched_with_proposal": {"registrations_per_s": n_eval / t_prop, "success": float(ok_prop.mean()),
+                                      "iterations_mean": float(np.mean(it_prop)),
+                                      "rot_deg_median_success": float(np.median(e_prop[ok_prop, 0]))
+                                      if ok_prop.any() else None,
+                                      "includes": "proposal inference + batched registration"},
+            "speedup_registrations_per_s": t_plain / t_prop,
+            "success_criterion": "rotation < 2 deg and translation < 5 cm vs ground truth"}
 
 
 # ---------------------------------------------------------------------------

@@ -58,6 +58,7 @@ typedef enum {
 } gcvo_status;
 
 typedef struct gcvo_ctx gcvo_ctx;   /* device, stream, scratch buffers */
+typedef struct gcvo_proposal gcvo_proposal; /* learned initial-pose network */
 typedef struct gcvo_grid gcvo_grid; /* voxel-hashed copy of a target cloud */
 
 /* Kernel parameters (Eq. 7 and the Remark that follows it). */
@@ -208,6 +209,56 @@ gcvo_status gcvo_register(gcvo_ctx *ctx, const gcvo_grid *target, const float *s
 gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_problem *problems,
                                   const gcvo_solver_params *params, double *T_out, gcvo_iter_log *logs,
                                   int *n_iter, int *status);
+
+/* ------------------------------------------------------------------------
+ * Learned initial-pose proposal (no counterpart in the paper: it is the
+ * learned-proposal extension of Algorithm 1's initial pose T^(0)).
+ *
+ * A point-set network maps a (source, target) pair to a twist: per point
+ * p = ((xyz - c) / s, l) with c and s the target's centroid and RMS radius,
+ * a shared MLP 4 -> 64 -> 128 -> 256 (ReLU after the first two layers),
+ * max-pooled over each cloud; the two 256-d features are concatenated and an
+ * MLP 512 -> 256 -> 128 -> 6 (ReLU after the first two) gives the twist
+ * (omega, v / s) of S T S^-1, S the shift by -c.  Weights are BF16 copies of
+ * FP32 master weights; every product accumulates in FP32.
+ *
+ * Batches: B pairs of n points each.  src_xyz / tgt_xyz: device, B x 3 x n
+ * (per pair a 3 x n SoA block); src_feat / tgt_feat: device, the first
+ * feature channel of pair b at feat[b * stride .. + n).  The flat parameter
+ * vector holds W1 (64x4), b1, W2 (128x64), b2, W3 (256x128), b3, H1
+ * (256x512), c1, H2 (128x256), c2, H3 (6x128), c3, row-major.
+ * ------------------------------------------------------------------------ */
+
+/* Number of parameters of the proposal network. */
+int64_t gcvo_proposal_n_params(void);
+
+/* Create a network with all parameters zero (set them before use). */
+gcvo_status gcvo_proposal_create(gcvo_ctx *ctx, gcvo_proposal **out);
+gcvo_status gcvo_proposal_destroy(gcvo_proposal *prop);
+
+/* Copy the FP32 master parameters in (host or device pointer, n_params
+ * floats) and reset the Adam state; or copy them out (checkpointing).
+ * Both synchronise the stream. */
+gcvo_status gcvo_proposal_set_params(gcvo_ctx *ctx, gcvo_proposal *prop, const float *params);
+gcvo_status gcvo_proposal_get_params(gcvo_ctx *ctx, const gcvo_proposal *prop, float *params_out);
+
+/* Forward pass for B pairs.  twist_out (host, B x 6, may be NULL): the
+ * normalised twists; T0_out (host, B x 16, may be NULL): the proposed
+ * initial poses S^-1 exp(omega, v) S in the caller's frame.  Synchronises. */
+gcvo_status gcvo_proposal_infer(gcvo_ctx *ctx, gcvo_proposal *prop, int n_pairs, int n_points,
+                                const float *src_xyz, const float *src_feat, int src_feat_stride,
+                                const float *tgt_xyz, const float *tgt_feat, int tgt_feat_stride,
+                                float *twist_out, double *T0_out);
+
+/* One training step on B labelled pairs (T_label: host, B x 16 poses with
+ * T^-1 z ~ x): forward, mean squared error of the normalised twist,
+ * backward, and an Adam step with learning rate lr (lr = 0 leaves the
+ * parameters unchanged).  loss_out (host, may be NULL) receives the loss,
+ * grad_out (host, n_params, may be NULL) the gradient.  Synchronises. */
+gcvo_status gcvo_proposal_train_step(gcvo_ctx *ctx, gcvo_proposal *prop, int n_pairs, int n_points,
+                                     const float *src_xyz, const float *src_feat, int src_feat_stride,
+                                     const float *tgt_xyz, const float *tgt_feat, int tgt_feat_stride,
+                                     const double *T_label, float lr, float *loss_out, float *grad_out);
 
 /* Profiling counters (no counterpart in the paper; used to measure the
  * pair kernel against its roofline). */

@@ -326,3 +326,81 @@ def gcvo_profile_read(ctx: Context) -> dict:
     p = gcvo_profile()
     _check(lib().gcvo_profile_read(ctx.handle, ctypes.byref(p)), "gcvo_profile_read")
     return dict(n_launches=p.n_launches, n_pair_launches=p.n_pair_launches, pair_kernel_ms=p.pair_kernel_ms)
+
+
+# ---------------------------------------------------------------------------
+# Learned initial-pose proposal
+# ---------------------------------------------------------------------------
+
+def _prop_lib():
+    L = lib()
+    if not getattr(L, "_prop_ready", False):
+        P, I = ctypes.c_void_p, ctypes.c_int
+        L.gcvo_proposal_n_params.restype = ctypes.c_int64
+        L.gcvo_proposal_n_params.argtypes = []
+        L.gcvo_proposal_create.argtypes = [P, ctypes.POINTER(ctypes.c_void_p)]
+        L.gcvo_proposal_destroy.argtypes = [P]
+        L.gcvo_proposal_set_params.argtypes = [P, P, P]
+        L.gcvo_proposal_get_params.argtypes = [P, P, P]
+        L.gcvo_proposal_infer.argtypes = [P, P, I, I, P, P, I, P, P, I, P, P]
+        L.gcvo_proposal_train_step.argtypes = [P, P, I, I, P, P, I, P, P, I, P, ctypes.c_float, P, P]
+        L._prop_ready = True
+    return L
+
+
+class Proposal:
+    """Handle of a proposal network (gcvo_proposal_*)."""
+
+    def __init__(self, ctx: Context):
+        L = _prop_lib()
+        h = ctypes.c_void_p()
+        _check(L.gcvo_proposal_create(ctx.handle, ctypes.byref(h)), "gcvo_proposal_create")
+        self.handle = h.value
+        self.ctx = ctx
+        self.n_params = int(L.gcvo_proposal_n_params())
+
+    def close(self):
+        if self.handle:
+            _prop_lib().gcvo_proposal_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: np.ndarray) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(_prop_lib().gcvo_proposal_set_params(self.ctx.handle, self.handle, p.ctypes.data), "set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(_prop_lib().gcvo_proposal_get_params(self.ctx.handle, self.handle, p.ctypes.data), "get_params")
+        return p
+
+    def infer(self, src_xyz, src_feat, tgt_xyz, tgt_feat):
+        """Batched clouds: xyz (B, 3, n), feat (B, n) device tensors.
+        Returns (twists (B, 6) normalised, T0 (B, 4, 4))."""
+        B, _, n = src_xyz.shape
+        tw = np.zeros((B, 6), dtype=np.float32)
+        T0 = np.zeros((B, 16))
+        _check(_prop_lib().gcvo_proposal_infer(self.ctx.handle, self.handle, B, n, _ptr(src_xyz), _ptr(src_feat),
+                                               int(src_feat.stride(0)), _ptr(tgt_xyz), _ptr(tgt_feat),
+                                               int(tgt_feat.stride(0)), tw.ctypes.data, T0.ctypes.data),
+               "gcvo_proposal_infer")
+        return tw, T0.reshape(B, 4, 4)
+
+    def train_step(self, src_xyz, src_feat, tgt_xyz, tgt_feat, T_label, lr: float, want_grad: bool = False):
+        B, _, n = src_xyz.shape
+        lab = np.ascontiguousarray(np.asarray(T_label, dtype=np.float64).reshape(B, 16))
+        loss = ctypes.c_float()
+        grad = np.zeros(self.n_params, dtype=np.float32) if want_grad else None
+        _check(_prop_lib().gcvo_proposal_train_step(self.ctx.handle, self.handle, B, n, _ptr(src_xyz),
+                                                    _ptr(src_feat), int(src_feat.stride(0)), _ptr(tgt_xyz),
+                                                    _ptr(tgt_feat), int(tgt_feat.stride(0)), lab.ctypes.data,
+                                                    float(lr), ctypes.byref(loss),
+                                                    grad.ctypes.data if grad is not None else None),
+               "gcvo_proposal_train_step")
+        return loss.value, grad

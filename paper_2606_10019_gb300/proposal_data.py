@@ -1,0 +1,84 @@
+"""Training and evaluation pairs for the learned initial-pose proposal.
+
+Pairs are drawn from the seeded scene generators (the corner scene of
+config 1 and, optionally, voxelised LiDAR frames of config 2), misaligned by
+a random rigid motion (rotation up to max_deg about a random axis,
+translation up to max_t), and labelled with the pose plain G-CVO-2 converges
+to when started from the true pose (the library does the labelling).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import datagen as D
+
+
+def corner_pairs(n_pairs: int, seed: int, n: int = 2000, max_deg: float = 30.0, max_t: float = 0.5):
+    """(tgt_xyz, tgt_l, src_xyz, src_l, T_true) per pair; T^-1 z ~ x."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n_pairs):
+        pair = D.make_corner_pair(frame=100000 * seed + b, n_src=n, n_tgt=n)
+        G = D.perturb(rng, max_deg, max_t)
+        src = D.apply(G, pair.src_xyz.astype(np.float64)).astype(np.float32)
+        out.append((pair.tgt_xyz, pair.tgt_feat[:, 0].copy(), src, pair.src_feat[:, 0].copy(), G @ pair.T_true))
+    return out
+
+
+def lidar_pairs(seq: "D.LidarSequence", n_pairs: int, seed: int, n: int = 4096, max_deg: float = 30.0,
+                max_t: float = 0.5):
+    """Consecutive-frame pairs of a LiDAR sequence, subsampled to n points,
+    with an extra random misalignment."""
+    rng = np.random.default_rng(seed)
+    out = []
+    nf = len(seq.poses) - 1
+    for b in range(n_pairs):
+        k = int(rng.integers(0, nf))
+        pair = seq.pair(k)
+        tx, tf = D.subsample(rng, pair.tgt_xyz, pair.tgt_feat, n)
+        sx, sf = D.subsample(rng, pair.src_xyz, pair.src_feat, n)
+        if len(tx) < n or len(sx) < n:
+            continue
+        G = D.perturb(rng, max_deg, max_t)
+        sx = D.apply(G, sx.astype(np.float64)).astype(np.float32)
+        out.append((tx, tf[:, 0].copy(), sx, sf[:, 0].copy(), G @ pair.T_true))
+    return out
+
+
+def to_device(pairs, dev):
+    """Batched tensors: src xyz (B, 3, n), src l (B, n), tgt xyz, tgt l."""
+    import torch
+    sx = torch.tensor(np.stack([p[2].T for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    sf = torch.tensor(np.stack([p[3] for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    tx = torch.tensor(np.stack([p[0].T for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    tf = torch.tensor(np.stack([p[1] for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    return sx, sf, tx, tf
+
+
+def problems(G, ctx, kp, batch, T0s, dev):
+    """gcvo_problem tuples (covariances and target grids built on the GPU)
+    for a batch from to_device; the returned list keeps the buffers alive."""
+    import torch
+    sx, sf, tx, tf = batch
+    n = sx.shape[2]
+    probs, keep = [], []
+    for k in range(sx.shape[0]):
+        tc = torch.empty((6, n), device=dev)
+        sc = torch.empty((6, n), device=dev)
+        G.gcvo_estimate_covariances(ctx, tx[k], kp, tc)
+        G.gcvo_estimate_covariances(ctx, sx[k], kp, sc)
+        g = G.gcvo_build_grid(ctx, tx[k], tc, tf[k:k + 1], kp)
+        probs.append((g, sx[k], sc, sf[k:k + 1], T0s[k]))
+        keep.append((tc, sc, g))
+    return probs, keep
+
+
+def pose_errors(Ts, T_true):
+    """Rotation (degrees) and translation (m) error of each pose."""
+    from scipy.spatial.transform import Rotation
+    e = []
+    for T, Tt in zip(Ts, T_true):
+        Dm = np.linalg.inv(Tt) @ T
+        e.append((np.degrees(np.linalg.norm(Rotation.from_matrix(Dm[:3, :3]).as_rotvec())),
+                  float(np.linalg.norm(Dm[:3, 3]))))
+    return np.array(e)

@@ -1,0 +1,131 @@
+"""Proposal network on the GPU vs the FP64 oracle (forward relative error
+<= 1e-2 with BF16 weights and activations; gradient cosine >= 0.999), and
+training by the project's own kernels."""
+import numpy as np
+import pytest
+
+from paper_2606_10019_gb300 import datagen as D
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(x):
+    """Round float32 values to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def penv():
+    import torch
+    from oracle import proposal as PR
+    from paper_2606_10019_gb300 import build as B
+    from paper_2606_10019_gb300 import gcvo as G
+    B.build()
+    ctx = G.gcvo_create(0)
+    yield PR, G, ctx, torch.device("cuda:0")
+    ctx.close()
+
+
+def _pairs(B, n, seed, max_deg=30.0, max_t=0.5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(B):
+        pair = D.make_corner_pair(frame=1000 * seed + b, n_src=n, n_tgt=n)
+        G = D.perturb(rng, max_deg, max_t)
+        src = D.apply(G, pair.src_xyz.astype(np.float64))
+        out.append((pair.tgt_xyz.astype(np.float64), pair.tgt_feat[:, 0], src, pair.src_feat[:, 0],
+                    G @ pair.T_true))
+    return out
+
+
+def _to_dev(pairs, dev):
+    import torch
+    sx = torch.tensor(np.stack([p[2].T for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    sf = torch.tensor(np.stack([p[3] for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    tx = torch.tensor(np.stack([p[0].T for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    tf = torch.tensor(np.stack([p[1] for p in pairs]), dtype=torch.float32, device=dev).contiguous()
+    return sx, sf, tx, tf
+
+
+def _oracle_batch(PR, pairs):
+    batch, labels = [], []
+    for tx, tf, sx, sf, T in pairs:
+        Pt, Ps, c, s = PR.normalise(tx, tf[:, None], sx, sf[:, None])
+        batch.append((Ps, Pt))
+        labels.append(PR.label_twist(T, c, s))
+    return batch, np.array(labels)
+
+
+def test_forward_and_gradient_match_oracle(penv):
+    PR, G, ctx, dev = penv
+    rng = np.random.default_rng(3)
+    p = PR.init_params(7)
+    for k in p:
+        if k[0] in "bc":
+            p[k] = rng.normal(scale=0.05, size=p[k].shape)
+    flat = PR.flat(p).astype(np.float32)
+    net = G.Proposal(ctx)
+    net.set_params(flat)
+    assert np.array_equal(net.get_params(), flat)
+    pairs = _pairs(4, 512, seed=1)
+    sx, sf, tx, tf = _to_dev(pairs, dev)
+    tw, T0 = net.infer(sx, sf, tx, tf)
+    # the oracle with the same BF16-rounded weights (biases stay FP32)
+    pq = {k: (bf16(v) if k[0] in "WH" else v.astype(np.float32).astype(np.float64)) for k, v in p.items()}
+    batch, labels = _oracle_batch(PR, pairs)
+    out, _ = PR.forward(pq, batch)
+    err = np.abs(tw - out).max() / np.abs(out).max()
+    assert err <= 1e-2, err
+    loss, grad = net.train_step(sx, sf, tx, tf, np.stack([q[4] for q in pairs]), lr=0.0, want_grad=True)
+    loss_o, g_o = PR.loss_and_grad(pq, batch, labels)
+    assert loss == pytest.approx(loss_o, rel=2e-2)
+    go = PR.flat(g_o)
+    cos = float(grad @ go / (np.linalg.norm(grad) * np.linalg.norm(go)))
+    assert cos >= 0.999, cos
+    assert np.array_equal(net.get_params(), flat)      # lr = 0: unchanged
+    net.close()
+
+
+def test_training_reduces_loss(penv):
+    PR, G, ctx, dev = penv
+    net = G.Proposal(ctx)
+    net.set_params(PR.flat(PR.init_params(11)).astype(np.float32))
+    pairs = _pairs(64, 512, seed=2)
+    sx, sf, tx, tf = _to_dev(pairs, dev)
+    T = np.stack([q[4] for q in pairs])
+    first = None
+    for it in range(150):
+        loss, _ = net.train_step(sx, sf, tx, tf, T, lr=1e-3)
+        first = loss if first is None else first
+    assert loss < 0.3 * first, (first, loss)
+    net.close()
+
+
+def test_trained_proposal_beats_identity_start(penv):
+    """Trained on G-CVO-labelled pairs by the project's kernels, the
+    proposal starts Algorithm 1 closer: on held-out pairs misaligned by up to
+    30 degrees / 0.5 m, proposal + G-CVO-2 succeeds (< 2 deg, < 5 cm) more
+    often and in fewer iterations than G-CVO-2 from the identity."""
+    PR, G, ctx, dev = penv
+    from paper_2606_10019_gb300 import proposal_data as PD
+    from paper_2606_10019_gb300 import train_proposal as TP
+    net = G.Proposal(ctx)
+    net.set_params(TP.init_params(net.n_params, 3))
+    TP.train(G, ctx, net, PD.corner_pairs(1024, 1), dev, steps=1500)
+    test = PD.corner_pairs(64, 2)
+    batch = PD.to_device(test, dev)
+    _, T0p = net.infer(*batch)
+    T_true = [p[4] for p in test]
+    kp = G.kernel_params(eig_max=0.01, eig_ratio=100.0)
+    sp = G.solver_params(k_max=200, eps_tol=1e-6)
+    res = {}
+    for name, T0s in (("identity", [np.eye(4)] * len(test)), ("proposal", list(T0p))):
+        probs, keep = PD.problems(G, ctx, kp, batch, T0s, dev)
+        T, _, n_iter, _ = G.gcvo_register_batched(ctx, probs, sp)
+        e = PD.pose_errors(list(T), T_true)
+        res[name] = (((e[:, 0] < 2.0) & (e[:, 1] < 0.05)).mean(), n_iter.mean())
+    assert res["proposal"][0] >= res["identity"][0] + 0.15, res
+    assert res["proposal"][1] * 2.0 <= res["identity"][1], res
+    net.close()
