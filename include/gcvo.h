@@ -210,6 +210,33 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
                                   const gcvo_solver_params *params, double *T_out, gcvo_iter_log *logs,
                                   int *n_iter, int *status);
 
+/* The evaluation of gcvo_eval (f, g and H = -M + Gamma at pose T) for
+ * callers that cannot allocate device memory: code running while another
+ * framework captures the stream into a CUDA graph, under a memory pool that
+ * owns every device byte, in a real-time loop that must not meet an
+ * allocation failure or the device-wide synchronisation of cudaMalloc /
+ * cudaFree, or in a plug-in without a context to keep buffers in.  (The
+ * paper has no counterpart; this is a deployment variant of one evaluation.)
+ *
+ * It needs no gcvo_ctx and allocates nothing: its scratch is one static
+ * device array of about 5.5 MiB in the library, reserved on every device that loads
+ * the library until the process exits.  The caller passes device pointers
+ * for every input (host pointers are rejected, since copying them would need
+ * a buffer), the target grid (built earlier with gcvo_build_grid), the
+ * stream, and host outputs.  Source points are processed in the caller's
+ * order, 16 per warp.
+ *  - n_src above 65536 returns GCVO_ERR_CAPACITY.
+ *  - The first call on a device looks up the array's device address (a
+ *    one-time set-up); make that first call before capturing a stream.
+ *  - Every call reuses the same array and overwrites the previous call's
+ *    contents; two calls whose GPU work overlaps (on different streams or
+ *    from different host threads without ordering) race and both results
+ *    are undefined.
+ * Synchronises cuda_stream before returning. */
+gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                             const float *src_feat, int64_t n_src, const double T[16], void *cuda_stream,
+                             double *f, double g[6], double H[36]);
+
 /* ------------------------------------------------------------------------
  * Learned initial-pose proposal (no counterpart in the paper: it is the
  * learned-proposal extension of Algorithm 1's initial pose T^(0)).

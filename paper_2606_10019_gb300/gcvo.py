@@ -404,3 +404,30 @@ class Proposal:
                                                     grad.ctypes.data if grad is not None else None),
                "gcvo_proposal_train_step")
         return loss.value, grad
+
+
+def gcvo_eval_static(grid: Grid, src_xyz, src_cov, src_feat, T, stream=None):
+    """gcvo_eval_static: the same evaluation as gcvo_eval without a context and
+    without allocating device memory (device inputs only, at most 65536
+    source points).  Returns (f, g, H)."""
+    L = lib()
+    if not getattr(L, "_static_ready", False):
+        P = ctypes.c_void_p
+        L.gcvo_eval_static.argtypes = [P, P, P, P, ctypes.c_int64, P, P, P, P, P]
+        L._static_ready = True
+    raw = 0
+    if stream is None:
+        import torch
+        raw = torch.cuda.current_stream().cuda_stream
+    elif isinstance(stream, int):
+        raw = stream
+    else:
+        raw = stream.cuda_stream
+    T = _pose(T)
+    f = ctypes.c_double()
+    g = np.zeros(6)
+    H = np.zeros(36)
+    _check(L.gcvo_eval_static(grid.handle, _ptr(src_xyz), _ptr(src_cov), _ptr(src_feat), _n(src_xyz), T.ctypes.data,
+                              ctypes.c_void_p(raw) if raw else None, ctypes.byref(f), g.ctypes.data, H.ctypes.data),
+           "gcvo_eval_static")
+    return f.value, g, H.reshape(6, 6)
