@@ -83,7 +83,7 @@ typedef struct {
 typedef struct {
     int order;          /* 2: G-CVO-2, Gauss-Newton step of Eq. (13);
                            1: G-CVO-1, gradient step with the line search of Eq. (9) */
-    int k_max;          /* iteration limit, 1..1000 */
+    int k_max;          /* iteration limit, 1..GCVO_MAX_KMAX */
     double eps_tol;     /* stop when ||xi^(k)||_1 < eps_tol */
     double mu0;         /* G-CVO-1 minimum step of Eq. (9) */
 } gcvo_solver_params;
@@ -121,7 +121,7 @@ typedef struct {
 /* Library-wide limits of this build. */
 #define GCVO_MAX_FEAT 3
 #define GCVO_MAX_KNN 16
-#define GCVO_MAX_KMAX 1000
+#define GCVO_MAX_KMAX 100000
 #define GCVO_MAX_PROBLEMS 4096
 
 /* Human-readable name of a status code (static storage). */

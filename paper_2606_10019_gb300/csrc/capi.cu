@@ -398,9 +398,13 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
     cudaStream_t s = ctx->stream;
     Prepared P;
     GCVO_TRY(prepare(ctx, np, pr, P));
-    GCVO_TRY(ctx->logs.ensure((size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
-    gcvo_iter_log *dlogs = ctx->logs.as<gcvo_iter_log>();
-    GCVO_CUDA(cudaMemsetAsync(dlogs, 0, (size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
+    // device log rows only when the caller asked for the log
+    gcvo_iter_log *dlogs = nullptr;
+    if (logs) {
+        GCVO_TRY(ctx->logs.ensure((size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
+        dlogs = ctx->logs.as<gcvo_iter_log>();
+        GCVO_CUDA(cudaMemsetAsync(dlogs, 0, (size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
+    }
     IterBufs b{};
     GCVO_TRY(iter_bufs(ctx, P, b, dlogs, sp->k_max));
     b.fa.eps_tol = sp->eps_tol;
