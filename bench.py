@@ -172,13 +172,8 @@ def run_gcvo(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(xyz_in, feat_in):
-        for k in range(F):
-            G.gcvo_estimate_covariances(ctx, xyz_in[k], kp, cov[k])
-        for k in range(F - 1):
-            if grids[k] is None:
-                grids[k] = G.gcvo_build_grid(ctx, xyz_in[k], cov[k], feat_in[k], kp)
-            else:
-                G.gcvo_rebuild_grid(ctx, grids[k], xyz_in[k], cov[k], feat_in[k], kp)
+        G.gcvo_estimate_covariances_batched(ctx, xyz_in, kp, cov)
+        grids[:] = G.gcvo_build_grids_batched(ctx, xyz_in[:-1], cov[:-1], feat_in[:-1], kp, grids)
         probs = [(grids[k], xyz_in[k + 1], cov[k + 1], feat_in[k + 1], np.eye(4)) for k in range(F - 1)]
         return G.gcvo_register_batched(ctx, probs, sp, want_log=True)
 

@@ -66,8 +66,10 @@ typedef struct {
     int kernel_mode;    /* 0: anisotropic kernel of Eq. (7) (default);
                            1: isotropic CVO kernel, Sigma_ij = iso_ell^2 I (Remark 3) */
     double sigma2;      /* kernel amplitude sigma^2 of Eq. (7a); default 1 */
-    double cutoff;      /* a pair contributes only if r^T Sigma_ij^{-1} r <= cutoff^2;
-                           must be > 0 (default 3) */
+    double cutoff;      /* a pair contributes only if r^T Sigma_ij^{-1} r <= cutoff^2
+                           (default 3); 0 disables the cutoff: every target /
+                           source pair is evaluated, the paper's dense objective
+                           (Sec. 5.4, O(N_X N_Z) per evaluation) */
     double iso_ell;     /* isotropic length scale (kernel_mode 1) */
     int knn;            /* n of Eq. (7b): neighbours per covariance, self included;
                            2..16 (default 10) */
@@ -175,6 +177,26 @@ gcvo_status gcvo_rebuild_grid(gcvo_ctx *ctx, gcvo_grid *grid, const float *xyz, 
  * destroyed; waits for work still using the grid's memory. */
 gcvo_status gcvo_grid_destroy(gcvo_grid *grid);
 
+/* gcvo_estimate_covariances for n_clouds clouds in one call: cloud k has
+ * n[k] points at xyz[k] (3 x n[k]) and its covariances go to cov_out[k]
+ * (6 x n[k]); all device memory.  The clouds are processed concurrently on
+ * the context's internal streams (one host thread each), after the work
+ * already queued on the context's stream, which then waits for them.  The
+ * results equal those of one call per cloud.  Returns the first failure. */
+gcvo_status gcvo_estimate_covariances_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
+                                              const int64_t *n, const gcvo_kernel_params *params,
+                                              float *const *cov_out);
+
+/* gcvo_build_grid / gcvo_rebuild_grid for n_clouds target clouds in one
+ * call, concurrently as in gcvo_estimate_covariances_batched: grids[k] ==
+ * NULL builds a new grid into grids[k], otherwise grids[k] is rebuilt in
+ * place.  Inputs as for gcvo_build_grid, per cloud, device memory only
+ * (cov may be NULL in kernel_mode 1).  Returns the first failure; grids
+ * built before it stay valid and belong to the caller. */
+gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
+                                     const float *const *cov, const float *const *feat, const int64_t *n,
+                                     const gcvo_kernel_params *params, gcvo_grid **grids);
+
 /* Number of points and occupied voxels of a grid. */
 gcvo_status gcvo_grid_info(const gcvo_grid *grid, int64_t *n_points, int64_t *n_cells, double *cell_size);
 
@@ -224,7 +246,7 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
  * for every input (host pointers are rejected, since copying them would need
  * a buffer), the target grid (built earlier with gcvo_build_grid), the
  * stream, and host outputs.  Source points are processed in the caller's
- * order, 16 per warp.
+ * order, 32 per work item.
  *  - n_src above 65536 returns GCVO_ERR_CAPACITY.
  *  - The first call on a device looks up the array's device address (a
  *    one-time set-up); make that first call before capturing a stream.
@@ -296,6 +318,16 @@ typedef struct {
     double pair_kernel_ms;   /* their summed device time, from CUDA events
                                 recorded on the context's stream around each launch */
 } gcvo_profile;
+
+/* Schedule of the evaluation pair pass (the autotuner; not in the paper):
+ * points per sub-tile, 8, 16 or 32, i.e. 4, 2 or 1 threads per source
+ * point.  set = 0 lets the autotuner pick per problem shape (the default:
+ * on the first call for a shape it times one pass with each schedule and
+ * keeps the fastest for the context); set = 8, 16 or 32 forces one; set =
+ * -1 changes nothing.  *last_used (may be NULL) receives the schedule of the
+ * last evaluation pass (0 before any).  Results do not depend on the
+ * schedule beyond FP32 summation order. */
+gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used);
 
 /* Turn profiling on (enable != 0) or off and reset the counters.
  * Synchronises the stream. */

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -26,7 +27,7 @@ bool is_device_ptr(const void *p) {
 bool valid_kernel_params(const gcvo_kernel_params *p) {
     if (!p) return false;
     if (p->kernel_mode != 0 && p->kernel_mode != 1) return false;
-    if (!(p->cutoff > 0) || !std::isfinite(p->cutoff)) return false;
+    if (!(p->cutoff >= 0) || !std::isfinite(p->cutoff)) return false;   // 0: dense, no cutoff
     if (!(p->sigma2 > 0) || !std::isfinite(p->sigma2)) return false;
     if (p->kernel_mode == 1 && !(p->iso_ell > 0)) return false;
     if (p->feat_dim < 1 || p->feat_dim > GCVO_MAX_FEAT) return false;
@@ -143,7 +144,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
 
     // device buffers
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t small_need = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 7 + al(sizeof(int)) * 4 + 256;
+    size_t small_need = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 7 + al(np * sizeof(int64_t)) +
+                        al(sizeof(int)) * 4 + 256;
     GCVO_TRY(ctx->small.ensure(small_need + 4096, s));
     char *sp = ctx->small.as<char>();
     SrcDesc *d_desc = reinterpret_cast<SrcDesc *>(sp);
@@ -160,11 +162,9 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sp += 256;
     int *d_pcnt = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
-    int *d_pincl = reinterpret_cast<int *>(sp);
-    sp += al(np * sizeof(int));
     int *d_pw0 = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
-    int *d_pw1 = reinterpret_cast<int *>(sp);
+    int64_t *d_poff = reinterpret_cast<int64_t *>(sp);
     P.d_nitems = d_nitems;
 
     GCVO_TRY(ctx->sort_keys.ensure(N * sizeof(unsigned long long), s));
@@ -179,6 +179,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->grp_prob.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->items.ensure(N * sizeof(int4), s));
     GCVO_TRY(ctx->item_prob.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->pgroup.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->status_word.ensure(256, s));
     char *vp = ctx->sort_vals.as<char>();
     int *vals = reinterpret_cast<int *>(vp);
@@ -205,6 +206,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sa.spos = ctx->src_pos.as<float4>();
     sa.sca = ctx->src_ca.as<float4>();
     sa.scb = ctx->src_cb.as<float4>();
+    sa.pgroup = ctx->pgroup.as<int>();
     sa.feat_dim = P.feat_dim;
     sa.iso = P.iso;
     GCVO_CUDA(launch_src_keys(sa, np, max_n, s));
@@ -217,14 +219,23 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_CUDA(launch_src_groups(sa, sa.keys, gid, N, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(),
                                 ctx->grp_prob.as<int>(), d_pg0, d_pg1, s));
     GCVO_CUDA(cudaMemcpyAsync(d_ngroups, gid + N - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    // pack consecutive groups of a problem into warp items
-    GCVO_CUDA(launch_pack(0, np, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(), d_pg0, d_pg1, d_pcnt, nullptr,
-                          nullptr, nullptr, nullptr, nullptr, s));
-    GCVO_CUDA(cudaMemcpyAsync(d_pincl, d_pcnt, np * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    GCVO_TRY(scan_inclusive_sum(d_pincl, np, ctx->scan_tmp.ptr, s));
-    GCVO_CUDA(launch_pack(1, np, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(), d_pg0, d_pg1, d_pcnt, d_pincl,
-                          ctx->items.as<int4>(), ctx->item_prob.as<int>(), d_pw0, d_pw1, s));
-    GCVO_CUDA(cudaMemcpyAsync(d_nitems, d_pincl + np - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    // work items: PAIR_ITEM consecutive sorted points of one problem (the
+    // sort puts problem p's points at its offset)
+    std::vector<int> hw0(np), hn(np);
+    std::vector<int64_t> hoff(np);
+    int n_items = 0;
+    for (int p = 0; p < np; ++p) {
+        hw0[p] = n_items;
+        hn[p] = (int)desc[p].n;
+        hoff[p] = desc[p].offset;
+        n_items += (int)((desc[p].n + PAIR_ITEM - 1) / PAIR_ITEM);
+    }
+    P.n_items = n_items;
+    GCVO_CUDA(cudaMemcpyAsync(d_pw0, hw0.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_pcnt, hn.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_poff, hoff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_nitems, &n_items, sizeof(int), cudaMemcpyHostToDevice, s));
+    GCVO_CUDA(launch_items(np, d_pw0, d_poff, d_pcnt, n_items, ctx->items.as<int4>(), ctx->item_prob.as<int>(), s));
 
     // read back group and item counts and ranges, source eigenvalue bounds
     void *hp;
@@ -232,16 +243,12 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     int *h = static_cast<int *>(hp);
     GCVO_CUDA(cudaMemcpyAsync(h, d_ngroups, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 1, ctx->status_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GCVO_CUDA(cudaMemcpyAsync(h + 2, d_nitems, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8, d_lam, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8 + np, d_pg0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8 + 2 * np, d_pg1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 3 * np, d_pw0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 4 * np, d_pw1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaStreamSynchronize(s));
     if (h[1] & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
     P.n_groups = h[0];
-    P.n_items = h[2];
     P.probs.assign(np, ProbDev{});
     for (int p = 0; p < np; ++p) {
         ProbDev &d = P.probs[p];
@@ -255,8 +262,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         d.iter = 0;
         d.g0 = h[8 + np + p];
         d.g1 = h[8 + 2 * np + p];
-        d.w0 = h[8 + 3 * np + p];
-        d.w1 = h[8 + 4 * np + p];
+        d.w0 = hw0[p];
+        d.w1 = hw0[p] + (int)((desc[p].n + PAIR_ITEM - 1) / PAIR_ITEM);
         int le = h[8 + p];
         int li = le >= 0 ? le : le ^ 0x7fffffff;
         float lam_src;
@@ -264,7 +271,9 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         const gcvo_kernel_params &kp = G->kp;
         double c2 = kp.cutoff * kp.cutoff;
         double rho2;
-        if (kp.kernel_mode == 1)
+        if (kp.cutoff == 0)   // dense: every pair, no cutoff
+            rho2 = c2 = INFINITY;
+        else if (kp.kernel_mode == 1)
             rho2 = c2 * kp.iso_ell * kp.iso_ell * (1.0 + 1e-5);
         else
             rho2 = c2 * ((double)G->store.d.lam_max + (double)lam_src) * (1.0 + 2e-4) + 1e-12;
@@ -293,8 +302,70 @@ struct IterBufs {
     PairArgs pa;
     FinalizeArgs fa;
     int *work;
-    int grid;
+    int grid;   // persistent blocks of the evaluation pass
+    int sub;    // its schedule: points per sub-tile
 };
+
+// Blocks of a persistent pair launch: one item per block at a time, as many
+// blocks as fit on the GPU.
+int pair_grid(const gcvo_ctx *ctx, const Prepared &P, int mode, int sub) {
+    int per_sm = std::max(1, pair_blocks_per_sm(mode, P.iso, P.feat_dim, sub));
+    return std::max(1, std::min(P.n_items, per_sm * ctx->sm_count));
+}
+
+// The autotuner: the schedule of the evaluation pass (8, 16 or 32 points per
+// sub-tile, i.e. 4, 2 or 1 lanes per point) for this shape of problem set
+// -- a forced one, the cached choice for the same shape, or the fastest of
+// one timed pass with each (the second of two, CUDA events).  The shape is
+// the kernel mode, the feature count and the log2 buckets of the problem
+// count and of the mean source size.
+gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
+    int sub = ctx->forced_sub;
+    if (!sub) {
+        int lb_n = 0, lb_p = 0;
+        while ((2LL << lb_n) <= P.n_points / std::max(1, P.n_problems)) ++lb_n;
+        while ((2 << lb_p) <= P.n_problems) ++lb_p;
+        const long long key = ((long long)P.iso << 40) | ((long long)P.feat_dim << 32) | ((long long)lb_p << 8) | lb_n;
+        for (auto &kv : ctx->tuned)
+            if (kv.first == key) sub = kv.second;
+        if (!sub) {
+            const int cands[3] = {8, 16, 32};
+            cudaEvent_t ev[6];
+            for (auto &e : ev) GCVO_CUDA(cudaEventCreate(&e));
+            float best = 0.f;
+            gcvo_status st = GCVO_OK;
+            for (int c = 0; c < 3 && st == GCVO_OK; ++c) {
+                const int g = pair_grid(ctx, P, PAIR_EVAL, cands[c]);
+                for (int rep = 0; rep < 2 && st == GCVO_OK; ++rep) {
+                    cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(int), ctx->stream);
+                    if (e == cudaSuccess && rep == 1) e = cudaEventRecord(ev[2 * c], ctx->stream);
+                    if (e == cudaSuccess) e = launch_pair(b.pa, PAIR_EVAL, P.iso, P.feat_dim, cands[c], g, ctx->stream);
+                    if (e == cudaSuccess && rep == 1) e = cudaEventRecord(ev[2 * c + 1], ctx->stream);
+                    if (e != cudaSuccess) {
+                        set_last_cuda_error(e, "schedule timing pass", __LINE__);
+                        st = GCVO_ERR_CUDA;
+                    }
+                }
+            }
+            if (st == GCVO_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = GCVO_ERR_CUDA;
+            for (int c = 0; c < 3 && st == GCVO_OK; ++c) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]) != cudaSuccess) st = GCVO_ERR_CUDA;
+                if (c == 0 || ms < best) {
+                    best = ms;
+                    sub = cands[c];
+                }
+            }
+            for (auto &e : ev) cudaEventDestroy(e);
+            if (st != GCVO_OK) return st;
+            ctx->tuned.emplace_back(key, sub);
+        }
+    }
+    b.sub = sub;
+    b.grid = pair_grid(ctx, P, PAIR_EVAL, sub);
+    ctx->last_sub = sub;
+    return GCVO_OK;
+}
 
 gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -312,6 +383,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     a.gstart = ctx->grp_start.as<int>();
     a.items = ctx->items.as<int4>();
     a.item_prob = ctx->item_prob.as<int>();
+    a.pgroup = ctx->pgroup.as<int>();
     a.n_items = P.d_nitems;
     a.probs = ctx->probs.as<ProbDev>();
     a.grids = ctx->grids.as<GridDev>();
@@ -339,11 +411,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     // group anchors and float rotation at the initial pose
     f.mode = FIN_ANCHORS;
     GCVO_CUDA(launch_finalize(f, ctx->stream));
-    int per_sm = pair_blocks_per_sm(PAIR_EVAL, P.iso, P.feat_dim);
-    if (per_sm < 1) per_sm = 1;
-    int want = (P.n_items + PAIR_WARPS - 1) / PAIR_WARPS;
-    b.grid = std::max(1, std::min(want, per_sm * ctx->sm_count));
-    return GCVO_OK;
+    return choose_schedule(ctx, P, b);
 }
 
 gcvo_status check_status_word(gcvo_ctx *ctx) {
@@ -356,9 +424,14 @@ gcvo_status check_status_word(gcvo_ctx *ctx) {
     return GCVO_OK;
 }
 
-gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode) {
-    GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), ctx->stream));
+// One pair pass on stream s (the work counter is reset first).  With
+// profiling on, the launch is bracketed by two events from the pool; inside
+// a stream capture they become event-record nodes of the graph.
+gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode, cudaStream_t s,
+                             bool capturing = false) {
+    GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (ctx->profiling && mode == PAIR_EVAL) {
         while (ctx->ev_pool.size() < ctx->ev_used + 2) {
             cudaEvent_t e;
@@ -368,25 +441,82 @@ gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int 
         e0 = ctx->ev_pool[ctx->ev_used];
         e1 = ctx->ev_pool[ctx->ev_used + 1];
         ctx->ev_used += 2;
-        GCVO_CUDA(cudaEventRecord(e0, ctx->stream));
+        GCVO_CUDA(cudaEventRecordWithFlags(e0, s, ev_flags));
     }
-    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, b.grid, ctx->stream));
-    if (e1) {
-        GCVO_CUDA(cudaEventRecord(e1, ctx->stream));
-        ctx->pair_launches += 1;
-    }
+    const int sub = mode == PAIR_EVAL ? b.sub : 8;
+    const int grid = mode == PAIR_EVAL ? b.grid : pair_grid(ctx, P, mode, sub);
+    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, sub, grid, s));
+    if (e1) GCVO_CUDA(cudaEventRecordWithFlags(e1, s, ev_flags));
     return GCVO_OK;
 }
 
 // Add the device time of the recorded pair-kernel launches (stream must be
 // synchronised) and release the events for reuse.
-gcvo_status collect_profile(gcvo_ctx *ctx) {
+gcvo_status collect_profile(gcvo_ctx *ctx, bool keep = false) {
     for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
         float ms = 0.f;
         GCVO_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
         ctx->pair_ms += ms;
+        ctx->pair_launches += 1;
     }
-    ctx->ev_used = 0;
+    if (!keep) ctx->ev_used = 0;
+    return GCVO_OK;
+}
+
+// One iteration of Algorithm 1 on stream s: G-CVO-2 is a pair pass and the
+// Gauss-Newton finalize; G-CVO-1 a gradient pass, its finalize (direction),
+// the line-search pass and the step.
+gcvo_status enqueue_iteration(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int order, cudaStream_t s,
+                              bool capturing) {
+    if (order == 2) {
+        GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
+        b.fa.mode = FIN_GN;
+        GCVO_CUDA(launch_finalize(b.fa, s));
+    } else {
+        GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
+        b.fa.mode = FIN_GRAD;
+        GCVO_CUDA(launch_finalize(b.fa, s));
+        GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_LINESEARCH, s, capturing));
+        b.fa.mode = FIN_LINESEARCH;
+        GCVO_CUDA(launch_finalize(b.fa, s));
+    }
+    return GCVO_OK;
+}
+
+// The U-iteration graph of a register call: captured on a private stream,
+// instantiated, and destroyed with this object.
+struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;   // kernel launches per replay
+    ~ChunkGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+gcvo_status capture_chunk(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int order, int U, ChunkGraph &cg) {
+    if (!ctx->cap_stream) GCVO_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = launches_so_far();
+    GCVO_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    gcvo_status st = GCVO_OK;
+    for (int u = 0; u < U && st == GCVO_OK; ++u) st = enqueue_iteration(ctx, P, b, order, ctx->cap_stream, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    // captured launches ran nothing: they are counted per replay instead
+    cg.kernels = launches_so_far() - l0;
+    count_launches(-cg.kernels);
+    if (st != GCVO_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != GCVO_OK) return st;
+        set_last_cuda_error(e, "cudaStreamEndCapture", __LINE__);
+        return GCVO_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&cg.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cg.exec = nullptr;
+        set_last_cuda_error(e, "cudaGraphInstantiate", __LINE__);
+        return GCVO_ERR_CUDA;
+    }
     return GCVO_OK;
 }
 
@@ -414,28 +544,23 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
     void *hp;
     GCVO_TRY(host_pinned(ctx, 64, &hp));
     int *h_active = static_cast<int *>(hp);
-    const int U = 4;
+    // U iterations per host check, replayed from one CUDA graph.  Iterations
+    // past a problem's convergence or k_max leave it untouched (the finalize
+    // skips inactive problems, the pair kernel their items).
+    const int U = std::min(8, sp->k_max);
+    ChunkGraph cg;
+    GCVO_TRY(capture_chunk(ctx, P, b, sp->order, U, cg));
     int it = 0;
     while (it < sp->k_max) {
-        for (int u = 0; u < U && it < sp->k_max; ++u, ++it) {
-            if (sp->order == 2) {
-                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
-                b.fa.mode = FIN_GN;
-                GCVO_CUDA(launch_finalize(b.fa, s));
-            } else {
-                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
-                b.fa.mode = FIN_GRAD;
-                GCVO_CUDA(launch_finalize(b.fa, s));
-                GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_LINESEARCH));
-                b.fa.mode = FIN_LINESEARCH;
-                GCVO_CUDA(launch_finalize(b.fa, s));
-            }
-        }
+        GCVO_CUDA(cudaGraphLaunch(cg.exec, s));
+        count_launches(cg.kernels);
+        it += U;
         GCVO_CUDA(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
         GCVO_CUDA(cudaStreamSynchronize(s));
-        GCVO_TRY(collect_profile(ctx));
+        GCVO_TRY(collect_profile(ctx, true));
         if (*h_active <= 0) break;
     }
+    ctx->ev_used = 0;
     GCVO_TRY(check_status_word(ctx));
     std::vector<ProbDev> out(np);
     GCVO_CUDA(cudaMemcpyAsync(out.data(), ctx->probs.ptr, np * sizeof(ProbDev), cudaMemcpyDeviceToHost, s));
@@ -460,6 +585,57 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
         if (status) status[p] = st;
     }
     return GCVO_OK;
+}
+
+// Runs fn(child, k) for k = 0 .. n-1 on up to GCVO_LANES child contexts,
+// one host thread each, every child on its own stream.  The children's work
+// starts after everything already queued on ctx->stream and ctx->stream
+// waits for all of it, so the call is stream-ordered like the single-cloud
+// calls.  Returns the first failure.
+constexpr int GCVO_LANES = 8;
+
+template <class F>
+gcvo_status run_lanes(gcvo_ctx *ctx, int n, F fn) {
+    const int K = std::min(GCVO_LANES, n);
+    while ((int)ctx->lanes.size() < K) {
+        cudaStream_t ls;
+        GCVO_CUDA(cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking));
+        gcvo_ctx *c = nullptr;
+        gcvo_status st = gcvo_create(&c, ctx->device, ls);
+        if (st != GCVO_OK) {
+            cudaStreamDestroy(ls);
+            return st;
+        }
+        ctx->lanes.push_back(c);
+        ctx->lane_streams.push_back(ls);
+    }
+    cudaEvent_t start;
+    GCVO_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    GCVO_CUDA(cudaEventRecord(start, ctx->stream));
+    std::vector<gcvo_status> st(K, GCVO_OK);
+    std::vector<std::thread> th;
+    for (int j = 0; j < K; ++j) {
+        th.emplace_back([&, j]() {
+            gcvo_ctx *c = ctx->lanes[j];
+            if (cudaSetDevice(ctx->device) != cudaSuccess || cudaStreamWaitEvent(c->stream, start, 0) != cudaSuccess) {
+                st[j] = GCVO_ERR_CUDA;
+                return;
+            }
+            for (int k = j; k < n && st[j] == GCVO_OK; k += K) st[j] = fn(c, k);
+        });
+    }
+    for (auto &t : th) t.join();
+    gcvo_status out = GCVO_OK;
+    for (int j = 0; j < K; ++j) {
+        if (out == GCVO_OK) out = st[j];
+        cudaEvent_t done;
+        GCVO_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        GCVO_CUDA(cudaEventRecord(done, ctx->lanes[j]->stream));
+        GCVO_CUDA(cudaStreamWaitEvent(ctx->stream, done, 0));
+        cudaEventDestroy(done);
+    }
+    cudaEventDestroy(start);
+    return out;
 }
 
 }  // namespace
@@ -533,7 +709,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
                       &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
-                      &ctx->anchors, &ctx->items, &ctx->item_prob};
+                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
         DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
@@ -541,6 +717,9 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
+    for (gcvo_ctx *c : ctx->lanes) gcvo_destroy(c);
+    for (cudaStream_t ls : ctx->lane_streams) cudaStreamDestroy(ls);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
@@ -556,6 +735,13 @@ gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
     ctx->pair_launches = 0;
     ctx->pair_ms = 0.0;
     ctx->launch_base = launches_so_far();
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used) {
+    if (!ctx || (set != -1 && set != 0 && set != 8 && set != 16 && set != 32)) return GCVO_ERR_INVALID_ARG;
+    if (set >= 0) ctx->forced_sub = set;
+    if (last_used) *last_used = ctx->last_sub;
     return GCVO_OK;
 }
 
@@ -576,7 +762,7 @@ gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n
     if (params->knn < 2 || params->knn > GCVO_MAX_KNN || n < params->knn || n > (1 << 28))
         return GCVO_ERR_INVALID_ARG;
     if (params->eig_max > 0 && !(params->eig_ratio >= 1.0)) return GCVO_ERR_INVALID_ARG;
-    if (!(params->cutoff > 0)) return GCVO_ERR_INVALID_ARG;
+    if (!(params->cutoff >= 0)) return GCVO_ERR_INVALID_ARG;
     GCVO_CUDA(cudaSetDevice(ctx->device));
     size_t need = staged_floats(xyz, 3 * (size_t)n);
     bool host_out = !is_device_ptr(cov_out);
@@ -686,7 +872,7 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
     GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
     int one = 1;
     GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL));
+    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, ctx->stream));
     b.fa.mode = FIN_EVAL;
     GCVO_CUDA(launch_finalize(b.fa, ctx->stream));
     EvalOut e{};
@@ -735,6 +921,37 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
     if (!ctx || !problems || !T_out || n_problems < 1) return GCVO_ERR_INVALID_ARG;
     GCVO_CUDA(cudaSetDevice(ctx->device));
     return run_register(ctx, n_problems, problems, params, T_out, logs, n_iter, status);
+}
+
+gcvo_status gcvo_estimate_covariances_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
+                                              const int64_t *n, const gcvo_kernel_params *params,
+                                              float *const *cov_out) {
+    if (!ctx || n_clouds < 1 || !xyz || !n || !params || !cov_out) return GCVO_ERR_INVALID_ARG;
+    for (int k = 0; k < n_clouds; ++k)
+        if (!xyz[k] || !cov_out[k] || !is_device_ptr(xyz[k]) || !is_device_ptr(cov_out[k]))
+            return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    return run_lanes(ctx, n_clouds, [&](gcvo_ctx *c, int k) {
+        return gcvo_estimate_covariances(c, xyz[k], n[k], params, cov_out[k]);
+    });
+}
+
+gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
+                                     const float *const *cov, const float *const *feat, const int64_t *n,
+                                     const gcvo_kernel_params *params, gcvo_grid **grids) {
+    if (!ctx || n_clouds < 1 || !xyz || !feat || !n || !params || !grids) return GCVO_ERR_INVALID_ARG;
+    if (params->kernel_mode == 0 && !cov) return GCVO_ERR_INVALID_ARG;
+    for (int k = 0; k < n_clouds; ++k) {
+        if (!xyz[k] || !feat[k] || !is_device_ptr(xyz[k]) || !is_device_ptr(feat[k])) return GCVO_ERR_INVALID_ARG;
+        if (params->kernel_mode == 0 && (!cov[k] || !is_device_ptr(cov[k]))) return GCVO_ERR_INVALID_ARG;
+        if (grids[k] && grids[k]->device != ctx->device) return GCVO_ERR_INVALID_ARG;
+    }
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    return run_lanes(ctx, n_clouds, [&](gcvo_ctx *c, int k) {
+        const float *ck = params->kernel_mode == 0 ? cov[k] : nullptr;
+        if (grids[k]) return gcvo_rebuild_grid(c, grids[k], xyz[k], ck, feat[k], n[k], params);
+        return gcvo_build_grid(c, xyz[k], ck, feat[k], n[k], params, &grids[k]);
+    });
 }
 
 }  // extern "C"

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 #include "gcvo.h"
@@ -186,7 +187,7 @@ struct gcvo_ctx {
     gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
     gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
     gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g;
-    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob;
+    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup;
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_retry;
     void *host_pinned = nullptr;
@@ -199,4 +200,13 @@ struct gcvo_ctx {
     long long launch_base = 0;
     long long pair_launches = 0;
     double pair_ms = 0.0;
+    // child contexts with their own streams for the *_batched calls
+    std::vector<gcvo_ctx *> lanes;
+    std::vector<cudaStream_t> lane_streams;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // pair-kernel schedule (points per sub-tile): forced (0 = autotune), the
+    // autotuner's choices per problem shape, and the last one used
+    int forced_sub = 0;
+    std::vector<std::pair<long long, int>> tuned;
+    int last_sub = 0;
 };

@@ -4,11 +4,10 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "knn.cuh"
 
 namespace gcvo {
 namespace {
-
-__device__ inline int dec_int(int k) { return k >= 0 ? k : k ^ 0x7fffffff; }
 
 __global__ void k_voxel_keys(const float *xyz, int64_t n, GridDev g, bool absolute, unsigned long long *keys,
                              int *vals) {
@@ -130,7 +129,12 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     if ((hb[7] & 2) && kp.kernel_mode == 0 && cov) return GCVO_ERR_INVALID_ARG;
 
     double h = cell;
-    if (h <= 0) {
+    if (h <= 0 && kp.cutoff == 0) {
+        // dense mode: no kernel range; a few large voxels hold the cloud
+        double ext = 0.0;
+        for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)mx[a] - (double)mn[a]);
+        h = std::max(ext / 4.0, 1e-3);
+    } else if (h <= 0) {
         // half the kernel range: finer voxels hug the range ball more tightly
         if (kp.kernel_mode == 1)
             h = 0.5 * kp.cutoff * kp.iso_ell;
@@ -227,170 +231,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int KNN_MAX = GCVO_MAX_KNN;
-
-// Symmetric 3x3 eigen-decomposition in double precision by cyclic Jacobi
-// sweeps; returns eigenvalues in w and eigenvectors as the columns of V.
-__device__ void jacobi3(double a[3][3], double w[3], double V[3][3]) {
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) V[r][c] = r == c ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 32; ++sweep) {
-        double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-        double dia = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
-        if (off <= 1e-300 || off < 1e-17 * dia) break;
-        const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
-        for (int k = 0; k < 3; ++k) {
-            int p = P[k], q = Q[k];
-            double apq = a[p][q];
-            if (apq == 0.0) continue;
-            double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
-            double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            double c = rsqrt(1.0 + t * t), s = t * c;
-            // A <- G^T A G with G the rotation in the (p, q) plane
-            for (int m = 0; m < 3; ++m) {
-                double amp = a[m][p], amq = a[m][q];
-                a[m][p] = c * amp - s * amq;
-                a[m][q] = s * amp + c * amq;
-            }
-            for (int m = 0; m < 3; ++m) {
-                double apm = a[p][m], aqm = a[q][m];
-                a[p][m] = c * apm - s * aqm;
-                a[q][m] = s * apm + c * aqm;
-            }
-            a[p][q] = a[q][p] = 0.0;
-            for (int m = 0; m < 3; ++m) {
-                double vmp = V[m][p], vmq = V[m][q];
-                V[m][p] = c * vmp - s * vmq;
-                V[m][q] = s * vmp + c * vmq;
-            }
-        }
-    }
-    for (int k = 0; k < 3; ++k) w[k] = a[k][k];
-}
-
-struct KnnList {
-    float d[KNN_MAX];
-    int i[KNN_MAX];   // original index (tie-break)
-    int k[KNN_MAX];   // sorted index in the grid searched
-};
-
-// The knn nearest points of q in grid g, searching shells R = 1..R_max of
-// voxels around q's voxel.  After shell R every point closer than R * h has
-// been seen, so the search is complete (returns true) once the knn-th
-// distance is within R * h.
-__device__ __forceinline__ bool knn_search(const GridDev &g, float4 q, int knn, int R_max, KnnList &L) {
-    int cq[3];
-    float qc[3] = {q.x, q.y, q.z};
-    for (int a = 0; a < 3; ++a) {
-        int c = (int)floorf((qc[a] - g.corner[a]) * g.inv_h);
-        cq[a] = min(max(c, 0), g.dims[a] - 1);
-    }
-#pragma unroll
-    for (int m = 0; m < KNN_MAX; ++m) {
-        L.d[m] = INFINITY;
-        L.i[m] = 0x7fffffff;
-        L.k[m] = -1;
-    }
-    float wd = INFINITY;   // knn-th distance so far
-    int wi = 0x7fffffff;   // its original index (INT_MAX while the list is short)
-    for (int R = 1; R <= R_max; ++R) {
-        for (int dx = -R; dx <= R; ++dx) {
-            int cx = cq[0] + dx;
-            if (cx < 0 || cx >= g.dims[0]) continue;
-            for (int dy = -R; dy <= R; ++dy) {
-                int cy = cq[1] + dy;
-                if (cy < 0 || cy >= g.dims[1]) continue;
-                // shell R: voxels with max(|dx|, |dy|, |dz|) == R; shell 1 is
-                // the whole 3 x 3 x 3 block, centre included
-                bool xy_edge = (dx == -R || dx == R || dy == -R || dy == R);
-                int step = (R == 1 || xy_edge) ? 1 : 2 * R;
-                for (int dz = -R; dz <= R; dz += step) {
-                    int cz = cq[2] + dz;
-                    if (cz < 0 || cz >= g.dims[2]) continue;
-                    unsigned long long key = ((unsigned long long)cx * g.dims[1] + cy) * g.dims[2] + cz;
-                    int c = grid_lookup(g, key);
-                    if (c < 0) continue;
-                    int s0 = g.cell_start[c], s1 = g.cell_start[c + 1];
-                    for (int k = s0; k < s1; ++k) {
-                        float4 y = g.pos[k];
-                        float ex = y.x - q.x, ey = y.y - q.y, ez = y.z - q.z;
-                        float d2 = ex * ex + ey * ey + ez * ez;
-                        if (d2 > wd) continue;
-                        int oi = g.orig[k];
-                        if (d2 == wd && oi >= wi) continue;
-                        float cd = d2;
-                        int ci = oi, ck = k;
-#pragma unroll
-                        for (int m = 0; m < KNN_MAX; ++m) {
-                            if (m < knn) {
-                                bool less = cd < L.d[m] || (cd == L.d[m] && ci < L.i[m]);
-                                if (less) {
-                                    float td = L.d[m];
-                                    int ti = L.i[m], tk = L.k[m];
-                                    L.d[m] = cd;
-                                    L.i[m] = ci;
-                                    L.k[m] = ck;
-                                    cd = td;
-                                    ci = ti;
-                                    ck = tk;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int m = 0; m < KNN_MAX; ++m)
-                            if (m == knn - 1) {
-                                wd = L.d[m];
-                                wi = L.i[m];
-                            }
-                    }
-                }
-            }
-        }
-        float reach = (float)R * g.h;
-        if (wi != 0x7fffffff && wd <= reach * reach * 0.999f) return true;
-    }
-    return false;
-}
-
-// Eq. (7b) over the list, then the eigenvalue bound; writes column o of cov_out.
-__device__ __forceinline__ void knn_write_cov(const GridDev &g, float4 q, const KnnList &L, int knn, double eig_max,
-                              double eig_ratio, int64_t n, int o, float *cov_out) {
-    // Sigma = 1/(n-1) sum (y - x)(y - x)^T, centred at the query point
-    float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int m = 0; m < KNN_MAX; ++m) {
-        if (m < knn) {
-            float4 y = g.pos[L.k[m]];
-            float d0 = y.x - q.x, d1 = y.y - q.y, d2 = y.z - q.z;
-            S[0] += d0 * d0;
-            S[1] += d0 * d1;
-            S[2] += d0 * d2;
-            S[3] += d1 * d1;
-            S[4] += d1 * d2;
-            S[5] += d2 * d2;
-        }
-    }
-    float inv = 1.0f / (float)(knn - 1);
-    for (int k = 0; k < 6; ++k) S[k] *= inv;
-    if (eig_max > 0.0) {
-        double a[3][3] = {{S[0], S[1], S[2]}, {S[1], S[3], S[4]}, {S[2], S[4], S[5]}};
-        double w[3], V[3][3];
-        jacobi3(a, w, V);
-        double lo = eig_max / eig_ratio;
-        for (int k = 0; k < 3; ++k) w[k] = fmin(fmax(w[k], lo), eig_max);
-        double B[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                B[r][c] = V[r][0] * w[0] * V[c][0] + V[r][1] * w[1] * V[c][1] + V[r][2] * w[2] * V[c][2];
-        S[0] = (float)B[0][0];
-        S[1] = (float)(0.5 * (B[0][1] + B[1][0]));
-        S[2] = (float)(0.5 * (B[0][2] + B[2][0]));
-        S[3] = (float)B[1][1];
-        S[4] = (float)(0.5 * (B[1][2] + B[2][1]));
-        S[5] = (float)B[2][2];
-    }
-    for (int k = 0; k < 6; ++k) cov_out[k * n + o] = S[k];
-}
+using namespace knn;
 
 // Pass 1 on the fine grid (shells 1 and 2); points whose neighbours lie
 // farther away are queued for pass 2.
@@ -406,152 +247,12 @@ __global__ void k_knn_cov(GridDev g, int knn, double eig_max, double eig_ratio, 
         retry[atomicAdd(n_retry, 1)] = (int)i;
 }
 
-// Pass 2: one warp per queued point, searching the coarse grid shell by
-// shell without a limit.  The lanes split each shell's voxels and keep
-// private sorted lists; after every shell the warp merges them (repeated
-// warp-wide minimum over each lane's next entry) into the knn nearest so
-// far, and stops once the knn-th distance is within the shells' reach.
-__global__ void k_knn_cov_far(GridDev fine, GridDev coarse, int knn, double eig_max, double eig_ratio, int64_t n,
-                              float *cov_out, const int *retry, const int *n_retry, unsigned *status) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const int m = *n_retry;
-    const int maxR = max(coarse.dims[0], max(coarse.dims[1], coarse.dims[2]));
-    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < m; t += gridDim.x * wpb) {
-        const int i = retry[t];
-        const float4 q = fine.pos[i];
-        int cq[3];
-        {
-            float qc[3] = {q.x, q.y, q.z};
-            for (int a = 0; a < 3; ++a) {
-                int c = (int)floorf((qc[a] - coarse.corner[a]) * coarse.inv_h);
-                cq[a] = min(max(c, 0), coarse.dims[a] - 1);
-            }
-        }
-        KnnList L;   // this lane's private list
-#pragma unroll
-        for (int k = 0; k < KNN_MAX; ++k) {
-            L.d[k] = INFINITY;
-            L.i[k] = 0x7fffffff;
-            L.k[k] = -1;
-        }
-        float wd = INFINITY;
-        int wi = 0x7fffffff;
-        KnnList M;   // merged result (identical in every lane)
-        bool done = false;
-        for (int R = 1; R <= maxR && !done; ++R) {
-            const int side = 2 * R + 1;
-            const int cube = side * side * side;
-            for (int v = lane; v < cube; v += 32) {
-                int dx = v / (side * side) - R, dy = (v / side) % side - R, dz = v % side - R;
-                if (R > 1 && max(abs(dx), max(abs(dy), abs(dz))) != R) continue;   // shell only
-                int cx = cq[0] + dx, cy = cq[1] + dy, cz = cq[2] + dz;
-                if (cx < 0 || cy < 0 || cz < 0 || cx >= coarse.dims[0] || cy >= coarse.dims[1] ||
-                    cz >= coarse.dims[2])
-                    continue;
-                unsigned long long key = ((unsigned long long)cx * coarse.dims[1] + cy) * coarse.dims[2] + cz;
-                int c = grid_lookup(coarse, key);
-                if (c < 0) continue;
-                for (int k = coarse.cell_start[c], k1 = coarse.cell_start[c + 1]; k < k1; ++k) {
-                    float4 y = coarse.pos[k];
-                    float ex = y.x - q.x, ey = y.y - q.y, ez = y.z - q.z;
-                    float d2 = ex * ex + ey * ey + ez * ez;
-                    if (d2 > wd) continue;
-                    int oi = coarse.orig[k];
-                    if (d2 == wd && oi >= wi) continue;
-                    float cd = d2;
-                    int ci = oi, ck = k;
-#pragma unroll
-                    for (int mm = 0; mm < KNN_MAX; ++mm) {
-                        if (mm < knn) {
-                            bool less = cd < L.d[mm] || (cd == L.d[mm] && ci < L.i[mm]);
-                            if (less) {
-                                float td = L.d[mm];
-                                int ti = L.i[mm], tk = L.k[mm];
-                                L.d[mm] = cd;
-                                L.i[mm] = ci;
-                                L.k[mm] = ck;
-                                cd = td;
-                                ci = ti;
-                                ck = tk;
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int mm = 0; mm < KNN_MAX; ++mm)
-                        if (mm == knn - 1) {
-                            wd = L.d[mm];
-                            wi = L.i[mm];
-                        }
-                }
-            }
-            // merge: knn rounds of a warp-wide minimum over (d, index)
-            int head = 0;
-            for (int r = 0; r < knn; ++r) {
-                float hd = INFINITY;
-                int hi = 0x7fffffff, hk = -1;
-#pragma unroll
-                for (int mm = 0; mm < KNN_MAX; ++mm)
-                    if (mm == head) {
-                        hd = L.d[mm];
-                        hi = L.i[mm];
-                        hk = L.k[mm];
-                    }
-                float bd = hd;
-                int bi = hi;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    float od = __shfl_xor_sync(FULL, bd, o);
-                    int oi = __shfl_xor_sync(FULL, bi, o);
-                    if (od < bd || (od == bd && oi < bi)) {
-                        bd = od;
-                        bi = oi;
-                    }
-                }
-                const bool mine = (hd == bd && hi == bi && hk >= 0);
-                const unsigned who = __ballot_sync(FULL, mine);
-                const int src = who ? __ffs(who) - 1 : 0;
-                const int bk = __shfl_sync(FULL, hk, src);
-                if (lane == src && who) ++head;
-#pragma unroll
-                for (int mm = 0; mm < KNN_MAX; ++mm)
-                    if (mm == r) {
-                        M.d[mm] = who ? bd : INFINITY;
-                        M.i[mm] = who ? bi : 0x7fffffff;
-                        M.k[mm] = who ? bk : -1;
-                    }
-            }
-            // every lane prunes with the merged knn-th distance from now on
-            float md = INFINITY;
-            int mi = 0x7fffffff, mk = -1;
-#pragma unroll
-            for (int mm = 0; mm < KNN_MAX; ++mm)
-                if (mm == knn - 1) {
-                    md = M.d[mm];
-                    mi = M.i[mm];
-                    mk = M.k[mm];
-                }
-            if (mk >= 0 && (md < wd || (md == wd && mi < wi))) {
-                wd = md;
-                wi = mi;
-            }
-            const float reach = (float)R * coarse.h;
-            done = mk >= 0 && md <= reach * reach * 0.999f;
-        }
-        bool full = true;
-#pragma unroll
-        for (int mm = 0; mm < KNN_MAX; ++mm)
-            if (mm < knn && M.k[mm] < 0) full = false;
-        if (!full) {
-            if (lane == 0) atomicOr(status, DEV_ERR_CAPACITY);
-            continue;
-        }
-        if (lane == 0) knn_write_cov(coarse, q, M, knn, eig_max, eig_ratio, n, fine.orig[i], cov_out);
-    }
-}
 
 }  // namespace
+
+void launch_knn_far(const GridDev &fine, const GridDev &coarse, int knn, double eig_max, double eig_ratio, int64_t n,
+                    float *cov_out, const int *retry, const int *n_retry, unsigned *status, int blocks,
+                    cudaStream_t s);
 
 gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gcvo_kernel_params &kp,
                             float *cov_out) {
@@ -563,7 +264,7 @@ gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gc
     q.feat_dim = 0;
     double cell = 0.0;
     if (kp.eig_max > 0) {
-        cell = kp.cutoff * std::sqrt(2.0 * kp.eig_max) * 0.5;
+        cell = (kp.cutoff > 0 ? kp.cutoff : 3.0) * std::sqrt(2.0 * kp.eig_max) * 0.5;
     } else {
         GCVO_TRY(ctx->small.ensure(4096, s));
         float *bb = ctx->small.as<float>();
@@ -602,9 +303,8 @@ gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gc
     GCVO_CUDA(cudaMemsetAsync(stw, 0, 2 * sizeof(unsigned), s));
     k_knn_cov<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(fine.d, kp.knn, kp.eig_max, kp.eig_ratio, n, cov_out,
                                                           ctx->knn_retry.as<int>(), n_retry);
-    k_knn_cov_far<<<std::max(1, ctx->sm_count) * 4, 128, 0, s>>>(fine.d, coarse.d, kp.knn, kp.eig_max,
-                                                                kp.eig_ratio, n, cov_out, ctx->knn_retry.as<int>(),
-                                                                n_retry, stw);
+    launch_knn_far(fine.d, coarse.d, kp.knn, kp.eig_max, kp.eig_ratio, n, cov_out, ctx->knn_retry.as<int>(), n_retry,
+                   stw, std::max(1, ctx->sm_count) * 4, s);
     count_launches(2);
     GCVO_CUDA(cudaGetLastError());
     unsigned hs = 0;

@@ -24,7 +24,7 @@ namespace gcvo {
 namespace {
 
 constexpr int64_t NA_MAX_SRC = 65536;                  // source points per call
-constexpr int NA_ITEM = 16;                            // points per warp item
+constexpr int NA_ITEM = PAIR_ITEM;                     // points per work item
 constexpr int NA_MAX_ITEMS = (int)(NA_MAX_SRC / NA_ITEM);
 
 // Byte offsets of the pieces of the scratch array (each 256-aligned).
@@ -34,7 +34,8 @@ constexpr size_t NA_SCA = NA_SPOS + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_SCB = NA_SCA + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_ANCHOR = NA_SCB + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_GSTART = NA_ANCHOR + al256(NA_MAX_SRC * 16);
-constexpr size_t NA_ITEMS = NA_GSTART + al256(NA_MAX_SRC * 4);
+constexpr size_t NA_PGROUP = NA_GSTART + al256(NA_MAX_SRC * 4);
+constexpr size_t NA_ITEMS = NA_PGROUP + al256(NA_MAX_SRC * 4);
 constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 16);
 constexpr size_t NA_PART = NA_IPROB + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_COUNTS = NA_PART + al256((size_t)NA_MAX_ITEMS * 64 * 4);
@@ -49,13 +50,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 // Pack the caller's SoA source (in its own order) into the float4 records of
 // the pair kernel and the largest covariance eigenvalue.  The caller's order
 // carries no spatial grouping, so every point is its own group (its own FP64
-// anchor and bounding box) and a warp item holds NA_ITEM of them.
+// anchor) and a work item holds NA_ITEM consecutive points.
 __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat, int feat_dim, int n, int iso,
                           unsigned char *base) {
     float4 *spos = reinterpret_cast<float4 *>(base + NA_SPOS);
     float4 *sca = reinterpret_cast<float4 *>(base + NA_SCA);
     float4 *scb = reinterpret_cast<float4 *>(base + NA_SCB);
     int *gstart = reinterpret_cast<int *>(base + NA_GSTART);
+    int *pgroup = reinterpret_cast<int *>(base + NA_PGROUP);
     int4 *items = reinterpret_cast<int4 *>(base + NA_ITEMS);
     int *iprob = reinterpret_cast<int *>(base + NA_IPROB);
     int *words = reinterpret_cast<int *>(base + NA_WORDS);
@@ -83,9 +85,10 @@ __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat,
     }
     if (bad) atomicOr(reinterpret_cast<unsigned *>(words + 3), DEV_ERR_NONFINITE);
     gstart[i] = i;
+    pgroup[i] = i;
     if (i % NA_ITEM == 0) {
         const int m = min(NA_ITEM, n - i);
-        items[i / NA_ITEM] = make_int4(i, m, i, m);   // first group, groups, first point, points
+        items[i / NA_ITEM] = make_int4(0, 0, i, m);   // first point, points
         iprob[i / NA_ITEM] = 0;
     }
 }
@@ -115,9 +118,10 @@ __global__ void k_na_setup(NaSetup a, unsigned char *base) {
     P->w1 = a.n_items;
     const int le = words[2];
     const float lam_src = __int_as_float(le >= 0 ? le : le ^ 0x7fffffff);
-    const double c2 = a.cutoff * a.cutoff;
+    double c2 = a.cutoff * a.cutoff;
     double rho2 = a.kernel_mode == 1 ? c2 * a.iso_ell * a.iso_ell * (1.0 + 1e-5)
                                      : c2 * ((double)G->lam_max + (double)lam_src) * (1.0 + 2e-4) + 1e-12;
+    if (a.cutoff == 0) rho2 = c2 = INFINITY;   // dense: every pair
     P->rho2 = (float)rho2;
     P->c2 = (float)c2;
     P->sigma2 = (float)a.sigma2;
@@ -212,6 +216,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.scb = reinterpret_cast<const float4 *>(base + NA_SCB);
     pa.anchor = fa.anchor;
     pa.gstart = fa.gstart;
+    pa.pgroup = reinterpret_cast<const int *>(base + NA_PGROUP);
     pa.items = reinterpret_cast<const int4 *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
     pa.n_items = words + 1;
@@ -224,9 +229,9 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.ls_literal = 0;
     int sm = 0;
     GCVO_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
-    int per_sm = pair_blocks_per_sm(PAIR_EVAL, iso, fd);
-    int grid = std::max(1, std::min((n_items + PAIR_WARPS - 1) / PAIR_WARPS, std::max(1, per_sm) * sm));
-    GCVO_CUDA(launch_pair(pa, PAIR_EVAL, iso, fd, grid, s));
+    int per_sm = pair_blocks_per_sm(PAIR_EVAL, iso, fd, 8);
+    int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * sm));
+    GCVO_CUDA(launch_pair(pa, PAIR_EVAL, iso, fd, 8, grid, s));
     fa.mode = FIN_EVAL;
     GCVO_CUDA(launch_finalize(fa, s));
     EvalOut e;

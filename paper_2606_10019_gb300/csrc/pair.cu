@@ -1,813 +1,20 @@
-// The per-iteration hot path of Algorithm 1:
-//   k_pair     -- transform the source (Alg. 1, "Transform Z with T^-1"),
-//                 scan the target voxels around each group of 32 source
-//                 points, and accumulate f (Eq. 5), g (Eq. 8) and the
-//                 Gauss-Newton matrix M (Eq. 11) -- or, for G-CVO-1, the
-//                 line-search polynomial of Eq. (9) -- per group;
-//   k_finalize -- FP64 sum of the group partials per problem, change of
+// The FP64 side of the per-iteration hot path of Algorithm 1, and the source
+// grouping done once per call:
+//   k_finalize -- FP64 sum of the item partials of each problem, change of
 //                 frame, connection term (Eq. 12), the 6x6 solve of Eq. (13)
-//                 and the update T <- T exp(xi).
-// Source grouping (once per call) sorts each source cloud by a Morton code
-// of its own voxels and cuts it into groups of at most 32 points that never
-// straddle a coarse voxel.
+//                 and the update T <- T exp(xi); per-group anchors for the
+//                 pair kernel (tile.cu) at the new pose.
+// Source grouping sorts each source cloud by a Morton code of its own voxels
+// and cuts it into groups of at most 32 points that never straddle a coarse
+// voxel; every group gets an FP64 anchor, every point its group index.
 #include <cstring>
 
 #include "common.cuh"
 #include "pair.cuh"
+#include "ptx.cuh"
 
 namespace gcvo {
 namespace {
-
-// ---------------------------------------------------------------------------
-// PTX helpers: mbarrier and bulk (TMA) global->shared copies.
-// ---------------------------------------------------------------------------
-__device__ inline uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ inline void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ inline void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ inline void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ inline float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ inline float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Compensated (TwoSum) warp reduction: returns (hi, lo) in lane 0.
-__device__ inline void warp_sum2(float v, float &hi, float &lo) {
-    hi = v;
-    lo = 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float oh = __shfl_down_sync(0xffffffffu, hi, o);
-        float ol = __shfl_down_sync(0xffffffffu, lo, o);
-        float s = hi + oh;
-        float bp = s - hi;
-        float err = (hi - (s - bp)) + (oh - bp);
-        hi = s;
-        lo = lo + ol + err;
-    }
-}
-
-constexpr float NEG_HALF_LOG2E = -0.72134752044448170368f;  // -1/2 * log2(e)
-static_assert(PAIR_CAP * 48 >= 28 * 33 * 4, "epilogue transpose must fit in the staging area");
-static_assert(PAIR_CAP <= 256, "queue entries are uint8");
-static_assert(PAIR_CAP * 48 >= (32 * 10 * 2 + 64) * 4, "phase-2 slots must fit in the staging area");
-
-struct WarpSmem {
-    float4 *pos, *ca, *cb;
-    uint8_t *queue;
-    uint64_t *bar;
-    int2 *seg;      // per packed group: its candidate segment in the staged list
-    int *own_off;   // per lane (owner): offset of its queued pairs in the warp list
-    int *own_nq;    // per lane: number of queued pairs
-    float *own_S;   // per lane: its point's sums (PAIR_OWN_S floats, smem atomics)
-    float4 *own_data;  // per lane: p, Sigma', features (and a_k for the line search)
-};
-
-__device__ inline WarpSmem warp_smem(unsigned char *base, int w, int mode) {
-    WarpSmem s;
-    unsigned char *p = base + (size_t)w * pair_warp_smem(mode);
-    s.pos = reinterpret_cast<float4 *>(p);
-    s.ca = reinterpret_cast<float4 *>(p + PAIR_CAP * 16);
-    s.cb = reinterpret_cast<float4 *>(p + PAIR_CAP * 32);
-    s.queue = p + PAIR_CAP * 48;
-    unsigned char *q = p + PAIR_CAP * 80;
-    s.bar = reinterpret_cast<uint64_t *>(q);
-    s.seg = reinterpret_cast<int2 *>(q + 16);
-    s.own_off = reinterpret_cast<int *>(q + 16 + PAIR_MAX_SUB * 8);
-    s.own_nq = s.own_off + 32;
-    s.own_S = reinterpret_cast<float *>(s.own_nq + 32);
-    s.own_data = reinterpret_cast<float4 *>(s.own_S + 32 * PAIR_OWN_S);
-    return s;
-}
-
-// ---------------------------------------------------------------------------
-// The pair kernel.
-//
-// One warp owns one group of <= 32 source points (one per lane).  Per
-// group: transform the points by T^{-1} (double), take the bounding box of
-// the transformed group, and list the target voxel columns (cx, cy) that
-// meet the box grown by rho; the occupied voxels of one column over the
-// needed cz range are contiguous in the target's sorted order, so each
-// column is one run.  Runs are staged into shared memory in chunks of
-// PAIR_CAP points by cp.async.bulk copies completing on an mbarrier.  Each
-// lane tests every staged point against its own source point (|r| <= rho,
-// broadcast loads) and queues the hits; then the lanes evaluate their
-// queues (Eq. 7 with the 3x3 adjugate, FP32) and accumulate
-//   S_f = sum w_ij,  S_u = sum w_ij Sigma_ij^-1 r_ij,  S_A = sum w_ij Sigma_ij^-1
-// with w_ij = c_ij k(x_i, p_j).  Per source point the contribution to
-// (f, g, M) follows from p_j, S_f, S_u, S_A (Eq. 8, 11); the warp reduces the
-// 28 values with compensated sums and writes one partial per group.
-// ---------------------------------------------------------------------------
-__device__ inline int ord_enc(float f) {
-    int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-__device__ inline float ord_dec(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
-
-// One anisotropic pair of Eq. (7): Sigma_ij = Sigma_i + Sigma'_j, the adjugate
-// and determinant of the 3x3, d^2 = r^T Sigma^-1 r, w = c_ij sigma^2
-// exp(-d^2 / 2) (zero beyond the cutoff), and the sums S_f += w,
-// S_u += w Sigma^-1 r, S_A += w Sigma^-1 (od*: the source point's p, Sigma',
-// features; x, ca, cb: the staged target point).
-template <int FD>
-__device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, const float4 cbv, const float4 od0,
-                                           const float4 od1, const float4 od2, const float c2, float *t,
-                                           int &n_kept) {
-    const float r0 = x.x - od0.x, r1 = x.y - od0.y, r2 = x.z - od0.z;
-    float cij = x.w * od0.w;
-    if (FD > 1) cij += cbv.z * od2.z + cbv.w * od2.w;
-    const float s00 = ca.x + od1.x, s01 = ca.y + od1.y, s02 = ca.z + od1.z;
-    const float s11 = ca.w + od1.w, s12 = cbv.x + od2.x, s22 = cbv.y + od2.y;
-    const float c00 = s11 * s22 - s12 * s12;
-    const float c01 = s02 * s12 - s01 * s22;
-    const float c02 = s01 * s12 - s02 * s11;
-    const float c11 = s00 * s22 - s02 * s02;
-    const float c12 = s01 * s02 - s00 * s12;
-    const float c22 = s00 * s11 - s01 * s01;
-    const float det = s00 * c00 + s01 * c01 + s02 * c02;
-    const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
-    const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
-    const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
-    const float qf = r0 * y0 + r1 * y1 + r2 * y2;
-    const float rdet = rcp_approx(det);
-    const float d2 = qf * rdet;
-    const bool keep = d2 <= c2;
-    const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-    n_kept += keep;
-    const float wd = wgt * rdet;
-    t[0] += wgt;
-    t[1] += wd * y0;
-    t[2] += wd * y1;
-    t[3] += wd * y2;
-    t[4] += wd * c00;
-    t[5] += wd * c01;
-    t[6] += wd * c02;
-    t[7] += wd * c11;
-    t[8] += wd * c12;
-    t[9] += wd * c22;
-}
-
-template <int MODE, bool ISO, int FD>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 5) k_pair(PairArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
-    constexpr int OWN_STRIDE = MODE == PAIR_EVAL ? 3 : 6;   // float4 per lane in own_data
-    static_assert(32 * 16 * OWN_STRIDE == (pair_warp_smem(MODE) - (PAIR_CAP * 80 + 16 + PAIR_MAX_SUB * 8 + 64 * 4 +
-                                                                 32 * PAIR_OWN_S * 4)),
-                  "own_data region size");
-    WarpSmem S = warp_smem(smem, w, MODE);
-    if (lane == 0) mbar_init(S.bar, 1);
-    __syncwarp();
-    unsigned parity = 0;
-    const int n_items = *a.n_items;
-
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(a.work, 1);
-        it = __shfl_sync(FULL, it, 0);
-        if (it >= n_items) break;
-        const int4 item = a.items[it];   // first group, groups, first point, points
-        const int prob = a.item_prob[it];
-        const ProbDev *P = a.probs + prob;
-        if (P->status != 0) {
-            // skip the rest of this finished problem's work items in one step
-            if (lane == 0) atomicMax(a.work, P->w1);
-            continue;
-        }
-        const GridDev *G = a.grids + prob;
-        const int fg = item.x, ng = item.y, j0 = item.z, cnt = item.w;
-        const bool act = lane < cnt;
-        // the item packs ng spatial groups (consecutive point ranges); lane
-        // s < ng holds the first point of group s, every lane finds its group
-        const int gs = lane < ng ? a.gstart[fg + lane] - j0 : 0;
-        int sub = 0;
-        for (int s2 = 1; s2 < ng; ++s2) sub += (__shfl_sync(FULL, gs, s2) <= lane) ? 1 : 0;
-        const int first_of_sub = __shfl_sync(FULL, gs, sub);
-
-        // ---- transform (Alg. 1, Z by T^-1) around the first point z_g of
-        // the lane's group: p_j - o = R^T (z_j - z_g) + [R^T (z_g - t) - o],
-        // the bracket (the anchor) computed in FP64 by the finalize.
-        float Rf[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
-        const float4 anc = a.anchor[fg + sub];
-        const int jj = act ? j0 + lane : j0;
-        const float4 zg = a.spos[j0 + first_of_sub];
-        float4 z = a.spos[jj];
-        float4 zb = a.scb[jj];
-        const float e0 = z.x - zg.x, e1 = z.y - zg.y, e2 = z.z - zg.z;
-        const float px = anc.x + (Rf[0] * e0 + Rf[3] * e1 + Rf[6] * e2);
-        const float py = anc.y + (Rf[1] * e0 + Rf[4] * e1 + Rf[7] * e2);
-        const float pz = anc.z + (Rf[2] * e0 + Rf[5] * e1 + Rf[8] * e2);
-        // Sigma'_j = R^T Sigma_j R
-        float q00 = 0.f, q01 = 0.f, q02 = 0.f, q11 = 0.f, q12 = 0.f, q22 = 0.f;
-        if (!ISO) {
-            float4 za = a.sca[jj];
-            float sm[9] = {za.x, za.y, za.z, za.y, za.w, zb.x, za.z, zb.x, zb.y};
-            float T1[9];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    T1[3 * r + c] = sm[3 * r] * Rf[c] + sm[3 * r + 1] * Rf[3 + c] + sm[3 * r + 2] * Rf[6 + c];
-            q00 = Rf[0] * T1[0] + Rf[3] * T1[3] + Rf[6] * T1[6];
-            q01 = Rf[0] * T1[1] + Rf[3] * T1[4] + Rf[6] * T1[7];
-            q02 = Rf[0] * T1[2] + Rf[3] * T1[5] + Rf[6] * T1[8];
-            q11 = Rf[1] * T1[1] + Rf[4] * T1[4] + Rf[7] * T1[7];
-            q12 = Rf[1] * T1[2] + Rf[4] * T1[5] + Rf[7] * T1[8];
-            q22 = Rf[2] * T1[2] + Rf[5] * T1[5] + Rf[8] * T1[8];
-        }
-        const float sg = P->sigma2;
-        const float l0 = sg * z.w;
-        const float l1 = FD > 1 ? sg * zb.z : 0.f;
-        const float l2 = FD > 1 ? sg * zb.w : 0.f;
-        const float rho2 = P->rho2, c2 = P->c2, iso_inv = P->iso_inv;
-
-        // line-search direction powers a_k (G-CVO-1 second pass)
-        float a1[3], a2[3], a3[3], a4[3];
-        if (MODE == PAIR_LINESEARCH) {
-            float om0 = P->dir32[0], om1 = P->dir32[1], om2 = P->dir32[2];
-            a1[0] = om1 * pz - om2 * py + P->dir32[3];
-            a1[1] = om2 * px - om0 * pz + P->dir32[4];
-            a1[2] = om0 * py - om1 * px + P->dir32[5];
-#define CROSS_W(dst, src)                            \
-    dst[0] = om1 * src[2] - om2 * src[1];            \
-    dst[1] = om2 * src[0] - om0 * src[2];            \
-    dst[2] = om0 * src[1] - om1 * src[0];
-            CROSS_W(a2, a1)
-            CROSS_W(a3, a2)
-            CROSS_W(a4, a3)
-#undef CROSS_W
-        }
-
-        // ---- owner tables: this lane's point data for the balanced phase 2,
-        // and its sums (zeroed)
-        S.own_data[lane * OWN_STRIDE + 0] = make_float4(px, py, pz, l0);
-        S.own_data[lane * OWN_STRIDE + 1] = make_float4(q00, q01, q02, q11);
-        S.own_data[lane * OWN_STRIDE + 2] = make_float4(q12, q22, l1, l2);
-        if (MODE == PAIR_LINESEARCH) {
-            S.own_data[lane * OWN_STRIDE + 3] = make_float4(a1[0], a1[1], a1[2], a2[0]);
-            S.own_data[lane * OWN_STRIDE + 4] = make_float4(a2[1], a2[2], a3[0], a3[1]);
-            S.own_data[lane * OWN_STRIDE + 5] = make_float4(a3[2], a4[0], a4[1], a4[2]);
-        }
-#pragma unroll
-        for (int k = 0; k < PAIR_OWN_S; ++k) S.own_S[lane * PAIR_OWN_S + k] = 0.f;
-
-        // ---- bounding box of the lane's transformed group
-        const unsigned smask = __match_any_sync(FULL, sub);
-        float bmin[3], bmax[3];
-        {
-            const float pp[3] = {px, py, pz};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                bmin[k] = ord_dec(__reduce_min_sync(smask, ord_enc(act ? pp[k] : INFINITY)));
-                bmax[k] = ord_dec(__reduce_max_sync(smask, ord_enc(act ? pp[k] : -INFINITY)));
-            }
-        }
-        const float rho = sqrtf(rho2);
-        const float h = G->h, ih = G->inv_h;
-        // culling radius: rho plus a margin for the float voxel assignment
-        const float rc = rho * 1.0001f + 1e-5f * h;
-        const float rc2 = rc * rc;
-        // voxel ranges of the lane's group (an empty range has hi < lo)
-        int lo[3], hi[3];
-        bool empty = !(bmin[0] <= bmax[0]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float fl = floorf((bmin[k] - rc - G->corner[k]) * ih);
-            float fh = floorf((bmax[k] + rc - G->corner[k]) * ih);
-            fl = fminf(fmaxf(fl, 0.0f), (float)G->dims[k]);
-            fh = fmaxf(fminf(fh, (float)(G->dims[k] - 1)), -1.0f);
-            if (!(fl <= fh)) empty = true;
-            lo[k] = empty ? 0 : (int)fl;
-            hi[k] = empty ? -1 : (int)fh;
-        }
-        const int my_cols = empty ? 0 : (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1);
-        // lane s < ng: column count of group s and its exclusive offset
-        int cols_s = __shfl_sync(FULL, my_cols, gs);
-        if (lane >= ng) cols_s = 0;
-        int cinc = cols_s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(FULL, cinc, o);
-            if (lane >= o) cinc += u;
-        }
-        const int coff_s = cinc - cols_s;
-        const int total_cols = __shfl_sync(FULL, cinc, 31);
-
-        // ---- accumulators
-        float Sf = 0.f, Su0 = 0.f, Su1 = 0.f, Su2 = 0.f;
-        float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
-        float L1 = 0.f, L2 = 0.f, L3 = 0.f, L4 = 0.f;  // line-search sums (f in Sf)
-        int n_pairs = 0, n_kept = 0, n_cand = 0;
-
-        const int dy = G->dims[1], dzs = G->dims[2];
-        for (int cb0 = 0; cb0 < total_cols; cb0 += 32) {
-            // ---- one (group, column) per lane.  A column (cx, cy) is kept
-            // when its xy rectangle lies within rho of the group box, and its
-            // cz range shrinks with that distance; the occupied voxels of the
-            // range are contiguous in the sorted target: one run per column.
-            const int c = cb0 + lane;
-            const bool cvalid = c < total_cols;
-            int cs = 0;
-            for (int s2 = 1; s2 < ng; ++s2) cs += (__shfl_sync(FULL, coff_s, s2) <= c) ? 1 : 0;
-            const int src_lane = __shfl_sync(FULL, gs, cs);          // a lane of group cs
-            const int cloc = c - __shfl_sync(FULL, coff_s, cs);
-            float cbmin[3], cbmax[3];
-            int clo[3], chi[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                cbmin[k] = __shfl_sync(FULL, bmin[k], src_lane);
-                cbmax[k] = __shfl_sync(FULL, bmax[k], src_lane);
-                clo[k] = __shfl_sync(FULL, lo[k], src_lane);
-                chi[k] = __shfl_sync(FULL, hi[k], src_lane);
-            }
-            int rs = 0, rl = 0;
-            if (cvalid) {
-                const int ncy = chi[1] - clo[1] + 1;
-                const int cx = clo[0] + cloc / ncy, cy = clo[1] + cloc % ncy;
-                const float x0 = G->corner[0] + (float)cx * h, y0 = G->corner[1] + (float)cy * h;
-                const float ddx = fmaxf(0.0f, fmaxf(x0 - cbmax[0], cbmin[0] - (x0 + h)));
-                const float ddy = fmaxf(0.0f, fmaxf(y0 - cbmax[1], cbmin[1] - (y0 + h)));
-                const float d2xy = ddx * ddx + ddy * ddy;
-                if (d2xy <= rc2) {
-                    const float ez = sqrtf(rc2 - d2xy);
-                    const int czl = max(clo[2], (int)floorf(fmaxf((cbmin[2] - ez - G->corner[2]) * ih, -1.0f)));
-                    const int czh = min(chi[2], (int)floorf(fminf((cbmax[2] + ez - G->corner[2]) * ih, (float)dzs)));
-                    // the column's occupied voxels, sorted by cz: keep [czl, czh]
-                    const int2 cr = G->col_range[cx * dy + cy];
-                    int first = -1, last = -1;
-                    for (int cc = cr.x; cc < cr.y; ++cc) {
-                        int zc = __ldg(G->cell_z + cc);
-                        if (zc >= czl) {
-                            if (zc <= czh) first = cc;
-                            break;
-                        }
-                    }
-                    if (first >= 0) {
-                        last = first;
-                        for (int cc = first + 1; cc < cr.y; ++cc) {
-                            if (__ldg(G->cell_z + cc) > czh) break;
-                            last = cc;
-                        }
-                        rs = __ldg(G->cell_start + first);
-                        rl = __ldg(G->cell_start + last + 1) - rs;
-                    }
-                }
-            }
-            // exclusive offsets of the runs; the runs of one group are
-            // contiguous, so each group owns one segment [seg_lo, seg_hi)
-            int incl = rl;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += u;
-            }
-            const int total = __shfl_sync(FULL, incl, 31);
-            const int off = incl - rl;
-            {
-                const unsigned pm = __match_any_sync(FULL, cvalid ? cs : -1);
-                const int slo = __reduce_min_sync(pm, off);
-                const int shi = __reduce_max_sync(pm, incl);
-                if (lane < ng) S.seg[lane] = make_int2(0, 0);
-                __syncwarp();
-                if (cvalid && lane == __ffs(pm) - 1) S.seg[cs] = make_int2(slo, shi);
-                __syncwarp();
-            }
-            const int2 myseg = S.seg[sub];
-
-            for (int base = 0; base < total; base += PAIR_CAP) {
-                const int m = min(PAIR_CAP, total - base);
-                // ---- stage the chunk [base, base + m) of the runs (TMA bulk copies)
-                fence_proxy_async_smem();
-                if (lane == 0) mbar_arrive_expect_tx(S.bar, (unsigned)m * 48u);
-                __syncwarp();
-                {
-                    int s0 = max(off, base), s1 = min(off + rl, base + m);
-                    if (s1 > s0) {
-                        int src = rs + (s0 - off), dst = s0 - base;
-                        unsigned bytes = (unsigned)(s1 - s0) * 16u;
-                        bulk_g2s(S.pos + dst, G->pos + src, bytes, S.bar);
-                        bulk_g2s(S.ca + dst, G->ca + src, bytes, S.bar);
-                        bulk_g2s(S.cb + dst, G->cb + src, bytes, S.bar);
-                    }
-                }
-                {
-                    // bounded wait; the exit decision is warp-uniform
-                    int spin = 0;
-                    bool all_done = false;
-                    for (;;) {
-                        bool done = mbar_try_wait(S.bar, parity);
-                        all_done = __all_sync(FULL, done);
-                        if (all_done || ++spin > (1 << 22)) break;
-                    }
-                    if (!all_done) {
-                        if (lane == 0) atomicOr(a.status_word, DEV_ERR_TIMEOUT);
-                        return;
-                    }
-                    parity ^= 1u;
-                }
-
-                // ---- phase 1: |r| <= rho test against the lane's own
-                // group segment of the chunk (a broadcast load per group)
-                const int k0 = max(myseg.x, base), k1 = min(myseg.y, base + m);
-                const int len = act ? max(0, k1 - k0) : 0;
-                const int tmax1 = __reduce_max_sync(FULL, len);
-                n_cand += len;
-                int nq = 0;
-                const int kb0 = k0 - base;
-                for (int t = 0; t < tmax1; t += 4) {
-                    float dd[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int tt = t + u;
-                        const int kk = len > 0 ? kb0 + min(tt, len - 1) : 0;
-                        const float4 x = S.pos[kk];
-                        const float rx = x.x - px, ry = x.y - py, rz = x.z - pz;
-                        dd[u] = tt < len ? rx * rx + ry * ry + rz * rz : INFINITY;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (dd[u] <= rho2) {
-                            S.queue[nq * 32 + lane] = (uint8_t)(kb0 + t + u);
-                            ++nq;
-                        }
-                    }
-                }
-                n_pairs += nq;
-
-                // ---- phase 2: the warp's queued pairs in owner-major order,
-                // split evenly over the lanes.  A lane accumulates locally
-                // while the owner stays the same and adds its sums into the
-                // owner's shared-memory slot when the owner changes.
-                int qinc = nq;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int u = __shfl_up_sync(FULL, qinc, o);
-                    if (lane >= o) qinc += u;
-                }
-                const int Q = __shfl_sync(FULL, qinc, 31);
-                S.own_off[lane] = qinc - nq;
-                S.own_nq[lane] = nq;
-                __syncwarp();
-                {
-                    const int share = (Q + 31) >> 5;
-                    int e = lane * share;
-                    const int e_end = min(e + share, Q);
-                    // owner of entry e: the last lane with a non-empty queue
-                    // starting at or before e
-                    int ow = 0;
-                    for (int l2 = 0; l2 < 32; ++l2)
-                        if (S.own_nq[l2] > 0 && S.own_off[l2] <= e) ow = l2;
-                    int q = e - S.own_off[ow];
-                    int ow_end = S.own_off[ow] + S.own_nq[ow];
-                    float4 od0 = S.own_data[ow * OWN_STRIDE + 0];
-                    float4 od1 = S.own_data[ow * OWN_STRIDE + 1];
-                    float4 od2 = S.own_data[ow * OWN_STRIDE + 2];
-                    float4 od3, od4, od5;
-                    if (MODE == PAIR_LINESEARCH) {
-                        od3 = S.own_data[ow * OWN_STRIDE + 3];
-                        od4 = S.own_data[ow * OWN_STRIDE + 4];
-                        od5 = S.own_data[ow * OWN_STRIDE + 5];
-                    }
-                    // this lane's range splits into owner segments: the first
-                    // is kept in fS until the range ends, segments wholly inside
-                    // the range belong to this lane alone and go straight to the
-                    // owner's sums, the last stays in t
-                    float t[10], fS[10];
-#pragma unroll
-                    for (int k = 0; k < 10; ++k) t[k] = fS[k] = 0.f;
-                    int seg = 0, f_owner = -1;
-                    while (e < e_end) {
-                        if (e >= ow_end) {
-                            if (MODE == PAIR_EVAL) {
-                                if (seg == 0) {
-                                    f_owner = ow;
-#pragma unroll
-                                    for (int k = 0; k < 10; ++k) fS[k] = t[k];
-                                } else {
-                                    float *dst = S.own_S + ow * PAIR_OWN_S;
-#pragma unroll
-                                    for (int k = 0; k < 10; ++k) dst[k] += t[k];
-                                }
-#pragma unroll
-                                for (int k = 0; k < 10; ++k) t[k] = 0.f;
-                            }
-                            ++seg;
-                            do {
-                                ++ow;
-                            } while (S.own_nq[ow] == 0);
-                            q = 0;
-                            ow_end = S.own_off[ow] + S.own_nq[ow];
-                            od0 = S.own_data[ow * OWN_STRIDE + 0];
-                            od1 = S.own_data[ow * OWN_STRIDE + 1];
-                            od2 = S.own_data[ow * OWN_STRIDE + 2];
-                            if (MODE == PAIR_LINESEARCH) {
-                                od3 = S.own_data[ow * OWN_STRIDE + 3];
-                                od4 = S.own_data[ow * OWN_STRIDE + 4];
-                                od5 = S.own_data[ow * OWN_STRIDE + 5];
-                            }
-                        }
-                        const int seg_end = min(e_end, ow_end);
-                        if (MODE == PAIR_EVAL && !ISO) {
-                            for (; e < seg_end; ++e, ++q) {
-                                const int k0 = S.queue[q * 32 + ow];
-                                pair_aniso<FD>(S.pos[k0], S.ca[k0], S.cb[k0], od0, od1, od2, c2, t, n_kept);
-                            }
-                            continue;
-                        }
-                        for (; e < seg_end; ++e, ++q) {
-                            const int k = S.queue[q * 32 + ow];
-                            const float4 x = S.pos[k];
-                            const float r0 = x.x - od0.x, r1 = x.y - od0.y, r2 = x.z - od0.z;
-                            float cij = x.w * od0.w;
-                            if (FD > 1) {
-                                const float4 b = S.cb[k];
-                                cij += b.z * od2.z + b.w * od2.w;
-                            }
-                            if (ISO) {
-                                const float d2 = (r0 * r0 + r1 * r1 + r2 * r2) * iso_inv;
-                                const bool keep = d2 <= c2;
-                                const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                                n_kept += keep;
-                                if (MODE == PAIR_EVAL) {
-                                    t[0] += wgt;
-                                    t[1] += wgt * r0;
-                                    t[2] += wgt * r1;
-                                    t[3] += wgt * r2;
-                                } else {
-                                    const float b1[3] = {od3.x, od3.y, od3.z}, b2[3] = {od3.w, od4.x, od4.y},
-                                                b3[3] = {od4.z, od4.w, od5.x}, b4[3] = {od5.y, od5.z, od5.w};
-                                    // A = I / ell^2
-                                    const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
-                                    const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
-                                    const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
-                                    const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
-                                    const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
-                                    const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
-                                    const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
-                                    const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
-                                    float be, ga, de, ep;
-                                    if (!a.ls_literal) {
-                                        be = -kr1;
-                                        ga = 0.5f * (kr2 - a11);
-                                        de = -kr3 * (1.f / 6.f) + 0.5f * a12;
-                                        ep = kr4 * (1.f / 24.f) - a13 * (1.f / 6.f) - a22 * 0.125f;
-                                    } else {
-                                        be = -kr1;
-                                        ga = -0.5f * a11 - kr2;
-                                        de = -a12 - kr3;
-                                        ep = -0.5f * (a22 + 2.f * a13 + 2.f * kr4);
-                                    }
-                                    Sf += wgt;
-                                    L1 += wgt * be;
-                                    L2 += wgt * (ga + 0.5f * be * be);
-                                    L3 += wgt * (de + be * ga + be * be * be * (1.f / 6.f));
-                                    L4 += wgt * (ep + be * de + 0.5f * be * be * ga + 0.5f * ga * ga +
-                                                 be * be * be * be * (1.f / 24.f));
-                                }
-                            } else {
-                                const float4 ca = S.ca[k];
-                                const float4 cbv = S.cb[k];
-                                const float s00 = ca.x + od1.x, s01 = ca.y + od1.y, s02 = ca.z + od1.z;
-                                const float s11 = ca.w + od1.w, s12 = cbv.x + od2.x, s22 = cbv.y + od2.y;
-                                const float c00 = s11 * s22 - s12 * s12;
-                                const float c01 = s02 * s12 - s01 * s22;
-                                const float c02 = s01 * s12 - s02 * s11;
-                                const float c11 = s00 * s22 - s02 * s02;
-                                const float c12 = s01 * s02 - s00 * s12;
-                                const float c22 = s00 * s11 - s01 * s01;
-                                const float det = s00 * c00 + s01 * c01 + s02 * c02;
-                                const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
-                                const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
-                                const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
-                                const float qf = r0 * y0 + r1 * y1 + r2 * y2;
-                                const float rdet = rcp_approx(det);
-                                const float d2 = qf * rdet;
-                                const bool keep = d2 <= c2;
-                                const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                                n_kept += keep;
-                                const float b1[3] = {od3.x, od3.y, od3.z}, b2[3] = {od3.w, od4.x, od4.y},
-                                            b3[3] = {od4.z, od4.w, od5.x}, b4[3] = {od5.y, od5.z, od5.w};
-                                // bilinear forms of A = adj / det with r and a_k
-                                const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
-                                const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
-                                const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
-                                const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
-                                const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
-                                const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
-                                const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
-                                const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
-                                const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
-                                const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
-                                const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
-                                const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
-                                const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
-                                const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
-                                float be, ga, de, ep;
-                                if (!a.ls_literal) {
-                                    be = -kr1;
-                                    ga = 0.5f * (kr2 - a11);
-                                    de = -kr3 * (1.f / 6.f) + 0.5f * a12;
-                                    ep = kr4 * (1.f / 24.f) - a13 * (1.f / 6.f) - a22 * 0.125f;
-                                } else {
-                                    be = -kr1;
-                                    ga = -0.5f * a11 - kr2;
-                                    de = -a12 - kr3;
-                                    ep = -0.5f * (a22 + 2.f * a13 + 2.f * kr4);
-                                }
-                                Sf += wgt;
-                                L1 += wgt * be;
-                                L2 += wgt * (ga + 0.5f * be * be);
-                                L3 += wgt * (de + be * ga + be * be * be * (1.f / 6.f));
-                                L4 += wgt * (ep + be * de + 0.5f * be * be * ga + 0.5f * ga * ga +
-                                             be * be * be * be * (1.f / 24.f));
-                            }
-                        }
-                    }
-                    if (MODE == PAIR_EVAL) {
-                        // first / last segment sums to per-lane slots in the
-                        // staging area (free once every lane is done with it),
-                        // then each owner adds the slots of the lanes that
-                        // covered its entries, in lane order
-                        __syncwarp();
-                        float *fslot = reinterpret_cast<float *>(S.pos);
-                        float *lslot = fslot + 32 * 10;
-                        int *fown = reinterpret_cast<int *>(lslot + 32 * 10);
-                        int *lown = fown + 32;
-                        const bool had = lane * share < Q;
-                        if (had && seg == 0) {
-#pragma unroll
-                            for (int k = 0; k < 10; ++k) fslot[lane * 10 + k] = t[k];
-                            fown[lane] = ow;
-                            lown[lane] = -1;
-                        } else if (had) {
-#pragma unroll
-                            for (int k = 0; k < 10; ++k) {
-                                fslot[lane * 10 + k] = fS[k];
-                                lslot[lane * 10 + k] = t[k];
-                            }
-                            fown[lane] = f_owner;
-                            lown[lane] = ow;
-                        } else {
-                            fown[lane] = -1;
-                            lown[lane] = -1;
-                        }
-                        __syncwarp();
-                        if (nq > 0) {
-                            const int off_me = S.own_off[lane];
-                            const int la = off_me / share, lb = (off_me + nq - 1) / share;
-                            float acc[10];
-#pragma unroll
-                            for (int k = 0; k < 10; ++k) acc[k] = 0.f;
-                            for (int l2 = la; l2 <= lb; ++l2) {
-                                if (fown[l2] == lane)
-#pragma unroll
-                                    for (int k = 0; k < 10; ++k) acc[k] += fslot[l2 * 10 + k];
-                                if (lown[l2] == lane)
-#pragma unroll
-                                    for (int k = 0; k < 10; ++k) acc[k] += lslot[l2 * 10 + k];
-                            }
-                            float *dst = S.own_S + lane * PAIR_OWN_S;
-#pragma unroll
-                            for (int k = 0; k < 10; ++k) dst[k] += acc[k];
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-
-        // ---- per-source-point epilogue and warp reduction
-        float v[PAIR_SLOTS];
-#pragma unroll
-        for (int k = 0; k < PAIR_SLOTS; ++k) v[k] = 0.f;
-        if (MODE == PAIR_EVAL) {
-            // this lane's point sums, assembled by the balanced phase 2
-            Sf = S.own_S[lane * PAIR_OWN_S + 0];
-            Su0 = S.own_S[lane * PAIR_OWN_S + 1];
-            Su1 = S.own_S[lane * PAIR_OWN_S + 2];
-            Su2 = S.own_S[lane * PAIR_OWN_S + 3];
-            A00 = S.own_S[lane * PAIR_OWN_S + 4];
-            A01 = S.own_S[lane * PAIR_OWN_S + 5];
-            A02 = S.own_S[lane * PAIR_OWN_S + 6];
-            A11 = S.own_S[lane * PAIR_OWN_S + 7];
-            A12 = S.own_S[lane * PAIR_OWN_S + 8];
-            A22 = S.own_S[lane * PAIR_OWN_S + 9];
-        }
-        if (MODE == PAIR_EVAL ? act : true) {
-            if (MODE == PAIR_EVAL) {
-                if (ISO) {
-                    Su0 *= iso_inv;
-                    Su1 *= iso_inv;
-                    Su2 *= iso_inv;
-                    A00 = A11 = A22 = Sf * iso_inv;
-                    A01 = A02 = A12 = 0.f;
-                }
-                v[0] = Sf;
-                // g_omega = -p x S_u, g_v = -S_u (Lemma 1)
-                v[1] = -(py * Su2 - pz * Su1);
-                v[2] = -(pz * Su0 - px * Su2);
-                v[3] = -(px * Su1 - py * Su0);
-                v[4] = -Su0;
-                v[5] = -Su1;
-                v[6] = -Su2;
-                // M = [[P^T S_A P, P S_A], [-S_A P, S_A]], P = p^ (Eq. 11 with J = [-p^, I])
-                float B00 = A01 * pz - A02 * py, B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
-                float B10 = A11 * pz - A12 * py, B11 = -A01 * pz + A12 * px, B12 = A01 * py - A11 * px;
-                float B20 = A12 * pz - A22 * py, B21 = -A02 * pz + A22 * px, B22 = A02 * py - A12 * px;
-                float W00 = pz * B10 - py * B20, W01 = pz * B11 - py * B21, W02 = pz * B12 - py * B22;
-                float W11 = -pz * B01 + px * B21, W12 = -pz * B02 + px * B22;
-                float W22 = py * B02 - px * B12;
-                float X00 = -pz * A01 + py * A02, X01 = -pz * A11 + py * A12, X02 = -pz * A12 + py * A22;
-                float X10 = pz * A00 - px * A02, X11 = pz * A01 - px * A12, X12 = pz * A02 - px * A22;
-                float X20 = -py * A00 + px * A01, X21 = -py * A01 + px * A11, X22 = -py * A02 + px * A12;
-                // upper triangle of M, row-major
-                v[7] = W00; v[8] = W01; v[9] = W02; v[10] = X00; v[11] = X01; v[12] = X02;
-                v[13] = W11; v[14] = W12; v[15] = X10; v[16] = X11; v[17] = X12;
-                v[18] = W22; v[19] = X20; v[20] = X21; v[21] = X22;
-                v[22] = A00; v[23] = A01; v[24] = A02;
-                v[25] = A11; v[26] = A12;
-                v[27] = A22;
-            } else {
-                v[0] = Sf;
-                v[1] = L1;
-                v[2] = L2;
-                v[3] = L3;
-                v[4] = L4;
-            }
-        }
-        const int nslot = MODE == PAIR_EVAL ? 28 : 5;
-        // compensated reduction over the lanes: transpose through shared
-        // memory (the staging area is free now), then lane k sums slot k
-        float *red = reinterpret_cast<float *>(S.pos);
-#pragma unroll
-        for (int k = 0; k < PAIR_SLOTS; ++k)
-            if (k < nslot) red[k * 33 + lane] = v[k];
-        __syncwarp();
-        float *out = a.part + (size_t)it * 64;
-        if (lane < nslot) {
-            float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) {
-                float x = red[lane * 33 + i];
-                float sm = hi + x;
-                float bp = sm - hi;
-                lo += (hi - (sm - bp)) + (x - bp);
-                hi = sm;
-            }
-            out[lane] = hi;
-            out[32 + lane] = lo;
-        }
-        int tp = __reduce_add_sync(0xffffffffu, n_pairs);
-        int tk = __reduce_add_sync(0xffffffffu, n_kept);
-        int tc = __reduce_add_sync(0xffffffffu, n_cand);
-        if (lane == 0) {
-            long long *cnts = a.counts + (size_t)it * 4;
-            cnts[0] = tp;
-            cnts[1] = tk;
-            cnts[2] = tc;
-        }
-        __syncwarp();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // FP64 finalize, one block per problem.
@@ -1380,6 +587,7 @@ __global__ void k_src_groups(SrcArgs a, const unsigned long long *keys, const in
         atomicMax(pg1 + p, g + 1);
     }
     atomicAdd(gcount + g, 1);
+    a.pgroup[i] = g;
     // packed source record in group order
     int src = a.vals[i];
     const SrcDesc d = a.desc[a.prob_of[src]];
@@ -1396,96 +604,11 @@ __global__ void k_src_groups(SrcArgs a, const unsigned long long *keys, const in
     a.scb[i] = make_float4(s[4], s[5], f1, f2);
 }
 
-__global__ void k_pack(int pass, int np, const int *gstart, const int *gcount, const int *pg0, const int *pg1,
-                       int *cnt, const int *incl, int4 *items, int *item_prob, int *pw0, int *pw1) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    int g0 = pg0[p], g1 = pg1[p];
-    int out = pass ? incl[p] - cnt[p] : 0;
-    if (pass) pw0[p] = out;
-    int n = 0, first = g0, pts = 0, ng = 0;
-    for (int g = g0; g < g1; ++g) {
-        int c = gcount[g];
-        if (ng > 0 && (pts + c > 32 || ng == PAIR_MAX_SUB)) {
-            if (pass) {
-                items[out + n] = make_int4(first, ng, gstart[first], pts);
-                item_prob[out + n] = p;
-            }
-            ++n;
-            first = g;
-            pts = 0;
-            ng = 0;
-        }
-        pts += c;
-        ++ng;
-    }
-    if (ng > 0) {
-        if (pass) {
-            items[out + n] = make_int4(first, ng, gstart[first], pts);
-            item_prob[out + n] = p;
-        }
-        ++n;
-    }
-    if (pass) pw1[p] = out + n;
-    else cnt[p] = n;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-size_t pair_smem_bytes(int mode) { return (size_t)PAIR_WARPS * pair_warp_smem(mode); }
-
-template <int MODE, bool ISO, int FD>
-static cudaError_t launch_pair_t(const PairArgs &a, int grid, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_pair<MODE, ISO, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pair_smem_bytes(MODE));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    k_pair<MODE, ISO, FD><<<grid, PAIR_WARPS * 32, pair_smem_bytes(MODE), s>>>(a);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template <int MODE, bool ISO, int FD>
-static int occupancy_t() {
-    int nb = 0;
-    cudaFuncSetAttribute(k_pair<MODE, ISO, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes(MODE));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<MODE, ISO, FD>, PAIR_WARPS * 32, pair_smem_bytes(MODE));
-    return nb;
-}
-
-int pair_blocks_per_sm(int mode, bool iso, int fd) {
-#define OCC(M, I, F) if (mode == M && iso == I && (fd > 1) == (F > 1)) return occupancy_t<M, I, F>();
-    OCC(PAIR_EVAL, false, 1) OCC(PAIR_EVAL, false, 3) OCC(PAIR_EVAL, true, 1) OCC(PAIR_EVAL, true, 3)
-    OCC(PAIR_LINESEARCH, false, 1) OCC(PAIR_LINESEARCH, false, 3) OCC(PAIR_LINESEARCH, true, 1)
-    OCC(PAIR_LINESEARCH, true, 3)
-#undef OCC
-    return 1;
-}
-
-cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int grid, cudaStream_t s) {
-#define L(M, I, F) if (mode == M && iso == I && (fd > 1) == (F > 1)) return launch_pair_t<M, I, F>(a, grid, s);
-    L(PAIR_EVAL, false, 1) L(PAIR_EVAL, false, 3) L(PAIR_EVAL, true, 1) L(PAIR_EVAL, true, 3)
-    L(PAIR_LINESEARCH, false, 1) L(PAIR_LINESEARCH, false, 3) L(PAIR_LINESEARCH, true, 1)
-    L(PAIR_LINESEARCH, true, 3)
-#undef L
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_pack(int pass, int np, const int *gstart, const int *gcount, const int *pg0, const int *pg1,
-                        int *cnt, const int *incl, int4 *items, int *item_prob, int *pw0, int *pw1,
-                        cudaStream_t s) {
-    k_pack<<<(np + 127) / 128, 128, 0, s>>>(pass, np, gstart, gcount, pg0, pg1, cnt, incl, items, item_prob, pw0,
-                                            pw1);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
     k_finalize<<<a.n_problems, 256, 0, s>>>(a);
     count_launches(1);

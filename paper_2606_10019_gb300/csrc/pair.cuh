@@ -5,16 +5,14 @@
 
 namespace gcvo {
 
-// Pair-kernel tiling: warps per block, points staged per warp and chunk,
-// spatial groups per warp item, per-lane owner sums and owner data (float4s).
+// Pair-kernel tiling (tile.cu): a block of PAIR_WARPS warps takes one work
+// item of PAIR_ITEM source points, split into sub-tiles of 8, 16 or 32
+// points (the schedule: 4, 2 or 1 lanes per point).  Target points are
+// staged PAIR_CAP at a time.
 constexpr int PAIR_WARPS = 4;
-constexpr int PAIR_CAP = 96;                       // <= 256 (uint8 queue entries)
-constexpr int PAIR_MAX_SUB = 16;
-constexpr int PAIR_OWN_S = 12;                     // 10 sums, padded
+constexpr int PAIR_ITEM = 32;
+constexpr int PAIR_CAP = 512;
 constexpr int PAIR_SLOTS = 28;
-__host__ __device__ constexpr int pair_warp_smem(int mode) {
-    return PAIR_CAP * 80 + 16 + PAIR_MAX_SUB * 8 + 64 * 4 + 32 * PAIR_OWN_S * 4 + 32 * 16 * (mode == 0 ? 3 : 6);
-}
 
 enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1 };
 enum FinMode { FIN_EVAL = 0, FIN_GN = 1, FIN_GRAD = 2, FIN_LINESEARCH = 3, FIN_ANCHORS = 4 };
@@ -43,15 +41,16 @@ struct EvalOut {
 struct PairArgs {
     const float4 *spos, *sca, *scb;
     const float4 *anchor;      // per group: R^T (z_g - t) - o, z_g its first point
-    const int *gstart;
-    const int4 *items;          // first group, groups, first point, points
+    const int *gstart;         // first point of each group
+    const int *pgroup;         // group of each point
+    const int4 *items;         // (0, 0, first point, points <= PAIR_ITEM)
     const int *item_prob;
     const int *n_items;
     const ProbDev *probs;
     const GridDev *grids;
-    float *part;               // n_groups x 64 (hi[32], lo[32])
-    long long *counts;         // n_groups x 4
-    int *work;                 // dynamic group counter (zeroed before launch)
+    float *part;               // n_items x 64 (hi[32], lo[32])
+    long long *counts;         // n_items x 4
+    int *work;                 // dynamic item counter (zeroed before launch)
     unsigned *status_word;
     int ls_literal;
 };
@@ -86,24 +85,26 @@ struct SrcArgs {
     int *lam_enc;
     unsigned *status_word;
     float4 *spos, *sca, *scb;
+    int *pgroup;
     int feat_dim;
     int iso;
 };
 
 size_t pair_smem_bytes(int mode);
-int pair_blocks_per_sm(int mode, bool iso, int fd);
-cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int grid, cudaStream_t s);
+// sub: points per sub-tile (8, 16, 32); the line-search pass uses 8.
+int pair_sub_for(int mode, int sub);
+int pair_blocks_per_sm(int mode, bool iso, int fd, int sub);
+cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
 cudaError_t launch_src_keys(const SrcArgs &a, int n_problems, int64_t max_n, cudaStream_t s);
 cudaError_t launch_src_segments(const unsigned long long *keys, int64_t n, int *seg, cudaStream_t s);
 cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStream_t s);
 cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
                               int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s);
-// Greedy packing of consecutive groups of one problem into warp items of at
-// most 32 points and PAIR_MAX_SUB groups.  pass 0 counts items per problem
-// into cnt; pass 1 writes them at offsets incl - cnt (incl = inclusive scan).
-cudaError_t launch_pack(int pass, int np, const int *gstart, const int *gcount, const int *pg0, const int *pg1,
-                        int *cnt, const int *incl, int4 *items, int *item_prob, int *pw0, int *pw1,
-                        cudaStream_t s);
+// Work items of PAIR_ITEM consecutive (sorted) source points per problem:
+// problem p owns items [w0[p], w0[p] + ceil(n[p] / PAIR_ITEM)) and its points
+// start at point_off[p].
+cudaError_t launch_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items,
+                         int4 *items, int *item_prob, cudaStream_t s);
 
 }  // namespace gcvo

@@ -1,0 +1,675 @@
+// The pair kernel: one evaluation of f (Eq. 5), g (Lemma 1, Eq. 8) and the
+// Gauss-Newton matrix M (Eq. 11) -- or, for G-CVO-1, the line-search
+// polynomial of Eq. (9) / Appendix B -- over every (target, source) pair of
+// every active problem within the Euclidean radius rho.
+//
+// A block of PAIR_WARPS warps takes one work item: PAIR_ITEM consecutive
+// source points of one problem in Morton order.
+//  1. Every point is moved into the target grid's frame with T^-1
+//     (Algorithm 1): p_j - o = R^T (z_j - z_g) + a_g, where a_g =
+//     R^T (z_g - t) - o is its group's anchor, computed in FP64 by the
+//     finalize; Sigma'_j = R^T Sigma_j R.
+//  2. The voxel columns (cx, cy) that meet the item's bounding box grown by
+//     rho are listed, one per thread.  The occupied voxels of one column over
+//     the needed cz range are contiguous in the grid's sorted order, so each
+//     column is one run of target points.  The runs are staged into shared
+//     memory PAIR_CAP points at a time by cp.async.bulk copies completing on
+//     an mbarrier.
+//  3. The item splits into sub-tiles of SUB points (SUB = 8, 16 or 32: 4, 2
+//     or 1 lanes per point, the schedule the autotuner picks); SUB / 8 warps
+//     share a sub-tile.  A warp holds its sub-tile's points one per lane of
+//     each group of SUB lanes, keeps the staged targets that lie within rho
+//     of the sub-tile's box (one test per target) and walks them 32 / SUB at
+//     a time: lane (q, i) pairs target q of the step with point i.  A target
+//     is read by SUB lanes at once (a broadcast), a point stays in
+//     registers, and no lane waits on another's branch.
+//  4. Per pair (Eq. 7): Sigma_ij = Sigma_i + Sigma'_j, its adjugate and
+//     determinant, d^2 = r^T Sigma_ij^-1 r, w = c_ij sigma^2 exp(-d^2 / 2)
+//     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
+//       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1.
+//  5. Per point, after the lanes and warps that share it are added: f += S_f,
+//     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the block adds
+//     its points' 28 values with compensated (TwoSum) FP32 sums and writes
+//     one (hi, lo) partial per item for the FP64 finalize.
+// With no cutoff (dense mode) rho and the cutoff are infinite and every
+// staged target meets every point: the same code visits all pairs.
+#include "common.cuh"
+#include "pair.cuh"
+#include "ptx.cuh"
+
+namespace gcvo {
+namespace {
+
+static_assert(PAIR_ITEM == 32 && PAIR_WARPS == 4, "an item is 32 points over 4 warps");
+static_assert(PAIR_CAP <= 65535, "target list entries are 16-bit");
+static_assert(PAIR_WARPS * PAIR_SLOTS * 33 * 4 <= PAIR_CAP * 32, "epilogue transposes fit in the staged ca, cb");
+static_assert(PAIR_WARPS * 32 * 10 * 4 <= PAIR_CAP * 16, "per-warp point sums fit in the staged pos");
+
+struct __align__(16) TileSmem {
+    float4 pos[PAIR_CAP];
+    float4 ca[PAIR_CAP];
+    float4 cb[PAIR_CAP];
+    unsigned short list[PAIR_WARPS][PAIR_CAP];   // per warp: staged targets near its sub-tile
+    float red[PAIR_WARPS][PAIR_SLOTS][2];        // per warp: (hi, lo) of each slot
+    float box[PAIR_WARPS][6];                    // per warp: sub-tile bounding box
+    long long cnt[PAIR_WARPS][3];
+    int scan[PAIR_WARPS];
+    uint64_t bar;
+    int item;
+};
+
+// One anisotropic pair (Eq. 7) into the lane sums t[10].
+template <int FD>
+__device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, const float4 cbv, float px, float py,
+                                           float pz, float l0, float l1, float l2, const float q[6], float rho2,
+                                           float c2, bool act, float *t, int &n_pairs, int &n_kept) {
+    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+    const bool in = act && rr <= rho2;
+    float cij = x.w * l0;
+    if (FD > 1) cij += cbv.z * l1 + cbv.w * l2;
+    const float s00 = ca.x + q[0], s01 = ca.y + q[1], s02 = ca.z + q[2];
+    const float s11 = ca.w + q[3], s12 = cbv.x + q[4], s22 = cbv.y + q[5];
+    const float c00 = s11 * s22 - s12 * s12;
+    const float c01 = s02 * s12 - s01 * s22;
+    const float c02 = s01 * s12 - s02 * s11;
+    const float c11 = s00 * s22 - s02 * s02;
+    const float c12 = s01 * s02 - s00 * s12;
+    const float c22 = s00 * s11 - s01 * s01;
+    const float det = s00 * c00 + s01 * c01 + s02 * c02;
+    const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+    const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+    const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+    const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+    const float rdet = rcp_approx(det);
+    const float d2 = qf * rdet;
+    const bool keep = in && d2 <= c2;
+    const float wgt = cij * ex2_approx(d2 * NEG_HALF_LOG2E);
+    const float wd = keep ? wgt * rdet : 0.f;
+    n_pairs += in;
+    n_kept += keep;
+    t[0] += keep ? wgt : 0.f;
+    t[1] += wd * y0;
+    t[2] += wd * y1;
+    t[3] += wd * y2;
+    t[4] += wd * c00;
+    t[5] += wd * c01;
+    t[6] += wd * c02;
+    t[7] += wd * c11;
+    t[8] += wd * c12;
+    t[9] += wd * c22;
+}
+
+// Line-search sums of one pair (Appendix B): with beta, gamma, delta, eps the
+// coefficients of the exponent's expansion along t xi, the kernel value
+// w e^(beta t + gamma t^2 + ...) contributes w * (1, beta, gamma + beta^2/2,
+// ...) to (S_f, L1, L2, L3, L4).
+__device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float kr3, float kr4, float a11, float a12,
+                                         float a13, float a22, int literal, float *t) {
+    float be, ga, de, ep;
+    if (!literal) {
+        be = -kr1;
+        ga = 0.5f * (kr2 - a11);
+        de = -kr3 * (1.f / 6.f) + 0.5f * a12;
+        ep = kr4 * (1.f / 24.f) - a13 * (1.f / 6.f) - a22 * 0.125f;
+    } else {
+        be = -kr1;
+        ga = -0.5f * a11 - kr2;
+        de = -a12 - kr3;
+        ep = -0.5f * (a22 + 2.f * a13 + 2.f * kr4);
+    }
+    t[0] += wgt;
+    t[1] += wgt * be;
+    t[2] += wgt * (ga + 0.5f * be * be);
+    t[3] += wgt * (de + be * ga + be * be * be * (1.f / 6.f));
+    t[4] += wgt * (ep + be * de + 0.5f * be * be * ga + 0.5f * ga * ga + be * be * be * be * (1.f / 24.f));
+}
+
+template <int MODE, bool ISO, int FD, int SUB>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
+    static_assert(SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 8, 16 or 32 points");
+    constexpr int TQ = 32 / SUB;    // targets per warp step
+    constexpr int WPS = SUB / 8;    // warps per sub-tile
+    constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
+    constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
+    __shared__ TileSmem S;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int qi = lane / SUB, si = lane % SUB;
+    const int st = w / WPS, wr = w % WPS;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (tid == 0) mbar_init(&S.bar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    const int n_items = *a.n_items;
+
+    for (;;) {
+        if (tid == 0) S.item = atomicAdd(a.work, 1);
+        __syncthreads();
+        const int it = S.item;
+        if (it >= n_items) break;
+        const int prob = a.item_prob[it];
+        const ProbDev *P = a.probs + prob;
+        if (P->status != 0) {
+            // skip the rest of this finished problem's items in one step
+            if (tid == 0) atomicMax(a.work, P->w1);
+            __syncthreads();
+            continue;
+        }
+        const GridDev *G = a.grids + prob;
+        const int4 item = a.items[it];
+        const int j0 = item.z, cnt = item.w;
+        const int sj = st * SUB + si;
+        const bool sval = sj < cnt;
+
+        // ---- 1. the lane's source point in the grid frame
+        float Rf[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
+        const int jj = j0 + (sval ? sj : 0);
+        const int grp = a.pgroup[jj];
+        const float4 anc = a.anchor[grp];
+        const float4 zg = a.spos[a.gstart[grp]];
+        const float4 z = a.spos[jj];
+        const float4 zb = a.scb[jj];
+        const float e0 = z.x - zg.x, e1 = z.y - zg.y, e2 = z.z - zg.z;
+        const float px = anc.x + (Rf[0] * e0 + Rf[3] * e1 + Rf[6] * e2);
+        const float py = anc.y + (Rf[1] * e0 + Rf[4] * e1 + Rf[7] * e2);
+        const float pz = anc.z + (Rf[2] * e0 + Rf[5] * e1 + Rf[8] * e2);
+        float qv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Sigma'_j = R^T Sigma_j R
+        if (!ISO) {
+            const float4 za = a.sca[jj];
+            const float sm[9] = {za.x, za.y, za.z, za.y, za.w, zb.x, za.z, zb.x, zb.y};
+            float T1[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    T1[3 * r + c] = sm[3 * r] * Rf[c] + sm[3 * r + 1] * Rf[3 + c] + sm[3 * r + 2] * Rf[6 + c];
+            qv[0] = Rf[0] * T1[0] + Rf[3] * T1[3] + Rf[6] * T1[6];
+            qv[1] = Rf[0] * T1[1] + Rf[3] * T1[4] + Rf[6] * T1[7];
+            qv[2] = Rf[0] * T1[2] + Rf[3] * T1[5] + Rf[6] * T1[8];
+            qv[3] = Rf[1] * T1[1] + Rf[4] * T1[4] + Rf[7] * T1[7];
+            qv[4] = Rf[1] * T1[2] + Rf[4] * T1[5] + Rf[7] * T1[8];
+            qv[5] = Rf[2] * T1[2] + Rf[5] * T1[5] + Rf[8] * T1[8];
+        }
+        const float sg = P->sigma2;
+        const float l0 = sg * z.w;
+        const float l1 = FD > 1 ? sg * zb.z : 0.f;
+        const float l2 = FD > 1 ? sg * zb.w : 0.f;
+        const float rho2 = P->rho2, c2 = P->c2, iso_inv = P->iso_inv;
+
+        // G-CVO-1 second pass: a_k = (xi^)^k p, xi the search direction
+        float b1[3], b2[3], b3[3], b4[3];
+        if (MODE == PAIR_LINESEARCH) {
+            const float om0 = P->dir32[0], om1 = P->dir32[1], om2 = P->dir32[2];
+            b1[0] = om1 * pz - om2 * py + P->dir32[3];
+            b1[1] = om2 * px - om0 * pz + P->dir32[4];
+            b1[2] = om0 * py - om1 * px + P->dir32[5];
+#define CROSS_W(dst, src)                 \
+    dst[0] = om1 * src[2] - om2 * src[1]; \
+    dst[1] = om2 * src[0] - om0 * src[2]; \
+    dst[2] = om0 * src[1] - om1 * src[0];
+            CROSS_W(b2, b1)
+            CROSS_W(b3, b2)
+            CROSS_W(b4, b3)
+#undef CROSS_W
+        }
+
+        // ---- bounding boxes: the warp's sub-tile, then the whole item
+        float wmin[3], wmax[3];
+        {
+            const float pp[3] = {px, py, pz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                wmin[k] = ord_dec(__reduce_min_sync(FULL, ord_enc(sval ? pp[k] : INFINITY)));
+                wmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                S.box[w][k] = wmin[k];
+                S.box[w][3 + k] = wmax[k];
+            }
+        __syncthreads();
+        float bmin[3], bmax[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            bmin[k] = S.box[0][k];
+            bmax[k] = S.box[0][3 + k];
+#pragma unroll
+            for (int v = 1; v < PAIR_WARPS; ++v) {
+                bmin[k] = fminf(bmin[k], S.box[v][k]);
+                bmax[k] = fmaxf(bmax[k], S.box[v][3 + k]);
+            }
+        }
+        const float rho = sqrtf(rho2);
+        const float h = G->h, ih = G->inv_h;
+        // culling radius: rho plus a margin for the float voxel assignment
+        const float rc = rho * 1.0001f + 1e-5f * h;
+        const float rc2 = rc * rc;
+        int lo[3], hi[3];
+        bool empty = !(bmin[0] <= bmax[0]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float fl = floorf((bmin[k] - rc - G->corner[k]) * ih);
+            float fh = floorf((bmax[k] + rc - G->corner[k]) * ih);
+            fl = fminf(fmaxf(fl, 0.0f), (float)G->dims[k]);
+            fh = fmaxf(fminf(fh, (float)(G->dims[k] - 1)), -1.0f);
+            if (!(fl <= fh)) empty = true;
+            lo[k] = empty ? 0 : (int)fl;
+            hi[k] = empty ? -1 : (int)fh;
+        }
+        const int ncy = empty ? 0 : hi[1] - lo[1] + 1;
+        const int n_cols = empty ? 0 : (hi[0] - lo[0] + 1) * ncy;
+
+        float t[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) t[k] = 0.f;
+        int n_pairs = 0, n_kept = 0;
+        long long n_cand = 0;
+        const int dy = G->dims[1], dzs = G->dims[2];
+
+        for (int cb0 = 0; cb0 < n_cols; cb0 += PAIR_WARPS * 32) {
+            // ---- 2. one column per thread: its run of target points.  A
+            // column is kept when its xy rectangle lies within rho of the
+            // item box; its cz range shrinks with that distance.
+            const int c = cb0 + tid;
+            int rs = 0, rl = 0;
+            if (c < n_cols) {
+                const int cx = lo[0] + c / ncy, cy = lo[1] + c % ncy;
+                const float x0 = G->corner[0] + (float)cx * h, y0 = G->corner[1] + (float)cy * h;
+                const float ddx = fmaxf(0.0f, fmaxf(x0 - bmax[0], bmin[0] - (x0 + h)));
+                const float ddy = fmaxf(0.0f, fmaxf(y0 - bmax[1], bmin[1] - (y0 + h)));
+                const float d2xy = ddx * ddx + ddy * ddy;
+                if (d2xy <= rc2) {
+                    const float ez = sqrtf(rc2 - d2xy);
+                    const int czl = max(lo[2], (int)floorf(fmaxf((bmin[2] - ez - G->corner[2]) * ih, -1.0f)));
+                    const int czh = min(hi[2], (int)floorf(fminf((bmax[2] + ez - G->corner[2]) * ih, (float)dzs)));
+                    const int2 cr = G->col_range[cx * dy + cy];
+                    // the column's voxels are sorted by cz: first with cz >= czl
+                    int l = cr.x, u = cr.y;
+                    while (l < u) {
+                        const int m = (l + u) >> 1;
+                        if (__ldg(G->cell_z + m) < czl) l = m + 1;
+                        else u = m;
+                    }
+                    const int first = l;
+                    u = cr.y;
+                    while (l < u) {   // first with cz > czh
+                        const int m = (l + u) >> 1;
+                        if (__ldg(G->cell_z + m) <= czh) l = m + 1;
+                        else u = m;
+                    }
+                    if (l > first) {
+                        rs = __ldg(G->cell_start + first);
+                        rl = __ldg(G->cell_start + l) - rs;
+                    }
+                }
+            }
+            // exclusive block offsets of the runs
+            int incl = rl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) S.scan[w] = incl;
+            __syncthreads();
+            int total = 0, wofs = 0;
+#pragma unroll
+            for (int v = 0; v < PAIR_WARPS; ++v) {
+                const int sv = S.scan[v];
+                wofs += v < w ? sv : 0;
+                total += sv;
+            }
+            const int off = wofs + incl - rl;
+
+            for (int base = 0; base < total; base += PAIR_CAP) {
+                const int m = min(PAIR_CAP, total - base);
+                // ---- stage the chunk [base, base + m) (bulk copies)
+                fence_proxy_async_smem();
+                __syncthreads();   // everyone is done with the previous chunk
+                if (tid == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * 48u);
+                __syncthreads();
+                {
+                    const int s0 = max(off, base), s1 = min(off + rl, base + m);
+                    if (s1 > s0) {
+                        const int src = rs + (s0 - off), dst = s0 - base;
+                        const unsigned bytes = (unsigned)(s1 - s0) * 16u;
+                        bulk_g2s(S.pos + dst, G->pos + src, bytes, &S.bar);
+                        bulk_g2s(S.ca + dst, G->ca + src, bytes, &S.bar);
+                        bulk_g2s(S.cb + dst, G->cb + src, bytes, &S.bar);
+                    }
+                }
+                {
+                    // bounded wait; the exit decision is block-uniform
+                    int spin = 0;
+                    bool all_done;
+                    for (;;) {
+                        all_done = __syncthreads_and(mbar_try_wait(&S.bar, parity)) != 0;
+                        if (all_done || ++spin > (1 << 20)) break;
+                    }
+                    if (!all_done) {
+                        if (tid == 0) atomicOr(a.status_word, DEV_ERR_TIMEOUT);
+                        return;
+                    }
+                    parity ^= 1u;
+                }
+
+                // ---- 3. the staged targets within rho of the sub-tile box
+                int L = 0;
+                for (int t0 = 0; t0 < m; t0 += 32) {
+                    const int tt = t0 + lane;
+                    bool hit = false;
+                    if (tt < m) {
+                        const float4 x = S.pos[tt];
+                        const float dx = fmaxf(0.f, fmaxf(wmin[0] - x.x, x.x - wmax[0]));
+                        const float dyy = fmaxf(0.f, fmaxf(wmin[1] - x.y, x.y - wmax[1]));
+                        const float dz = fmaxf(0.f, fmaxf(wmin[2] - x.z, x.z - wmax[2]));
+                        hit = dx * dx + dyy * dyy + dz * dz <= rc2;
+                    }
+                    const unsigned bal = __ballot_sync(FULL, hit);
+                    if (hit) S.list[w][L + __popc(bal & lt_mask)] = (unsigned short)tt;
+                    L += __popc(bal);
+                }
+                __syncwarp();
+                if (wr == 0 && qi == 0 && sval) n_cand += L;
+
+                // ---- 4. TQ targets per warp step, one per group of lanes;
+                // the WPS warps of a sub-tile take interleaved steps
+                for (int j = wr * TQ; j < L; j += TQ * WPS) {
+                    const int idx = j + qi;
+                    const bool act = sval && idx < L;
+                    const int k = S.list[w][min(idx, L - 1)];
+                    const float4 x = S.pos[k];
+                    if (MODE == PAIR_EVAL && !ISO) {
+                        pair_aniso<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                                       n_kept);
+                        continue;
+                    }
+                    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+                    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                    const bool in = act && rr <= rho2;
+                    float cij = x.w * l0;
+                    if (FD > 1) {
+                        const float4 cbv = S.cb[k];
+                        cij += cbv.z * l1 + cbv.w * l2;
+                    }
+                    if (ISO) {
+                        const float d2 = rr * iso_inv;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        if (MODE == PAIR_EVAL) {
+                            t[0] += wgt;
+                            t[1] += wgt * r0;
+                            t[2] += wgt * r1;
+                            t[3] += wgt * r2;
+                        } else {
+                            // A = I / ell^2
+                            const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
+                            const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
+                            const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
+                            const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
+                            const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
+                            const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
+                            const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
+                            const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
+                            ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
+                        }
+                    } else {
+                        // anisotropic line search (MODE == PAIR_LINESEARCH)
+                        const float4 ca = S.ca[k];
+                        const float4 cbv = S.cb[k];
+                        const float s00 = ca.x + qv[0], s01 = ca.y + qv[1], s02 = ca.z + qv[2];
+                        const float s11 = ca.w + qv[3], s12 = cbv.x + qv[4], s22 = cbv.y + qv[5];
+                        const float c00 = s11 * s22 - s12 * s12;
+                        const float c01 = s02 * s12 - s01 * s22;
+                        const float c02 = s01 * s12 - s02 * s11;
+                        const float c11 = s00 * s22 - s02 * s02;
+                        const float c12 = s01 * s02 - s00 * s12;
+                        const float c22 = s00 * s11 - s01 * s01;
+                        const float det = s00 * c00 + s01 * c01 + s02 * c02;
+                        const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+                        const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+                        const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+                        const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+                        const float rdet = rcp_approx(det);
+                        const float d2 = qf * rdet;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        // bilinear forms of A = adj / det with r and a_k
+                        const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
+                        const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
+                        const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
+                        const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
+                        const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
+                        const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
+                        const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
+                        const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
+                        const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
+                        const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
+                        const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
+                        const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
+                        const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
+                        const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
+                        ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
+                    }
+                }
+            }
+            __syncthreads();   // S.scan is rewritten by the next column batch
+        }
+
+        // ---- 5. per point: add the TQ lanes that share it, then (in warp
+        // order, through the free staging area) the WPS warps
+#pragma unroll
+        for (int k = 0; k < NT; ++k)
+#pragma unroll
+            for (int o = SUB; o < 32; o <<= 1) t[k] += __shfl_xor_sync(FULL, t[k], o);
+        if (WPS > 1) {
+            float *acc = reinterpret_cast<float *>(S.pos);
+            if (qi == 0)
+#pragma unroll
+                for (int k = 0; k < NT; ++k) acc[(w * 32 + si) * NT + k] = t[k];
+            __syncthreads();
+            if (wr == 0 && qi == 0)
+#pragma unroll
+                for (int k = 0; k < NT; ++k) {
+                    float x = acc[(w * 32 + si) * NT + k];
+#pragma unroll
+                    for (int r = 1; r < WPS; ++r) x += acc[((w + r) * 32 + si) * NT + k];
+                    t[k] = x;
+                }
+        }
+        float v[NSLOT];
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) v[k] = 0.f;
+        if (wr == 0 && qi == 0 && sval) {
+            if (MODE == PAIR_EVAL) {
+                float Sf = t[0], Su0 = t[1], Su1 = t[2], Su2 = t[3];
+                float A00 = t[4], A01 = t[5], A02 = t[6], A11 = t[7], A12 = t[8], A22 = t[9];
+                if (ISO) {
+                    Su0 *= iso_inv;
+                    Su1 *= iso_inv;
+                    Su2 *= iso_inv;
+                    A00 = A11 = A22 = Sf * iso_inv;
+                    A01 = A02 = A12 = 0.f;
+                }
+                v[0] = Sf;
+                // g_omega = -p x S_u, g_v = -S_u (Lemma 1)
+                v[1] = -(py * Su2 - pz * Su1);
+                v[2] = -(pz * Su0 - px * Su2);
+                v[3] = -(px * Su1 - py * Su0);
+                v[4] = -Su0;
+                v[5] = -Su1;
+                v[6] = -Su2;
+                // M = [[P^T S_A P, P S_A], [-S_A P, S_A]], P = p^ (Eq. 11 with J = [-p^, I])
+                const float B00 = A01 * pz - A02 * py, B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
+                const float B10 = A11 * pz - A12 * py, B11 = -A01 * pz + A12 * px, B12 = A01 * py - A11 * px;
+                const float B20 = A12 * pz - A22 * py, B21 = -A02 * pz + A22 * px, B22 = A02 * py - A12 * px;
+                (void)B00;
+                v[7] = pz * B10 - py * B20;
+                v[8] = pz * B11 - py * B21;
+                v[9] = pz * B12 - py * B22;
+                v[10] = -pz * A01 + py * A02;
+                v[11] = -pz * A11 + py * A12;
+                v[12] = -pz * A12 + py * A22;
+                v[13] = -pz * B01 + px * B21;
+                v[14] = -pz * B02 + px * B22;
+                v[15] = pz * A00 - px * A02;
+                v[16] = pz * A01 - px * A12;
+                v[17] = pz * A02 - px * A22;
+                v[18] = py * B02 - px * B12;
+                v[19] = -py * A00 + px * A01;
+                v[20] = -py * A01 + px * A11;
+                v[21] = -py * A02 + px * A12;
+                v[22] = A00;
+                v[23] = A01;
+                v[24] = A02;
+                v[25] = A11;
+                v[26] = A12;
+                v[27] = A22;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) v[k] = t[k];
+            }
+        }
+        // compensated sums over the sub-tile's points: transpose through the
+        // free staging area, lane k adds slot k
+        float *tr = reinterpret_cast<float *>(S.ca) + w * PAIR_SLOTS * 33;
+        __syncwarp();
+        if (qi == 0)
+#pragma unroll
+            for (int k = 0; k < NSLOT; ++k) tr[k * (SUB + 1) + si] = v[k];
+        __syncwarp();
+        if (lane < NSLOT) {
+            float hs = 0.f, ls = 0.f;
+#pragma unroll
+            for (int i2 = 0; i2 < SUB; ++i2) {
+                const float x = tr[lane * (SUB + 1) + i2];
+                const float sm = hs + x;
+                const float bp = sm - hs;
+                ls += (hs - (sm - bp)) + (x - bp);
+                hs = sm;
+            }
+            S.red[w][lane][0] = hs;
+            S.red[w][lane][1] = ls;
+        }
+        {
+            const int tp = __reduce_add_sync(FULL, n_pairs);
+            const int tk = __reduce_add_sync(FULL, n_kept);
+            const long long tc = (long long)__reduce_add_sync(FULL, (unsigned)n_cand);
+            if (lane == 0) {
+                S.cnt[w][0] = tp;
+                S.cnt[w][1] = tk;
+                S.cnt[w][2] = tc;
+            }
+        }
+        __syncthreads();
+        if (w == 0) {
+            float *out = a.part + (size_t)it * 64;
+            if (lane < NSLOT) {
+                float hs = S.red[0][lane][0], ls = S.red[0][lane][1];
+#pragma unroll
+                for (int v2 = 1; v2 < PAIR_WARPS; ++v2) {
+                    const float x = S.red[v2][lane][0];
+                    const float sm = hs + x;
+                    const float bp = sm - hs;
+                    ls += (hs - (sm - bp)) + (x - bp) + S.red[v2][lane][1];
+                    hs = sm;
+                }
+                out[lane] = hs;
+                out[32 + lane] = ls;
+            }
+            if (lane < 3) {
+                long long s2 = 0;
+#pragma unroll
+                for (int v2 = 0; v2 < PAIR_WARPS; ++v2) s2 += S.cnt[v2][lane];
+                a.counts[(size_t)it * 4 + lane] = s2;
+            }
+        }
+        // S.red / S.cnt are rewritten only after the next item's first
+        // barrier, S.item only after this one
+        __syncthreads();
+    }
+}
+
+__global__ void k_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items, int4 *items,
+                        int *item_prob) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    // the problem whose item range holds it: last p with w0[p] <= it
+    int l = 0, u = np - 1;
+    while (l < u) {
+        const int m = (l + u + 1) >> 1;
+        if (w0[m] <= it) l = m;
+        else u = m - 1;
+    }
+    const int k = it - w0[l];
+    const int first = k * PAIR_ITEM;
+    items[it] = make_int4(0, 0, (int)(point_off[l] + first), min(PAIR_ITEM, n_pts[l] - first));
+    item_prob[it] = l;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+template <int MODE, bool ISO, int FD, int SUB>
+static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
+    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool ISO, int FD, int SUB>
+static int occupancy_t() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32, 0);
+    return nb;
+}
+
+// The line-search pass (G-CVO-1) runs with SUB = 8 only; the evaluation
+// pass in all three schedules.
+#define PAIR_VARIANTS(X)                                                                                  \
+    X(PAIR_EVAL, false, 1, 8) X(PAIR_EVAL, false, 3, 8) X(PAIR_EVAL, true, 1, 8) X(PAIR_EVAL, true, 3, 8) \
+    X(PAIR_EVAL, false, 1, 16) X(PAIR_EVAL, false, 3, 16) X(PAIR_EVAL, true, 1, 16)                       \
+    X(PAIR_EVAL, true, 3, 16) X(PAIR_EVAL, false, 1, 32) X(PAIR_EVAL, false, 3, 32)                      \
+    X(PAIR_EVAL, true, 1, 32) X(PAIR_EVAL, true, 3, 32) X(PAIR_LINESEARCH, false, 1, 8)                  \
+    X(PAIR_LINESEARCH, false, 3, 8) X(PAIR_LINESEARCH, true, 1, 8) X(PAIR_LINESEARCH, true, 3, 8)
+
+int pair_sub_for(int mode, int sub) { return mode == PAIR_EVAL && (sub == 16 || sub == 32) ? sub : 8; }
+
+int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
+    sub = pair_sub_for(mode, sub);
+#define OCC(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return occupancy_t<M, I, F, U>();
+    PAIR_VARIANTS(OCC)
+#undef OCC
+    return 1;
+}
+
+cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s) {
+    sub = pair_sub_for(mode, sub);
+#define L(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return launch_tile_t<M, I, F, U>(a, grid, s);
+    PAIR_VARIANTS(L)
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items,
+                         int4 *items, int *item_prob, cudaStream_t s) {
+    if (n_items < 1) return cudaSuccess;
+    k_items<<<(n_items + 255) / 256, 256, 0, s>>>(np, w0, point_off, n_pts, n_items, items, item_prob);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gcvo

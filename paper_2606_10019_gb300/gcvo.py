@@ -99,6 +99,9 @@ def lib() -> ctypes.CDLL:
         L.gcvo_eval.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
         L.gcvo_register.argtypes = [P, P, P, P, P, I64, P, P, P, P, P]
         L.gcvo_register_batched.argtypes = [P, I, P, P, P, P, P, P]
+        L.gcvo_estimate_covariances_batched.argtypes = [P, I, P, P, P, P]
+        L.gcvo_build_grids_batched.argtypes = [P, I, P, P, P, P, P, P]
+        L.gcvo_pair_schedule.argtypes = [P, I, P]
         L.gcvo_profile_enable.argtypes = [P, I]
         L.gcvo_profile_read.argtypes = [P, P]
         _lib = L
@@ -244,6 +247,46 @@ def gcvo_rebuild_grid(ctx: Context, grid: Grid, xyz, cov, feat, params: gcvo_ker
     return grid
 
 
+def _ptr_array(arrs):
+    out = (ctypes.c_void_p * len(arrs))()
+    for k, a in enumerate(arrs):
+        out[k] = _ptr(a)
+    return out
+
+
+def gcvo_estimate_covariances_batched(ctx: Context, xyz_list, params: gcvo_kernel_params, cov_list) -> None:
+    """Covariances of several device clouds in one call (concurrent)."""
+    n = (ctypes.c_int64 * len(xyz_list))(*[_n(x) for x in xyz_list])
+    _check(lib().gcvo_estimate_covariances_batched(ctx.handle, len(xyz_list), _ptr_array(xyz_list), n,
+                                                   ctypes.byref(params), _ptr_array(cov_list)),
+           "gcvo_estimate_covariances_batched")
+
+
+def gcvo_build_grids_batched(ctx: Context, xyz_list, cov_list, feat_list, params: gcvo_kernel_params,
+                             grids=None) -> list:
+    """Build (grids[k] None) or rebuild grids for several device clouds in one
+    call (concurrent).  Returns the list of Grid objects."""
+    m = len(xyz_list)
+    grids = list(grids) if grids is not None else [None] * m
+    h = (ctypes.c_void_p * m)(*[g.handle if g is not None else None for g in grids])
+    n = (ctypes.c_int64 * m)(*[_n(x) for x in xyz_list])
+    covs = _ptr_array(cov_list) if cov_list is not None else None
+    st = lib().gcvo_build_grids_batched(ctx.handle, m, _ptr_array(xyz_list), covs, _ptr_array(feat_list), n,
+                                        ctypes.byref(params), h)
+    out = []
+    for k in range(m):
+        keep = (xyz_list[k], cov_list[k] if cov_list is not None else None, feat_list[k])
+        if grids[k] is not None:
+            grids[k]._keep = keep
+            out.append(grids[k])
+        elif h[k]:
+            out.append(Grid(h[k], ctx, keep))
+        else:
+            out.append(None)
+    _check(st, "gcvo_build_grids_batched")
+    return out
+
+
 @dataclass
 class EvalResult:
     f: float
@@ -316,6 +359,14 @@ def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solv
     if logs is not None:
         out_logs = [_logs_to_list(logs[k * params.k_max:(k + 1) * params.k_max], int(n_iter[k])) for k in range(n)]
     return T.reshape(n, 4, 4), out_logs, n_iter, status
+
+
+def gcvo_pair_schedule(ctx: Context, set: int = -1) -> int:
+    """Force the pair-pass schedule (8, 16, 32 points per sub-tile), hand it
+    back to the autotuner (0) or leave it (-1); returns the last one used."""
+    last = ctypes.c_int()
+    _check(lib().gcvo_pair_schedule(ctx.handle, int(set), ctypes.byref(last)), "gcvo_pair_schedule")
+    return last.value
 
 
 def gcvo_profile_enable(ctx: Context, enable: bool = True) -> None:

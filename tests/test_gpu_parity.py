@@ -52,6 +52,44 @@ def test_eval_corner_anisotropic(env, n):
         _check_eval(O, G, ctx, case, T)
 
 
+@pytest.mark.parametrize("sub", [8, 16, 32])
+def test_eval_every_schedule(env, sub):
+    """Each pair-pass schedule (4, 2 or 1 lanes per source point) meets the
+    tolerance, anisotropic and isotropic; the autotuner picks one of them."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=1111, n_tgt=1500, frame=7)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    iso = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=3.0), iso=True)
+    iso.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08))
+    try:
+        G.gcvo_pair_schedule(ctx, sub)
+        for c in (case, iso):
+            for T in _poses(pair):
+                _check_eval(O, G, ctx, c, T)
+        assert G.gcvo_pair_schedule(ctx) == sub
+    finally:
+        G.gcvo_pair_schedule(ctx, 0)
+    G.gcvo_eval(ctx, case.grid, *case.src, np.eye(4))
+    assert G.gcvo_pair_schedule(ctx) in (8, 16, 32)
+
+
+def test_eval_dense_no_cutoff(env):
+    """cutoff = 0: the paper's dense objective over every pair (Sec. 5.4),
+    anisotropic and isotropic, against the oracle without a cutoff; every
+    pair is a pair-eval."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=700, n_tgt=900, frame=11)
+    case = Case(O, pair, O.KernelParams(cutoff=0.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01, cutoff=0.0))
+    iso = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=0.0), iso=True)
+    iso.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08, cutoff=0.0))
+    for c in (case, iso):
+        for T in _poses(pair):
+            r = G.gcvo_eval(ctx, c.grid, *c.src, T)
+            o = O.evaluate(c.prob, T, c.kp_o)
+            assert rel_f(r.f, o.f) <= TOL and rel_g(r.g, o.g, o.gabs) <= TOL and rel_H(r.H, o.H) <= TOL
+            assert r.n_pairs == 700 * 900
+
+
 def test_eval_isotropic(env):
     """Remark 3: Sigma_ij = ell^2 I."""
     O, G, ctx, dev = env
@@ -190,9 +228,9 @@ def test_register_first_order_matches_oracle(env):
 
 
 def test_batched_equals_single(env):
-    """One launch over several problems gives each problem what it gets
-    alone.  The pair kernel adds per-point sums with shared-memory atomics,
-    so the two runs agree to rounding (not bit for bit)."""
+    """One launch over several problems gives each problem exactly what it
+    gets alone: a problem's work items, their partial sums and the order in
+    which the finalize adds them do not depend on the other problems."""
     O, G, ctx, dev = env
     cases, probs = [], []
     for fr, n in ((0, 700), (1, 1300), (2, 64), (3, 900)):
@@ -204,9 +242,55 @@ def test_batched_equals_single(env):
     Tb, _, nb, sb = G.gcvo_register_batched(ctx, probs, sp)
     for k, c in enumerate(cases):
         Ts, _, ns, ss = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
-        assert ss == sb[k] and abs(ns - nb[k]) <= 2
-        ang, dt = O.pose_error(Ts, Tb[k])
-        assert ang < 1e-7 and dt < 1e-7
+        assert ss == sb[k] and ns == nb[k]
+        assert np.array_equal(Ts, Tb[k])
+
+
+def test_batched_covariances_and_grids_equal_single(env):
+    """The concurrent multi-cloud calls give exactly the single-cloud
+    results: covariances bit for bit, and grids that evaluate identically."""
+    import torch
+    O, G, ctx, dev = env
+    kp = G.kernel_params(eig_max=0.01)
+    sizes = (900, 64, 1500, 333, 20, 700, 1200, 50, 410)
+    pairs = [D.make_corner_pair(n_src=n, n_tgt=n + 17, frame=10 + k) for k, n in enumerate(sizes)]
+    xyz = [soa(p.tgt_xyz, dev) for p in pairs]
+    feat = [soa(p.tgt_feat, dev) for p in pairs]
+    cov_b = [torch.empty((6, x.shape[1]), device=dev) for x in xyz]
+    G.gcvo_estimate_covariances_batched(ctx, xyz, kp, cov_b)
+    grids_b = G.gcvo_build_grids_batched(ctx, xyz, cov_b, feat, kp)
+    grids_b = G.gcvo_build_grids_batched(ctx, xyz, cov_b, feat, kp, grids_b)   # rebuild in place
+    for k, p in enumerate(pairs):
+        c1 = torch.empty_like(cov_b[k])
+        G.gcvo_estimate_covariances(ctx, xyz[k], kp, c1)
+        assert torch.equal(c1, cov_b[k])
+        g1 = G.gcvo_build_grid(ctx, xyz[k], c1, feat[k], kp)
+        sx, sf = soa(p.src_xyz, dev), soa(p.src_feat, dev)
+        sc = torch.empty((6, sx.shape[1]), device=dev)
+        G.gcvo_estimate_covariances(ctx, sx, kp, sc)
+        r1 = G.gcvo_eval(ctx, g1, sx, sc, sf, p.T_true)
+        rb = G.gcvo_eval(ctx, grids_b[k], sx, sc, sf, p.T_true)
+        assert r1.f == rb.f and np.array_equal(r1.g, rb.g) and np.array_equal(r1.H, rb.H)
+
+
+def test_profiled_register_counts_and_times_pair_launches(env):
+    """With profiling on, every pair pass of the graph-replayed register
+    loop is timed by its own pair of CUDA events, and the result does not
+    change."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=800, n_tgt=800, frame=3)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    sp = G.solver_params(k_max=40, eps_tol=1e-8)
+    T0, _, n0, _ = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), sp)
+    G.gcvo_profile_enable(ctx, True)
+    T1, _, n1, _ = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), sp)
+    prof = G.gcvo_profile_read(ctx)
+    G.gcvo_profile_enable(ctx, False)
+    assert np.array_equal(T0, T1) and n0 == n1
+    # whole replays of 8 iterations, one pair pass each
+    assert prof["n_pair_launches"] % 8 == 0 and n1 <= prof["n_pair_launches"] < n1 + 8
+    assert prof["pair_kernel_ms"] > 0
+    assert prof["n_launches"] >= 2 * prof["n_pair_launches"]
 
 
 @pytest.mark.slow
