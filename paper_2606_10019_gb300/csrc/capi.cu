@@ -82,8 +82,10 @@ int ceil_log2(int64_t v) {
 struct Prepared {
     int n_problems = 0;
     int n_groups = 0;
-    int n_items = 0;
-    int *d_nitems = nullptr;
+    int n_items = 0;            // upper bound of the work items
+    int *d_nitems = nullptr;    // their count (device)
+    const int64_t *d_poff = nullptr;
+    const int *d_npts = nullptr;
     int64_t n_points = 0;
     int feat_dim = 1;
     bool iso = false;
@@ -162,8 +164,6 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sp += 256;
     int *d_pcnt = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
-    int *d_pw0 = reinterpret_cast<int *>(sp);
-    sp += al(np * sizeof(int));
     int64_t *d_poff = reinterpret_cast<int64_t *>(sp);
     P.d_nitems = d_nitems;
 
@@ -180,6 +180,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->items.ensure(N * sizeof(int4), s));
     GCVO_TRY(ctx->item_prob.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->pgroup.ensure(N * sizeof(int), s));
+    if (N >= (1LL << 26)) return GCVO_ERR_CAPACITY;   // point index of a sub-tile word
     GCVO_TRY(ctx->status_word.ensure(256, s));
     char *vp = ctx->sort_vals.as<char>();
     int *vals = reinterpret_cast<int *>(vp);
@@ -219,23 +220,20 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_CUDA(launch_src_groups(sa, sa.keys, gid, N, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(),
                                 ctx->grp_prob.as<int>(), d_pg0, d_pg1, s));
     GCVO_CUDA(cudaMemcpyAsync(d_ngroups, gid + N - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    // work items: PAIR_ITEM consecutive sorted points of one problem (the
-    // sort puts problem p's points at its offset)
-    std::vector<int> hw0(np), hn(np);
+    // per-problem point offsets and sizes for the work-item packing, which
+    // depends on the pair schedule and is done by choose_schedule
+    std::vector<int> hn(np);
     std::vector<int64_t> hoff(np);
-    int n_items = 0;
     for (int p = 0; p < np; ++p) {
-        hw0[p] = n_items;
         hn[p] = (int)desc[p].n;
         hoff[p] = desc[p].offset;
-        n_items += (int)((desc[p].n + PAIR_ITEM - 1) / PAIR_ITEM);
     }
-    P.n_items = n_items;
-    GCVO_CUDA(cudaMemcpyAsync(d_pw0, hw0.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
+    P.n_items = (int)N;   // upper bound: every item holds a point
+    P.d_poff = d_poff;
+    P.d_npts = d_pcnt;
     GCVO_CUDA(cudaMemcpyAsync(d_pcnt, hn.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
     GCVO_CUDA(cudaMemcpyAsync(d_poff, hoff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    GCVO_CUDA(cudaMemcpyAsync(d_nitems, &n_items, sizeof(int), cudaMemcpyHostToDevice, s));
-    GCVO_CUDA(launch_items(np, d_pw0, d_poff, d_pcnt, n_items, ctx->items.as<int4>(), ctx->item_prob.as<int>(), s));
+    GCVO_TRY(ctx->pack_tmp.ensure(5 * (((size_t)N + 63) / 64 * 64) * sizeof(int), s));
 
     // read back group and item counts and ranges, source eigenvalue bounds
     void *hp;
@@ -262,8 +260,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         d.iter = 0;
         d.g0 = h[8 + np + p];
         d.g1 = h[8 + 2 * np + p];
-        d.w0 = hw0[p];
-        d.w1 = hw0[p] + (int)((desc[p].n + PAIR_ITEM - 1) / PAIR_ITEM);
+        d.w0 = 0;   // set with the work items
+        d.w1 = 0;
         int le = h[8 + p];
         int li = le >= 0 ? le : le ^ 0x7fffffff;
         float lam_src;
@@ -319,8 +317,15 @@ int pair_grid(const gcvo_ctx *ctx, const Prepared &P, int mode, int sub) {
 // one timed pass with each (the second of two, CUDA events).  The shape is
 // the kernel mode, the feature count and the log2 buckets of the problem
 // count and of the mean source size.
+gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sub) {
+    return pack_items(P.n_problems, ctx->sort_keys.as<unsigned long long>(), P.n_points, sub, P.d_poff, P.d_npts,
+                      ctx->pack_tmp.as<int>(), ctx->items.as<int4>(), ctx->item_prob.as<int>(), P.d_nitems,
+                      ctx->probs.as<ProbDev>(), ctx->scan_tmp.ptr, ctx->stream);
+}
+
 gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
     int sub = ctx->forced_sub;
+    int packed = 0;
     if (!sub) {
         int lb_n = 0, lb_p = 0;
         while ((2LL << lb_n) <= P.n_points / std::max(1, P.n_problems)) ++lb_n;
@@ -329,12 +334,14 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
         for (auto &kv : ctx->tuned)
             if (kv.first == key) sub = kv.second;
         if (!sub) {
-            const int cands[3] = {8, 16, 32};
-            cudaEvent_t ev[6];
+            const int cands[4] = {4, 8, 16, 32};
+            cudaEvent_t ev[8];
             for (auto &e : ev) GCVO_CUDA(cudaEventCreate(&e));
             float best = 0.f;
             gcvo_status st = GCVO_OK;
-            for (int c = 0; c < 3 && st == GCVO_OK; ++c) {
+            for (int c = 0; c < 4 && st == GCVO_OK; ++c) {
+                st = pack(ctx, P, cands[c]);
+                packed = cands[c];
                 const int g = pair_grid(ctx, P, PAIR_EVAL, cands[c]);
                 for (int rep = 0; rep < 2 && st == GCVO_OK; ++rep) {
                     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(int), ctx->stream);
@@ -348,7 +355,7 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
                 }
             }
             if (st == GCVO_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = GCVO_ERR_CUDA;
-            for (int c = 0; c < 3 && st == GCVO_OK; ++c) {
+            for (int c = 0; c < 4 && st == GCVO_OK; ++c) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]) != cudaSuccess) st = GCVO_ERR_CUDA;
                 if (c == 0 || ms < best) {
@@ -361,6 +368,7 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
             ctx->tuned.emplace_back(key, sub);
         }
     }
+    if (packed != sub) GCVO_TRY(pack(ctx, P, sub));
     b.sub = sub;
     b.grid = pair_grid(ctx, P, PAIR_EVAL, sub);
     ctx->last_sub = sub;
@@ -443,9 +451,8 @@ gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int 
         ctx->ev_used += 2;
         GCVO_CUDA(cudaEventRecordWithFlags(e0, s, ev_flags));
     }
-    const int sub = mode == PAIR_EVAL ? b.sub : 8;
-    const int grid = mode == PAIR_EVAL ? b.grid : pair_grid(ctx, P, mode, sub);
-    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, sub, grid, s));
+    const int grid = mode == PAIR_EVAL ? b.grid : pair_grid(ctx, P, mode, b.sub);
+    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, b.sub, grid, s));
     if (e1) GCVO_CUDA(cudaEventRecordWithFlags(e1, s, ev_flags));
     return GCVO_OK;
 }
@@ -709,7 +716,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
                       &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
-                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup};
+                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup, &ctx->pack_tmp};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
         DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,

@@ -187,7 +187,7 @@ struct gcvo_ctx {
     gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
     gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
     gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g;
-    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup;
+    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup, pack_tmp;
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_retry;
     void *host_pinned = nullptr;

@@ -24,7 +24,8 @@ namespace gcvo {
 namespace {
 
 constexpr int64_t NA_MAX_SRC = 65536;                  // source points per call
-constexpr int NA_ITEM = PAIR_ITEM;                     // points per work item
+constexpr int NA_SUB = 8;                              // points per sub-tile (one warp)
+constexpr int NA_ITEM = NA_SUB * PAIR_WARPS;           // points per work item
 constexpr int NA_MAX_ITEMS = (int)(NA_MAX_SRC / NA_ITEM);
 
 // Byte offsets of the pieces of the scratch array (each 256-aligned).
@@ -36,7 +37,7 @@ constexpr size_t NA_ANCHOR = NA_SCB + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_GSTART = NA_ANCHOR + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_PGROUP = NA_GSTART + al256(NA_MAX_SRC * 4);
 constexpr size_t NA_ITEMS = NA_PGROUP + al256(NA_MAX_SRC * 4);
-constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 16);
+constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 4 * PAIR_WARPS);
 constexpr size_t NA_PART = NA_IPROB + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_COUNTS = NA_PART + al256((size_t)NA_MAX_ITEMS * 64 * 4);
 constexpr size_t NA_PROB = NA_COUNTS + al256((size_t)NA_MAX_ITEMS * 4 * 8);
@@ -58,7 +59,7 @@ __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat,
     float4 *scb = reinterpret_cast<float4 *>(base + NA_SCB);
     int *gstart = reinterpret_cast<int *>(base + NA_GSTART);
     int *pgroup = reinterpret_cast<int *>(base + NA_PGROUP);
-    int4 *items = reinterpret_cast<int4 *>(base + NA_ITEMS);
+    int *items = reinterpret_cast<int *>(base + NA_ITEMS);
     int *iprob = reinterpret_cast<int *>(base + NA_IPROB);
     int *words = reinterpret_cast<int *>(base + NA_WORDS);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,8 +88,11 @@ __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat,
     gstart[i] = i;
     pgroup[i] = i;
     if (i % NA_ITEM == 0) {
-        const int m = min(NA_ITEM, n - i);
-        items[i / NA_ITEM] = make_int4(0, 0, i, m);   // first point, points
+        // one sub-tile of NA_SUB consecutive points per warp: first << 6 | points
+        for (int w = 0; w < PAIR_WARPS; ++w) {
+            const int f = i + w * NA_SUB, m = max(0, min(NA_SUB, n - f));
+            items[(i / NA_ITEM) * PAIR_WARPS + w] = m > 0 ? (int)(((unsigned)f << 6) | (unsigned)m) : 0;
+        }
         iprob[i / NA_ITEM] = 0;
     }
 }
@@ -229,9 +233,9 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.ls_literal = 0;
     int sm = 0;
     GCVO_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
-    int per_sm = pair_blocks_per_sm(PAIR_EVAL, iso, fd, 8);
+    int per_sm = pair_blocks_per_sm(PAIR_EVAL, iso, fd, NA_SUB);
     int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * sm));
-    GCVO_CUDA(launch_pair(pa, PAIR_EVAL, iso, fd, 8, grid, s));
+    GCVO_CUDA(launch_pair(pa, PAIR_EVAL, iso, fd, NA_SUB, grid, s));
     fa.mode = FIN_EVAL;
     GCVO_CUDA(launch_finalize(fa, s));
     EvalOut e;

@@ -6,11 +6,10 @@
 namespace gcvo {
 
 // Pair-kernel tiling (tile.cu): a block of PAIR_WARPS warps takes one work
-// item of PAIR_ITEM source points, split into sub-tiles of 8, 16 or 32
-// points (the schedule: 4, 2 or 1 lanes per point).  Target points are
-// staged PAIR_CAP at a time.
+// item of up to PAIR_WARPS sub-tiles, one per warp, each of at most SUB = 4,
+// 8, 16 or 32 source points (the schedule: 8, 4, 2 or 1 lanes per point).
+// Target points are staged PAIR_CAP at a time.
 constexpr int PAIR_WARPS = 4;
-constexpr int PAIR_ITEM = 32;
 constexpr int PAIR_CAP = 512;
 constexpr int PAIR_SLOTS = 28;
 
@@ -43,7 +42,7 @@ struct PairArgs {
     const float4 *anchor;      // per group: R^T (z_g - t) - o, z_g its first point
     const int *gstart;         // first point of each group
     const int *pgroup;         // group of each point
-    const int4 *items;         // (0, 0, first point, points <= PAIR_ITEM)
+    const int4 *items;         // per item, per warp: first point << 6 | points
     const int *item_prob;
     const int *n_items;
     const ProbDev *probs;
@@ -91,7 +90,7 @@ struct SrcArgs {
 };
 
 size_t pair_smem_bytes(int mode);
-// sub: points per sub-tile (8, 16, 32); the line-search pass uses 8.
+// sub: points per sub-tile (4, 8, 16, 32).
 int pair_sub_for(int mode, int sub);
 int pair_blocks_per_sm(int mode, bool iso, int fd, int sub);
 cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s);
@@ -101,10 +100,13 @@ cudaError_t launch_src_segments(const unsigned long long *keys, int64_t n, int *
 cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStream_t s);
 cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
                               int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s);
-// Work items of PAIR_ITEM consecutive (sorted) source points per problem:
-// problem p owns items [w0[p], w0[p] + ceil(n[p] / PAIR_ITEM)) and its points
-// start at point_off[p].
-cudaError_t launch_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items,
-                         int4 *items, int *item_prob, cudaStream_t s);
+// Work items for sub-tiles of at most `sub` points over the n sorted source
+// points (keys as sorted; problem p's points start at point_off[p]):
+// items[it] holds one (first point << 6 | points) word per warp, item_prob
+// the problem, probs[p].w0 / w1 each problem's item range and *d_nitems the
+// count (device side, no synchronisation).  tmp: 5 x round_up(n, 64) ints.
+gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
+                       const int *n_pts, int *tmp, int4 *items, int *item_prob, int *d_nitems, ProbDev *probs,
+                       void *scan_tmp, cudaStream_t s);
 
 }  // namespace gcvo

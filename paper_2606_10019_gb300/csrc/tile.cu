@@ -3,8 +3,11 @@
 // polynomial of Eq. (9) / Appendix B -- over every (target, source) pair of
 // every active problem within the Euclidean radius rho.
 //
-// A block of PAIR_WARPS warps takes one work item: PAIR_ITEM consecutive
-// source points of one problem in Morton order.
+// The source points of a problem are sorted by Morton code.  A sub-tile is
+// a run of at most SUB of them inside one Morton voxel of edge rho (level 2);
+// a work item is up to PAIR_WARPS consecutive sub-tiles inside one voxel of
+// edge 2 rho (level 3), so both stay compact.  A block of PAIR_WARPS warps
+// takes one item, warp w its sub-tile w.
 //  1. Every point is moved into the target grid's frame with T^-1
 //     (Algorithm 1): p_j - o = R^T (z_j - z_g) + a_g, where a_g =
 //     R^T (z_g - t) - o is its group's anchor, computed in FP64 by the
@@ -15,9 +18,8 @@
 //     column is one run of target points.  The runs are staged into shared
 //     memory PAIR_CAP points at a time by cp.async.bulk copies completing on
 //     an mbarrier.
-//  3. The item splits into sub-tiles of SUB points (SUB = 8, 16 or 32: 4, 2
-//     or 1 lanes per point, the schedule the autotuner picks); SUB / 8 warps
-//     share a sub-tile.  A warp holds its sub-tile's points one per lane of
+//  3. SUB = 4, 8, 16 or 32 (8, 4, 2 or 1 lanes per point) is the schedule the
+//     autotuner picks.  A warp holds its sub-tile's points one per lane of
 //     each group of SUB lanes, keeps the staged targets that lie within rho
 //     of the sub-tile's box (one test per target) and walks them 32 / SUB at
 //     a time: lane (q, i) pairs target q of the step with point i.  A target
@@ -27,7 +29,7 @@
 //     determinant, d^2 = r^T Sigma_ij^-1 r, w = c_ij sigma^2 exp(-d^2 / 2)
 //     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
 //       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1.
-//  5. Per point, after the lanes and warps that share it are added: f += S_f,
+//  5. Per point, after the lanes that share it are added: f += S_f,
 //     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the block adds
 //     its points' 28 values with compensated (TwoSum) FP32 sums and writes
 //     one (hi, lo) partial per item for the FP64 finalize.
@@ -40,10 +42,9 @@
 namespace gcvo {
 namespace {
 
-static_assert(PAIR_ITEM == 32 && PAIR_WARPS == 4, "an item is 32 points over 4 warps");
+static_assert(PAIR_WARPS == 4, "an item is up to four sub-tiles, one per warp");
 static_assert(PAIR_CAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_WARPS * PAIR_SLOTS * 33 * 4 <= PAIR_CAP * 32, "epilogue transposes fit in the staged ca, cb");
-static_assert(PAIR_WARPS * 32 * 10 * 4 <= PAIR_CAP * 16, "per-warp point sums fit in the staged pos");
 
 struct __align__(16) TileSmem {
     float4 pos[PAIR_CAP];
@@ -127,15 +128,13 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
 
 template <int MODE, bool ISO, int FD, int SUB>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
-    static_assert(SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 8, 16 or 32 points");
+    static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
     constexpr int TQ = 32 / SUB;    // targets per warp step
-    constexpr int WPS = SUB / 8;    // warps per sub-tile
     constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
     __shared__ TileSmem S;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int qi = lane / SUB, si = lane % SUB;
-    const int st = w / WPS, wr = w % WPS;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (tid == 0) mbar_init(&S.bar, 1);
@@ -157,16 +156,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             continue;
         }
         const GridDev *G = a.grids + prob;
-        const int4 item = a.items[it];
-        const int j0 = item.z, cnt = item.w;
-        const int sj = st * SUB + si;
-        const bool sval = sj < cnt;
+        // this warp's sub-tile: first point << 6 | points (0: none)
+        const unsigned word = (unsigned)reinterpret_cast<const int *>(a.items)[(size_t)it * PAIR_WARPS + w];
+        const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
+        const bool sval = si < cnt;
 
         // ---- 1. the lane's source point in the grid frame
         float Rf[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
-        const int jj = j0 + (sval ? sj : 0);
+        const int jj = j0 + (sval ? si : 0);
         const int grp = a.pgroup[jj];
         const float4 anc = a.anchor[grp];
         const float4 zg = a.spos[a.gstart[grp]];
@@ -375,11 +374,10 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     L += __popc(bal);
                 }
                 __syncwarp();
-                if (wr == 0 && qi == 0 && sval) n_cand += L;
+                if (qi == 0 && sval) n_cand += L;
 
-                // ---- 4. TQ targets per warp step, one per group of lanes;
-                // the WPS warps of a sub-tile take interleaved steps
-                for (int j = wr * TQ; j < L; j += TQ * WPS) {
+                // ---- 4. TQ targets per warp step, one per group of lanes
+                for (int j = 0; j < L; j += TQ) {
                     const int idx = j + qi;
                     const bool act = sval && idx < L;
                     const int k = S.list[w][min(idx, L - 1)];
@@ -465,31 +463,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             __syncthreads();   // S.scan is rewritten by the next column batch
         }
 
-        // ---- 5. per point: add the TQ lanes that share it, then (in warp
-        // order, through the free staging area) the WPS warps
+        // ---- 5. per point: add the TQ lanes that share it
 #pragma unroll
         for (int k = 0; k < NT; ++k)
 #pragma unroll
             for (int o = SUB; o < 32; o <<= 1) t[k] += __shfl_xor_sync(FULL, t[k], o);
-        if (WPS > 1) {
-            float *acc = reinterpret_cast<float *>(S.pos);
-            if (qi == 0)
-#pragma unroll
-                for (int k = 0; k < NT; ++k) acc[(w * 32 + si) * NT + k] = t[k];
-            __syncthreads();
-            if (wr == 0 && qi == 0)
-#pragma unroll
-                for (int k = 0; k < NT; ++k) {
-                    float x = acc[(w * 32 + si) * NT + k];
-#pragma unroll
-                    for (int r = 1; r < WPS; ++r) x += acc[((w + r) * 32 + si) * NT + k];
-                    t[k] = x;
-                }
-        }
         float v[NSLOT];
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) v[k] = 0.f;
-        if (wr == 0 && qi == 0 && sval) {
+        if (qi == 0 && sval) {
             if (MODE == PAIR_EVAL) {
                 float Sf = t[0], Su0 = t[1], Su1 = t[2], Su2 = t[3];
                 float A00 = t[4], A01 = t[5], A02 = t[6], A11 = t[7], A12 = t[8], A22 = t[9];
@@ -599,21 +581,59 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
     }
 }
 
-__global__ void k_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items, int4 *items,
-                        int *item_prob) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= n_items) return;
-    // the problem whose item range holds it: last p with w0[p] <= it
-    int l = 0, u = np - 1;
-    while (l < u) {
-        const int m = (l + u + 1) >> 1;
-        if (w0[m] <= it) l = m;
-        else u = m - 1;
-    }
-    const int k = it - w0[l];
-    const int first = k * PAIR_ITEM;
-    items[it] = make_int4(0, 0, (int)(point_off[l] + first), min(PAIR_ITEM, n_pts[l] - first));
-    item_prob[it] = l;
+// Work-item packing over the sorted source points (keys: problem << 30 |
+// Morton code of the fine voxels of edge rho / 4).
+// Start of each point's run of equal keys >> shift (input of a max-scan).
+__global__ void k_seg_heads(const unsigned long long *keys, int64_t n, int shift, int *seg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool head = i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift);
+    seg[i] = head ? (int)i : 0;
+}
+
+// Sub-tile heads: every sub-th point of a level-2 run.
+__global__ void k_sub_heads(const int *seg2, int64_t n, int sub, int *sid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sid[i] = ((int)i - seg2[i]) % sub == 0 ? 1 : 0;
+}
+
+// Item heads: every PAIR_WARPS-th sub-tile of a level-3 run.  sid is the
+// inclusive count of sub-tile heads; the first point of a level-3 run is a
+// sub-tile head (a level-3 boundary is a level-2 boundary).
+__global__ void k_item_heads(const int *sid, const int *seg3, int64_t n, int *iid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool sub_head = i == 0 || sid[i] != sid[i - 1];
+    iid[i] = sub_head && (sid[i] - sid[seg3[i]]) % PAIR_WARPS == 0 ? 1 : 0;
+}
+
+__global__ void k_sub_count(const int *sid, int64_t n, int *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    atomicAdd(cnt + sid[i] - 1, 1);
+}
+
+// Each sub-tile head writes its (first point << 6 | points) word into slot
+// (its index in the level-3 run) mod PAIR_WARPS of its item.
+__global__ void k_fill_items(const unsigned long long *keys, const int *sid, const int *seg3, const int *iid,
+                             const int *cnt, int64_t n, int *items, int *item_prob) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!(i == 0 || sid[i] != sid[i - 1])) return;
+    const int slot = (sid[i] - sid[seg3[i]]) % PAIR_WARPS;
+    const int it = iid[i] - 1;
+    items[(size_t)it * PAIR_WARPS + slot] = (int)(((unsigned)i << 6) | (unsigned)cnt[sid[i] - 1]);
+    if (slot == 0) item_prob[it] = (int)(keys[i] >> 30);
+}
+
+// Item range of each problem: its points are [off, off + n).
+__global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts, const int *iid, ProbDev *probs) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int64_t f = point_off[p];
+    probs[p].w0 = iid[f] - 1;
+    probs[p].w1 = iid[f + n_pts[p] - 1];
 }
 
 }  // namespace
@@ -635,16 +655,15 @@ static int occupancy_t() {
     return nb;
 }
 
-// The line-search pass (G-CVO-1) runs with SUB = 8 only; the evaluation
-// pass in all three schedules.
-#define PAIR_VARIANTS(X)                                                                                  \
-    X(PAIR_EVAL, false, 1, 8) X(PAIR_EVAL, false, 3, 8) X(PAIR_EVAL, true, 1, 8) X(PAIR_EVAL, true, 3, 8) \
-    X(PAIR_EVAL, false, 1, 16) X(PAIR_EVAL, false, 3, 16) X(PAIR_EVAL, true, 1, 16)                       \
-    X(PAIR_EVAL, true, 3, 16) X(PAIR_EVAL, false, 1, 32) X(PAIR_EVAL, false, 3, 32)                      \
-    X(PAIR_EVAL, true, 1, 32) X(PAIR_EVAL, true, 3, 32) X(PAIR_LINESEARCH, false, 1, 8)                  \
-    X(PAIR_LINESEARCH, false, 3, 8) X(PAIR_LINESEARCH, true, 1, 8) X(PAIR_LINESEARCH, true, 3, 8)
+// Both passes in all four schedules (the line-search pass of G-CVO-1 runs
+// over the same items as the evaluation pass).
+#define PAIR_VARIANTS_M(X, M)                                                                 \
+    X(M, false, 1, 4) X(M, false, 3, 4) X(M, true, 1, 4) X(M, true, 3, 4) X(M, false, 1, 8)    \
+    X(M, false, 3, 8) X(M, true, 1, 8) X(M, true, 3, 8) X(M, false, 1, 16) X(M, false, 3, 16) \
+    X(M, true, 1, 16) X(M, true, 3, 16) X(M, false, 1, 32) X(M, false, 3, 32) X(M, true, 1, 32) X(M, true, 3, 32)
+#define PAIR_VARIANTS(X) PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH)
 
-int pair_sub_for(int mode, int sub) { return mode == PAIR_EVAL && (sub == 16 || sub == 32) ? sub : 8; }
+int pair_sub_for(int, int sub) { return sub == 4 || sub == 16 || sub == 32 ? sub : 8; }
 
 int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
     sub = pair_sub_for(mode, sub);
@@ -664,12 +683,37 @@ cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_items(int np, const int *w0, const int64_t *point_off, const int *n_pts, int n_items,
-                         int4 *items, int *item_prob, cudaStream_t s) {
-    if (n_items < 1) return cudaSuccess;
-    k_items<<<(n_items + 255) / 256, 256, 0, s>>>(np, w0, point_off, n_pts, n_items, items, item_prob);
+gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
+                       const int *n_pts, int *tmp, int4 *items, int *item_prob, int *d_nitems, ProbDev *probs,
+                       void *scan_tmp, cudaStream_t s) {
+    if (n >= (1LL << 26) || (sub != 4 && sub != 8 && sub != 16 && sub != 32)) return GCVO_ERR_CAPACITY;
+    const size_t stride = ((size_t)n + 63) / 64 * 64;
+    int *seg2 = tmp, *seg3 = tmp + stride, *sid = tmp + 2 * stride, *iid = tmp + 3 * stride,
+        *cnt = tmp + 4 * stride;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 6, seg2);
+    k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 9, seg3);
+    count_launches(2);
+    GCVO_CUDA(cudaGetLastError());
+    GCVO_TRY(scan_inclusive_max(seg2, n, scan_tmp, s));
+    GCVO_TRY(scan_inclusive_max(seg3, n, scan_tmp, s));
+    k_sub_heads<<<blocks, 256, 0, s>>>(seg2, n, sub, sid);
     count_launches(1);
-    return cudaGetLastError();
+    GCVO_CUDA(cudaGetLastError());
+    GCVO_TRY(scan_inclusive_sum(sid, n, scan_tmp, s));
+    k_item_heads<<<blocks, 256, 0, s>>>(sid, seg3, n, iid);
+    count_launches(1);
+    GCVO_CUDA(cudaGetLastError());
+    GCVO_TRY(scan_inclusive_sum(iid, n, scan_tmp, s));
+    GCVO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(items, 0, (size_t)n * sizeof(int4), s));
+    k_sub_count<<<blocks, 256, 0, s>>>(sid, n, cnt);
+    k_fill_items<<<blocks, 256, 0, s>>>(keys, sid, seg3, iid, cnt, n, reinterpret_cast<int *>(items), item_prob);
+    k_item_ranges<<<(np + 127) / 128, 128, 0, s>>>(np, point_off, n_pts, iid, probs);
+    count_launches(3);
+    GCVO_CUDA(cudaGetLastError());
+    GCVO_CUDA(cudaMemcpyAsync(d_nitems, iid + n - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return GCVO_OK;
 }
 
 }  // namespace gcvo
