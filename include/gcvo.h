@@ -320,10 +320,10 @@ typedef struct {
 } gcvo_profile;
 
 /* Schedule of the evaluation pair pass (the autotuner; not in the paper):
- * points per sub-tile, 8, 16 or 32, i.e. 4, 2 or 1 threads per source
+ * points per sub-tile, 4, 8, 16 or 32, i.e. 8, 4, 2 or 1 threads per source
  * point.  set = 0 lets the autotuner pick per problem shape (the default:
  * on the first call for a shape it times one pass with each schedule and
- * keeps the fastest for the context); set = 8, 16 or 32 forces one; set =
+ * keeps the fastest for the context); set = 4, 8, 16 or 32 forces one; set =
  * -1 changes nothing.  *last_used (may be NULL) receives the schedule of the
  * last evaluation pass (0 before any).  Results do not depend on the
  * schedule beyond FP32 summation order. */

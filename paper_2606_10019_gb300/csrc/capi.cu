@@ -746,7 +746,8 @@ gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
 }
 
 gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used) {
-    if (!ctx || (set != -1 && set != 0 && set != 8 && set != 16 && set != 32)) return GCVO_ERR_INVALID_ARG;
+    if (!ctx || (set != -1 && set != 0 && set != 4 && set != 8 && set != 16 && set != 32))
+        return GCVO_ERR_INVALID_ARG;
     if (set >= 0) ctx->forced_sub = set;
     if (last_used) *last_used = ctx->last_sub;
     return GCVO_OK;

@@ -362,7 +362,7 @@ def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solv
 
 
 def gcvo_pair_schedule(ctx: Context, set: int = -1) -> int:
-    """Force the pair-pass schedule (8, 16, 32 points per sub-tile), hand it
+    """Force the pair-pass schedule (4, 8, 16, 32 points per sub-tile), hand it
     back to the autotuner (0) or leave it (-1); returns the last one used."""
     last = ctypes.c_int()
     _check(lib().gcvo_pair_schedule(ctx.handle, int(set), ctypes.byref(last)), "gcvo_pair_schedule")
