@@ -229,8 +229,10 @@ def test_register_first_order_matches_oracle(env):
 
 def test_batched_equals_single(env):
     """One launch over several problems gives each problem exactly what it
-    gets alone: a problem's work items, their partial sums and the order in
-    which the finalize adds them do not depend on the other problems."""
+    gets alone: for a given pair schedule, a problem's work items, their
+    partial sums and the order in which the finalize adds them do not depend
+    on the other problems.  (Left to the autotuner, the batch and the single
+    problem may run different schedules, which changes FP32 rounding.)"""
     O, G, ctx, dev = env
     cases, probs = [], []
     for fr, n in ((0, 700), (1, 1300), (2, 64), (3, 900)):
@@ -239,11 +241,21 @@ def test_batched_equals_single(env):
         cases.append(c)
         probs.append((c.grid, *c.src, np.eye(4)))
     sp = G.solver_params(k_max=60, eps_tol=1e-8)
-    Tb, _, nb, sb = G.gcvo_register_batched(ctx, probs, sp)
+    try:
+        G.gcvo_pair_schedule(ctx, 8)
+        Tb, _, nb, sb = G.gcvo_register_batched(ctx, probs, sp)
+        for k, c in enumerate(cases):
+            Ts, _, ns, ss = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
+            assert ss == sb[k] and ns == nb[k]
+            assert np.array_equal(Ts, Tb[k])
+    finally:
+        G.gcvo_pair_schedule(ctx, 0)
+    # autotuned: equal to rounding
+    Tb, _, _, _ = G.gcvo_register_batched(ctx, probs, sp)
     for k, c in enumerate(cases):
-        Ts, _, ns, ss = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
-        assert ss == sb[k] and ns == nb[k]
-        assert np.array_equal(Ts, Tb[k])
+        Ts, _, _, _ = G.gcvo_register(ctx, c.grid, *c.src, np.eye(4), sp)
+        ang, dt = O.pose_error(Ts, Tb[k])
+        assert ang < 1e-6 and dt < 1e-6
 
 
 def test_batched_covariances_and_grids_equal_single(env):
