@@ -319,7 +319,7 @@ int pair_grid(const gcvo_ctx *ctx, const Prepared &P, int mode, int sub) {
 // count and of the mean source size.
 gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sub) {
     return pack_items(P.n_problems, ctx->sort_keys.as<unsigned long long>(), P.n_points, sub, P.d_poff, P.d_npts,
-                      ctx->pack_tmp.as<int>(), ctx->items.as<int4>(), ctx->item_prob.as<int>(), P.d_nitems,
+                      ctx->pack_tmp.as<int>(), ctx->items.as<int>(), ctx->item_prob.as<int>(), P.d_nitems,
                       ctx->probs.as<ProbDev>(), ctx->scan_tmp.ptr, ctx->stream);
 }
 
@@ -389,7 +389,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     a.scb = ctx->src_cb.as<float4>();
     a.anchor = ctx->anchors.as<float4>();
     a.gstart = ctx->grp_start.as<int>();
-    a.items = ctx->items.as<int4>();
+    a.items = ctx->items.as<int>();
     a.item_prob = ctx->item_prob.as<int>();
     a.pgroup = ctx->pgroup.as<int>();
     a.n_items = P.d_nitems;
@@ -720,7 +720,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
         DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
-                        &kg->col_range, &kg->cell_z};
+                        &kg->col_range, &kg->cell_z, &kg->vox_first};
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
@@ -850,6 +850,7 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
     s.hval.release();
     s.col_range.release();
     s.cell_z.release();
+    s.vox_first.release();
     delete grid;
     return GCVO_OK;
 }

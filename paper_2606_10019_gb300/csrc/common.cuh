@@ -78,6 +78,7 @@ struct GridDev {
     const unsigned long long *hkeys;  // open-addressing table of voxel keys
     const int *hval;          // voxel index of each table slot
     const int2 *col_range;    // per (cx, cy) column: its voxels [x, y) in sorted order
+    const int *vox_first;     // target grids: first sorted point of every voxel, dense (+1 entry)
     const int *cell_z;        // cz of each occupied voxel
     unsigned long long hmask; // table size - 1 (power of two)
     double origin[3];         // o (target grid) or 0 (kNN grid), double
@@ -156,7 +157,7 @@ __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, f
 // ---------------------------------------------------------------------------
 struct GridStore {
     GridDev d{};
-    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval, col_range, cell_z;
+    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval, col_range, cell_z, vox_first;
 };
 
 // Build a grid from SoA inputs.  absolute: keep absolute coordinates and no

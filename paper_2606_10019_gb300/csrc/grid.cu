@@ -68,6 +68,14 @@ __global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t
     }
 }
 
+// Points per voxel, stored one slot up: after an inclusive scan, entry v is
+// the number of points in voxels before v (the first sorted point of v).
+__global__ void k_vox_count(const unsigned long long *keys, int64_t n, int *vox) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    atomicAdd(vox + keys[i] + 1, 1);
+}
+
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -158,6 +166,18 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
         g.dims[a] = (int)std::floor(ext) + 2;
         prod *= g.dims[a];
     }
+    // a target grid keeps a dense per-voxel table: coarsen voxels beyond
+    // 2^26 of them
+    while (!absolute && prod > (double)(1 << 26)) {
+        h *= 1.26;
+        g.h = (float)h;
+        g.inv_h = (float)(1.0 / h);
+        prod = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            g.dims[a] = (int)std::floor(((double)mx[a] - (double)mn[a]) / h) + 2;
+            prod *= g.dims[a];
+        }
+    }
     if (prod > 4.0e18) return GCVO_ERR_CAPACITY;
     const double n_columns = (double)g.dims[0] * (double)g.dims[1];
     if (n_columns > (double)(1 << 27)) return GCVO_ERR_CAPACITY;
@@ -168,7 +188,8 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(ctx->sort_keys.ensure(n * sizeof(unsigned long long), s));
     GCVO_TRY(ctx->sort_vals.ensure(n * sizeof(int) * 2 + 1024, s));
     GCVO_TRY(ctx->sort_tmp.ensure(radix_sort_scratch_bytes(n), s));
-    GCVO_TRY(ctx->scan_tmp.ensure(scan_scratch_bytes(n) + 1024, s));
+    const int64_t n_vox = absolute ? 0 : (int64_t)prod;
+    GCVO_TRY(ctx->scan_tmp.ensure(scan_scratch_bytes(std::max<int64_t>(n, n_vox + 1)) + 1024, s));
     auto *keys = ctx->sort_keys.as<unsigned long long>();
     int *vals = ctx->sort_vals.as<int>();
     int *incl = vals + ((n + 63) / 64) * 64;
@@ -206,6 +227,14 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
                                      out.orig.as<int>());
     count_launches(3);
     GCVO_CUDA(cudaGetLastError());
+    if (!absolute) {
+        GCVO_TRY(out.vox_first.ensure((size_t)(n_vox + 1) * sizeof(int), s));
+        GCVO_CUDA(cudaMemsetAsync(out.vox_first.ptr, 0, (size_t)(n_vox + 1) * sizeof(int), s));
+        k_vox_count<<<blocks, 256, 0, s>>>(keys, n, out.vox_first.as<int>());
+        count_launches(1);
+        GCVO_CUDA(cudaGetLastError());
+        GCVO_TRY(scan_inclusive_sum(out.vox_first.as<int>(), n_vox + 1, ctx->scan_tmp.ptr, s));
+    }
 
     g.pos = out.pos.as<float4>();
     g.ca = out.ca.as<float4>();
@@ -216,6 +245,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.hval = out.hval.as<int>();
     g.col_range = out.col_range.as<int2>();
     g.cell_z = out.cell_z.as<int>();
+    g.vox_first = absolute ? nullptr : out.vox_first.as<int>();
     g.hmask = H - 1;
     g.n = (int)n;
     g.n_cells = n_cells;

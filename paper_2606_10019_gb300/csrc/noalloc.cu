@@ -24,8 +24,8 @@ namespace gcvo {
 namespace {
 
 constexpr int64_t NA_MAX_SRC = 65536;                  // source points per call
-constexpr int NA_SUB = 8;                              // points per sub-tile (one warp)
-constexpr int NA_ITEM = NA_SUB * PAIR_WARPS;           // points per work item
+constexpr int NA_SUB = 8;                              // points per work item (one warp)
+constexpr int NA_ITEM = NA_SUB;
 constexpr int NA_MAX_ITEMS = (int)(NA_MAX_SRC / NA_ITEM);
 
 // Byte offsets of the pieces of the scratch array (each 256-aligned).
@@ -37,7 +37,7 @@ constexpr size_t NA_ANCHOR = NA_SCB + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_GSTART = NA_ANCHOR + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_PGROUP = NA_GSTART + al256(NA_MAX_SRC * 4);
 constexpr size_t NA_ITEMS = NA_PGROUP + al256(NA_MAX_SRC * 4);
-constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 4 * PAIR_WARPS);
+constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_PART = NA_IPROB + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_COUNTS = NA_PART + al256((size_t)NA_MAX_ITEMS * 64 * 4);
 constexpr size_t NA_PROB = NA_COUNTS + al256((size_t)NA_MAX_ITEMS * 4 * 8);
@@ -88,11 +88,8 @@ __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat,
     gstart[i] = i;
     pgroup[i] = i;
     if (i % NA_ITEM == 0) {
-        // one sub-tile of NA_SUB consecutive points per warp: first << 6 | points
-        for (int w = 0; w < PAIR_WARPS; ++w) {
-            const int f = i + w * NA_SUB, m = max(0, min(NA_SUB, n - f));
-            items[(i / NA_ITEM) * PAIR_WARPS + w] = m > 0 ? (int)(((unsigned)f << 6) | (unsigned)m) : 0;
-        }
+        // a work item of NA_ITEM consecutive points: first << 6 | points
+        items[i / NA_ITEM] = (int)(((unsigned)i << 6) | (unsigned)min(NA_ITEM, n - i));
         iprob[i / NA_ITEM] = 0;
     }
 }
@@ -221,7 +218,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.anchor = fa.anchor;
     pa.gstart = fa.gstart;
     pa.pgroup = reinterpret_cast<const int *>(base + NA_PGROUP);
-    pa.items = reinterpret_cast<const int4 *>(base + NA_ITEMS);
+    pa.items = reinterpret_cast<const int *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
     pa.n_items = words + 1;
     pa.probs = fa.probs;

@@ -5,12 +5,12 @@
 
 namespace gcvo {
 
-// Pair-kernel tiling (tile.cu): a block of PAIR_WARPS warps takes one work
-// item of up to PAIR_WARPS sub-tiles, one per warp, each of at most SUB = 4,
-// 8, 16 or 32 source points (the schedule: 8, 4, 2 or 1 lanes per point).
-// Target points are staged PAIR_CAP at a time.
+// Pair-kernel tiling (tile.cu): blocks of PAIR_WARPS independent warps; a
+// warp takes one work item, a sub-tile of at most SUB = 4, 8, 16 or 32 source
+// points (the schedule: 8, 4, 2 or 1 lanes per point), and stages target
+// points PAIR_WCAP at a time in its own shared memory.
 constexpr int PAIR_WARPS = 4;
-constexpr int PAIR_CAP = 512;
+constexpr int PAIR_WCAP = 160;
 constexpr int PAIR_SLOTS = 28;
 
 enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1 };
@@ -42,7 +42,7 @@ struct PairArgs {
     const float4 *anchor;      // per group: R^T (z_g - t) - o, z_g its first point
     const int *gstart;         // first point of each group
     const int *pgroup;         // group of each point
-    const int4 *items;         // per item, per warp: first point << 6 | points
+    const int *items;          // per item (sub-tile): first point << 6 | points
     const int *item_prob;
     const int *n_items;
     const ProbDev *probs;
@@ -100,13 +100,14 @@ cudaError_t launch_src_segments(const unsigned long long *keys, int64_t n, int *
 cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStream_t s);
 cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
                               int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s);
-// Work items for sub-tiles of at most `sub` points over the n sorted source
-// points (keys as sorted; problem p's points start at point_off[p]):
-// items[it] holds one (first point << 6 | points) word per warp, item_prob
-// the problem, probs[p].w0 / w1 each problem's item range and *d_nitems the
-// count (device side, no synchronisation).  tmp: 5 x round_up(n, 64) ints.
+// Work items (sub-tiles of at most `sub` points inside one Morton voxel of
+// edge rho) over the n sorted source points (keys as sorted; problem p's
+// points start at point_off[p]): items[it] = first point << 6 | points,
+// item_prob the problem, probs[p].w0 / w1 each problem's item range and
+// *d_nitems the count (device side, no synchronisation).
+// tmp: 3 x round_up(n, 64) ints.
 gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
-                       const int *n_pts, int *tmp, int4 *items, int *item_prob, int *d_nitems, ProbDev *probs,
+                       const int *n_pts, int *tmp, int *items, int *item_prob, int *d_nitems, ProbDev *probs,
                        void *scan_tmp, cudaStream_t s);
 
 }  // namespace gcvo

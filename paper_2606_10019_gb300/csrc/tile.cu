@@ -3,23 +3,23 @@
 // polynomial of Eq. (9) / Appendix B -- over every (target, source) pair of
 // every active problem within the Euclidean radius rho.
 //
-// The source points of a problem are sorted by Morton code.  A sub-tile is
-// a run of at most SUB of them inside one Morton voxel of edge rho (level 2);
-// a work item is up to PAIR_WARPS consecutive sub-tiles inside one voxel of
-// edge 2 rho (level 3), so both stay compact.  A block of PAIR_WARPS warps
-// takes one item, warp w its sub-tile w.
+// The source points of a problem are sorted by Morton code and cut into
+// sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho.
+// Every warp works alone on one sub-tile at a time (a work item), taken from
+// a global counter; no warp waits for another.
 //  1. Every point is moved into the target grid's frame with T^-1
 //     (Algorithm 1): p_j - o = R^T (z_j - z_g) + a_g, where a_g =
 //     R^T (z_g - t) - o is its group's anchor, computed in FP64 by the
 //     finalize; Sigma'_j = R^T Sigma_j R.
-//  2. The voxel columns (cx, cy) that meet the item's bounding box grown by
-//     rho are listed, one per thread.  The occupied voxels of one column over
-//     the needed cz range are contiguous in the grid's sorted order, so each
-//     column is one run of target points.  The runs are staged into shared
-//     memory PAIR_CAP points at a time by cp.async.bulk copies completing on
-//     an mbarrier.
+//  2. The voxel columns (cx, cy) that meet the sub-tile's bounding box grown
+//     by rho are listed, one per lane.  Points are sorted by voxel with cz
+//     fastest, so the voxels of one column over the needed cz range hold one
+//     run of points, read from the grid's dense per-voxel prefix table with
+//     two loads.  The runs are staged into the warp's shared memory
+//     PAIR_WCAP points at a time by cp.async.bulk copies completing on the
+//     warp's mbarrier.
 //  3. SUB = 4, 8, 16 or 32 (8, 4, 2 or 1 lanes per point) is the schedule the
-//     autotuner picks.  A warp holds its sub-tile's points one per lane of
+//     autotuner picks.  The warp holds its sub-tile's points one per lane of
 //     each group of SUB lanes, keeps the staged targets that lie within rho
 //     of the sub-tile's box (one test per target) and walks them 32 / SUB at
 //     a time: lane (q, i) pairs target q of the step with point i.  A target
@@ -30,9 +30,9 @@
 //     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
 //       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1.
 //  5. Per point, after the lanes that share it are added: f += S_f,
-//     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the block adds
+//     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the warp adds
 //     its points' 28 values with compensated (TwoSum) FP32 sums and writes
-//     one (hi, lo) partial per item for the FP64 finalize.
+//     one (hi, lo) partial per sub-tile for the FP64 finalize.
 // With no cutoff (dense mode) rho and the cutoff are infinite and every
 // staged target meets every point: the same code visits all pairs.
 #include "common.cuh"
@@ -42,21 +42,17 @@
 namespace gcvo {
 namespace {
 
-static_assert(PAIR_WARPS == 4, "an item is up to four sub-tiles, one per warp");
-static_assert(PAIR_CAP <= 65535, "target list entries are 16-bit");
-static_assert(PAIR_WARPS * PAIR_SLOTS * 33 * 4 <= PAIR_CAP * 32, "epilogue transposes fit in the staged ca, cb");
+static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
+static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
 
-struct __align__(16) TileSmem {
-    float4 pos[PAIR_CAP];
-    float4 ca[PAIR_CAP];
-    float4 cb[PAIR_CAP];
-    unsigned short list[PAIR_WARPS][PAIR_CAP];   // per warp: staged targets near its sub-tile
-    float red[PAIR_WARPS][PAIR_SLOTS][2];        // per warp: (hi, lo) of each slot
-    float box[PAIR_WARPS][6];                    // per warp: sub-tile bounding box
-    long long cnt[PAIR_WARPS][3];
-    int scan[PAIR_WARPS];
+// Per warp: staged target points, the list of those near the sub-tile, and
+// the mbarrier the bulk copies complete on.
+struct __align__(16) WarpStage {
+    float4 pos[PAIR_WCAP];
+    float4 ca[PAIR_WCAP];
+    float4 cb[PAIR_WCAP];
+    unsigned short list[PAIR_WCAP];
     uint64_t bar;
-    int item;
 };
 
 // One anisotropic pair (Eq. 7) into the lane sums t[10].
@@ -132,32 +128,32 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
     constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
-    __shared__ TileSmem S;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    __shared__ WarpStage stage[PAIR_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (tid == 0) mbar_init(&S.bar, 1);
-    __syncthreads();
+    WarpStage &S = stage[w];
+    if (lane == 0) mbar_init(&S.bar, 1);
+    __syncwarp();
     unsigned parity = 0;
     const int n_items = *a.n_items;
 
     for (;;) {
-        if (tid == 0) S.item = atomicAdd(a.work, 1);
-        __syncthreads();
-        const int it = S.item;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(a.work, 1);
+        it = __shfl_sync(FULL, it, 0);
         if (it >= n_items) break;
         const int prob = a.item_prob[it];
         const ProbDev *P = a.probs + prob;
         if (P->status != 0) {
             // skip the rest of this finished problem's items in one step
-            if (tid == 0) atomicMax(a.work, P->w1);
-            __syncthreads();
+            if (lane == 0) atomicMax(a.work, P->w1);
             continue;
         }
         const GridDev *G = a.grids + prob;
-        // this warp's sub-tile: first point << 6 | points (0: none)
-        const unsigned word = (unsigned)reinterpret_cast<const int *>(a.items)[(size_t)it * PAIR_WARPS + w];
+        // the sub-tile: first point << 6 | points
+        const unsigned word = (unsigned)a.items[it];
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
         const bool sval = si < cnt;
 
@@ -215,32 +211,14 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
 #undef CROSS_W
         }
 
-        // ---- bounding boxes: the warp's sub-tile, then the whole item
-        float wmin[3], wmax[3];
+        // ---- bounding box of the sub-tile
+        float bmin[3], bmax[3];
         {
             const float pp[3] = {px, py, pz};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                wmin[k] = ord_dec(__reduce_min_sync(FULL, ord_enc(sval ? pp[k] : INFINITY)));
-                wmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
-            }
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                S.box[w][k] = wmin[k];
-                S.box[w][3 + k] = wmax[k];
-            }
-        __syncthreads();
-        float bmin[3], bmax[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            bmin[k] = S.box[0][k];
-            bmax[k] = S.box[0][3 + k];
-#pragma unroll
-            for (int v = 1; v < PAIR_WARPS; ++v) {
-                bmin[k] = fminf(bmin[k], S.box[v][k]);
-                bmax[k] = fmaxf(bmax[k], S.box[v][3 + k]);
+                bmin[k] = ord_dec(__reduce_min_sync(FULL, ord_enc(sval ? pp[k] : INFINITY)));
+                bmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
             }
         }
         const float rho = sqrtf(rho2);
@@ -266,15 +244,14 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         float t[NT];
 #pragma unroll
         for (int k = 0; k < NT; ++k) t[k] = 0.f;
-        int n_pairs = 0, n_kept = 0;
-        long long n_cand = 0;
+        int n_pairs = 0, n_kept = 0, n_cand = 0;
         const int dy = G->dims[1], dzs = G->dims[2];
 
-        for (int cb0 = 0; cb0 < n_cols; cb0 += PAIR_WARPS * 32) {
-            // ---- 2. one column per thread: its run of target points.  A
+        for (int cb0 = 0; cb0 < n_cols; cb0 += 32) {
+            // ---- 2. one column per lane: its run of target points.  A
             // column is kept when its xy rectangle lies within rho of the
-            // item box; its cz range shrinks with that distance.
-            const int c = cb0 + tid;
+            // box; its cz range shrinks with that distance.
+            const int c = cb0 + lane;
             int rs = 0, rl = 0;
             if (c < n_cols) {
                 const int cx = lo[0] + c / ncy, cy = lo[1] + c % ncy;
@@ -286,52 +263,30 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     const float ez = sqrtf(rc2 - d2xy);
                     const int czl = max(lo[2], (int)floorf(fmaxf((bmin[2] - ez - G->corner[2]) * ih, -1.0f)));
                     const int czh = min(hi[2], (int)floorf(fminf((bmax[2] + ez - G->corner[2]) * ih, (float)dzs)));
-                    const int2 cr = G->col_range[cx * dy + cy];
-                    // the column's voxels are sorted by cz: first with cz >= czl
-                    int l = cr.x, u = cr.y;
-                    while (l < u) {
-                        const int m = (l + u) >> 1;
-                        if (__ldg(G->cell_z + m) < czl) l = m + 1;
-                        else u = m;
-                    }
-                    const int first = l;
-                    u = cr.y;
-                    while (l < u) {   // first with cz > czh
-                        const int m = (l + u) >> 1;
-                        if (__ldg(G->cell_z + m) <= czh) l = m + 1;
-                        else u = m;
-                    }
-                    if (l > first) {
-                        rs = __ldg(G->cell_start + first);
-                        rl = __ldg(G->cell_start + l) - rs;
+                    if (czl <= czh) {
+                        const size_t base = ((size_t)cx * dy + cy) * dzs;
+                        rs = __ldg(G->vox_first + base + czl);
+                        rl = __ldg(G->vox_first + base + czh + 1) - rs;
                     }
                 }
             }
-            // exclusive block offsets of the runs
+            // exclusive warp offsets of the runs
             int incl = rl;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(FULL, incl, o);
                 if (lane >= o) incl += v;
             }
-            if (lane == 31) S.scan[w] = incl;
-            __syncthreads();
-            int total = 0, wofs = 0;
-#pragma unroll
-            for (int v = 0; v < PAIR_WARPS; ++v) {
-                const int sv = S.scan[v];
-                wofs += v < w ? sv : 0;
-                total += sv;
-            }
-            const int off = wofs + incl - rl;
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int off = incl - rl;
 
-            for (int base = 0; base < total; base += PAIR_CAP) {
-                const int m = min(PAIR_CAP, total - base);
+            for (int base = 0; base < total; base += PAIR_WCAP) {
+                const int m = min(PAIR_WCAP, total - base);
                 // ---- stage the chunk [base, base + m) (bulk copies)
                 fence_proxy_async_smem();
-                __syncthreads();   // everyone is done with the previous chunk
-                if (tid == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * 48u);
-                __syncthreads();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * 48u);
+                __syncwarp();
                 {
                     const int s0 = max(off, base), s1 = min(off + rl, base + m);
                     if (s1 > s0) {
@@ -343,15 +298,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     }
                 }
                 {
-                    // bounded wait; the exit decision is block-uniform
+                    // bounded wait; the exit decision is warp-uniform
                     int spin = 0;
                     bool all_done;
                     for (;;) {
-                        all_done = __syncthreads_and(mbar_try_wait(&S.bar, parity)) != 0;
-                        if (all_done || ++spin > (1 << 20)) break;
+                        all_done = __all_sync(FULL, mbar_try_wait(&S.bar, parity));
+                        if (all_done || ++spin > (1 << 22)) break;
                     }
                     if (!all_done) {
-                        if (tid == 0) atomicOr(a.status_word, DEV_ERR_TIMEOUT);
+                        if (lane == 0) atomicOr(a.status_word, DEV_ERR_TIMEOUT);
                         return;
                     }
                     parity ^= 1u;
@@ -364,23 +319,23 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     bool hit = false;
                     if (tt < m) {
                         const float4 x = S.pos[tt];
-                        const float dx = fmaxf(0.f, fmaxf(wmin[0] - x.x, x.x - wmax[0]));
-                        const float dyy = fmaxf(0.f, fmaxf(wmin[1] - x.y, x.y - wmax[1]));
-                        const float dz = fmaxf(0.f, fmaxf(wmin[2] - x.z, x.z - wmax[2]));
+                        const float dx = fmaxf(0.f, fmaxf(bmin[0] - x.x, x.x - bmax[0]));
+                        const float dyy = fmaxf(0.f, fmaxf(bmin[1] - x.y, x.y - bmax[1]));
+                        const float dz = fmaxf(0.f, fmaxf(bmin[2] - x.z, x.z - bmax[2]));
                         hit = dx * dx + dyy * dyy + dz * dz <= rc2;
                     }
                     const unsigned bal = __ballot_sync(FULL, hit);
-                    if (hit) S.list[w][L + __popc(bal & lt_mask)] = (unsigned short)tt;
+                    if (hit) S.list[L + __popc(bal & lt_mask)] = (unsigned short)tt;
                     L += __popc(bal);
                 }
                 __syncwarp();
                 if (qi == 0 && sval) n_cand += L;
 
-                // ---- 4. TQ targets per warp step, one per group of lanes
+                // ---- 4. TQ targets per step, one per group of lanes
                 for (int j = 0; j < L; j += TQ) {
                     const int idx = j + qi;
                     const bool act = sval && idx < L;
-                    const int k = S.list[w][min(idx, L - 1)];
+                    const int k = S.list[min(idx, L - 1)];
                     const float4 x = S.pos[k];
                     if (MODE == PAIR_EVAL && !ISO) {
                         pair_aniso<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
@@ -459,8 +414,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
                     }
                 }
+                __syncwarp();   // the list and staged points are reused by the next chunk
             }
-            __syncthreads();   // S.scan is rewritten by the next column batch
         }
 
         // ---- 5. per point: add the TQ lanes that share it
@@ -491,10 +446,9 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 v[5] = -Su1;
                 v[6] = -Su2;
                 // M = [[P^T S_A P, P S_A], [-S_A P, S_A]], P = p^ (Eq. 11 with J = [-p^, I])
-                const float B00 = A01 * pz - A02 * py, B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
+                const float B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
                 const float B10 = A11 * pz - A12 * py, B11 = -A01 * pz + A12 * px, B12 = A01 * py - A11 * px;
                 const float B20 = A12 * pz - A22 * py, B21 = -A02 * pz + A22 * px, B22 = A02 * py - A12 * px;
-                (void)B00;
                 v[7] = pz * B10 - py * B20;
                 v[8] = pz * B11 - py * B21;
                 v[9] = pz * B12 - py * B22;
@@ -522,13 +476,14 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             }
         }
         // compensated sums over the sub-tile's points: transpose through the
-        // free staging area, lane k adds slot k
-        float *tr = reinterpret_cast<float *>(S.ca) + w * PAIR_SLOTS * 33;
+        // warp's staging area (free now), lane k adds slot k
+        float *tr = reinterpret_cast<float *>(S.pos);
         __syncwarp();
         if (qi == 0)
 #pragma unroll
             for (int k = 0; k < NSLOT; ++k) tr[k * (SUB + 1) + si] = v[k];
         __syncwarp();
+        float *out = a.part + (size_t)it * 64;
         if (lane < NSLOT) {
             float hs = 0.f, ls = 0.f;
 #pragma unroll
@@ -539,50 +494,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 ls += (hs - (sm - bp)) + (x - bp);
                 hs = sm;
             }
-            S.red[w][lane][0] = hs;
-            S.red[w][lane][1] = ls;
+            out[lane] = hs;
+            out[32 + lane] = ls;
         }
-        {
-            const int tp = __reduce_add_sync(FULL, n_pairs);
-            const int tk = __reduce_add_sync(FULL, n_kept);
-            const long long tc = (long long)__reduce_add_sync(FULL, (unsigned)n_cand);
-            if (lane == 0) {
-                S.cnt[w][0] = tp;
-                S.cnt[w][1] = tk;
-                S.cnt[w][2] = tc;
-            }
+        const int tp = __reduce_add_sync(FULL, n_pairs);
+        const int tk = __reduce_add_sync(FULL, n_kept);
+        const int tc = __reduce_add_sync(FULL, n_cand);
+        if (lane == 0) {
+            long long *cnts = a.counts + (size_t)it * 4;
+            cnts[0] = tp;
+            cnts[1] = tk;
+            cnts[2] = tc;
         }
-        __syncthreads();
-        if (w == 0) {
-            float *out = a.part + (size_t)it * 64;
-            if (lane < NSLOT) {
-                float hs = S.red[0][lane][0], ls = S.red[0][lane][1];
-#pragma unroll
-                for (int v2 = 1; v2 < PAIR_WARPS; ++v2) {
-                    const float x = S.red[v2][lane][0];
-                    const float sm = hs + x;
-                    const float bp = sm - hs;
-                    ls += (hs - (sm - bp)) + (x - bp) + S.red[v2][lane][1];
-                    hs = sm;
-                }
-                out[lane] = hs;
-                out[32 + lane] = ls;
-            }
-            if (lane < 3) {
-                long long s2 = 0;
-#pragma unroll
-                for (int v2 = 0; v2 < PAIR_WARPS; ++v2) s2 += S.cnt[v2][lane];
-                a.counts[(size_t)it * 4 + lane] = s2;
-            }
-        }
-        // S.red / S.cnt are rewritten only after the next item's first
-        // barrier, S.item only after this one
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 // Work-item packing over the sorted source points (keys: problem << 30 |
-// Morton code of the fine voxels of edge rho / 4).
+// Morton code of the fine voxels of edge rho / 4): one item per sub-tile.
 // Start of each point's run of equal keys >> shift (input of a max-scan).
 __global__ void k_seg_heads(const unsigned long long *keys, int64_t n, int shift, int *seg) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,42 +527,30 @@ __global__ void k_sub_heads(const int *seg2, int64_t n, int sub, int *sid) {
     sid[i] = ((int)i - seg2[i]) % sub == 0 ? 1 : 0;
 }
 
-// Item heads: every PAIR_WARPS-th sub-tile of a level-3 run.  sid is the
-// inclusive count of sub-tile heads; the first point of a level-3 run is a
-// sub-tile head (a level-3 boundary is a level-2 boundary).
-__global__ void k_item_heads(const int *sid, const int *seg3, int64_t n, int *iid) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const bool sub_head = i == 0 || sid[i] != sid[i - 1];
-    iid[i] = sub_head && (sid[i] - sid[seg3[i]]) % PAIR_WARPS == 0 ? 1 : 0;
-}
-
+// Each sub-tile head writes its item word: first point << 6 | points.
 __global__ void k_sub_count(const int *sid, int64_t n, int *cnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     atomicAdd(cnt + sid[i] - 1, 1);
 }
 
-// Each sub-tile head writes its (first point << 6 | points) word into slot
-// (its index in the level-3 run) mod PAIR_WARPS of its item.
-__global__ void k_fill_items(const unsigned long long *keys, const int *sid, const int *seg3, const int *iid,
-                             const int *cnt, int64_t n, int *items, int *item_prob) {
+__global__ void k_fill_items(const unsigned long long *keys, const int *sid, const int *cnt, int64_t n, int *items,
+                             int *item_prob) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (!(i == 0 || sid[i] != sid[i - 1])) return;
-    const int slot = (sid[i] - sid[seg3[i]]) % PAIR_WARPS;
-    const int it = iid[i] - 1;
-    items[(size_t)it * PAIR_WARPS + slot] = (int)(((unsigned)i << 6) | (unsigned)cnt[sid[i] - 1]);
-    if (slot == 0) item_prob[it] = (int)(keys[i] >> 30);
+    const int it = sid[i] - 1;
+    items[it] = (int)(((unsigned)i << 6) | (unsigned)cnt[it]);
+    item_prob[it] = (int)(keys[i] >> 30);
 }
 
 // Item range of each problem: its points are [off, off + n).
-__global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts, const int *iid, ProbDev *probs) {
+__global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts, const int *sid, ProbDev *probs) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const int64_t f = point_off[p];
-    probs[p].w0 = iid[f] - 1;
-    probs[p].w1 = iid[f + n_pts[p] - 1];
+    probs[p].w0 = sid[f] - 1;
+    probs[p].w1 = sid[f + n_pts[p] - 1];
 }
 
 }  // namespace
@@ -684,35 +601,27 @@ cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, 
 }
 
 gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
-                       const int *n_pts, int *tmp, int4 *items, int *item_prob, int *d_nitems, ProbDev *probs,
+                       const int *n_pts, int *tmp, int *items, int *item_prob, int *d_nitems, ProbDev *probs,
                        void *scan_tmp, cudaStream_t s) {
     if (n >= (1LL << 26) || (sub != 4 && sub != 8 && sub != 16 && sub != 32)) return GCVO_ERR_CAPACITY;
     const size_t stride = ((size_t)n + 63) / 64 * 64;
-    int *seg2 = tmp, *seg3 = tmp + stride, *sid = tmp + 2 * stride, *iid = tmp + 3 * stride,
-        *cnt = tmp + 4 * stride;
+    int *seg2 = tmp, *sid = tmp + stride, *cnt = tmp + 2 * stride;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 6, seg2);
-    k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 9, seg3);
-    count_launches(2);
+    count_launches(1);
     GCVO_CUDA(cudaGetLastError());
     GCVO_TRY(scan_inclusive_max(seg2, n, scan_tmp, s));
-    GCVO_TRY(scan_inclusive_max(seg3, n, scan_tmp, s));
     k_sub_heads<<<blocks, 256, 0, s>>>(seg2, n, sub, sid);
     count_launches(1);
     GCVO_CUDA(cudaGetLastError());
     GCVO_TRY(scan_inclusive_sum(sid, n, scan_tmp, s));
-    k_item_heads<<<blocks, 256, 0, s>>>(sid, seg3, n, iid);
-    count_launches(1);
-    GCVO_CUDA(cudaGetLastError());
-    GCVO_TRY(scan_inclusive_sum(iid, n, scan_tmp, s));
     GCVO_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), s));
-    GCVO_CUDA(cudaMemsetAsync(items, 0, (size_t)n * sizeof(int4), s));
     k_sub_count<<<blocks, 256, 0, s>>>(sid, n, cnt);
-    k_fill_items<<<blocks, 256, 0, s>>>(keys, sid, seg3, iid, cnt, n, reinterpret_cast<int *>(items), item_prob);
-    k_item_ranges<<<(np + 127) / 128, 128, 0, s>>>(np, point_off, n_pts, iid, probs);
+    k_fill_items<<<blocks, 256, 0, s>>>(keys, sid, cnt, n, items, item_prob);
+    k_item_ranges<<<(np + 127) / 128, 128, 0, s>>>(np, point_off, n_pts, sid, probs);
     count_launches(3);
     GCVO_CUDA(cudaGetLastError());
-    GCVO_CUDA(cudaMemcpyAsync(d_nitems, iid + n - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    GCVO_CUDA(cudaMemcpyAsync(d_nitems, sid + n - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
     return GCVO_OK;
 }
 
