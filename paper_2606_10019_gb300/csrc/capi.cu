@@ -311,42 +311,47 @@ int pair_grid(const gcvo_ctx *ctx, const Prepared &P, int mode, int sub) {
     return std::max(1, std::min(P.n_items, per_sm * ctx->sm_count));
 }
 
-// The autotuner: the schedule of the evaluation pass (8, 16 or 32 points per
-// sub-tile, i.e. 4, 2 or 1 lanes per point) for this shape of problem set
-// -- a forced one, the cached choice for the same shape, or the fastest of
-// one timed pass with each (the second of two, CUDA events).  The shape is
-// the kernel mode, the feature count and the log2 buckets of the problem
-// count and of the mean source size.
-gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sub) {
-    return pack_items(P.n_problems, ctx->sort_keys.as<unsigned long long>(), P.n_points, sub, P.d_poff, P.d_npts,
-                      ctx->pack_tmp.as<int>(), ctx->items.as<int>(), ctx->item_prob.as<int>(), P.d_nitems,
-                      ctx->probs.as<ProbDev>(), ctx->scan_tmp.ptr, ctx->stream);
+// A schedule of the pair passes: sub (points per sub-tile: 4, 8, 16 or 32,
+// i.e. 8, 4, 2 or 1 lanes per point) | level << 8 (the Morton voxel level
+// that sub-tiles never cross: 2 = edge rho, 3 = edge 2 rho).  The work items
+// are packed for it.
+gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sched) {
+    return pack_items(P.n_problems, ctx->sort_keys.as<unsigned long long>(), P.n_points, sched & 0xff, sched >> 8,
+                      P.d_poff, P.d_npts, ctx->pack_tmp.as<int>(), ctx->items.as<int>(), ctx->item_prob.as<int>(),
+                      P.d_nitems, ctx->probs.as<ProbDev>(), ctx->scan_tmp.ptr, ctx->stream);
 }
 
+// The autotuner: the schedule for this shape of problem set -- a forced
+// one, the cached choice for the same shape, or the fastest of one timed
+// evaluation pass with each candidate (the second of two, CUDA events).  The
+// shape is the kernel mode, the feature count and the log2 buckets of the
+// problem count and of the mean source size.
 gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
-    int sub = ctx->forced_sub;
+    int sched = ctx->forced_sub ? (ctx->forced_sub | 2 << 8) : 0;
     int packed = 0;
-    if (!sub) {
+    if (!sched) {
         int lb_n = 0, lb_p = 0;
         while ((2LL << lb_n) <= P.n_points / std::max(1, P.n_problems)) ++lb_n;
         while ((2 << lb_p) <= P.n_problems) ++lb_p;
         const long long key = ((long long)P.iso << 40) | ((long long)P.feat_dim << 32) | ((long long)lb_p << 8) | lb_n;
         for (auto &kv : ctx->tuned)
-            if (kv.first == key) sub = kv.second;
-        if (!sub) {
-            const int cands[4] = {4, 8, 16, 32};
-            cudaEvent_t ev[8];
+            if (kv.first == key) sched = kv.second;
+        if (!sched) {
+            constexpr int NC = 7;
+            const int cands[NC] = {4 | 2 << 8, 8 | 2 << 8, 16 | 2 << 8, 32 | 2 << 8, 8 | 3 << 8, 16 | 3 << 8, 32 | 3 << 8};
+            cudaEvent_t ev[2 * NC];
             for (auto &e : ev) GCVO_CUDA(cudaEventCreate(&e));
             float best = 0.f;
             gcvo_status st = GCVO_OK;
-            for (int c = 0; c < 4 && st == GCVO_OK; ++c) {
+            for (int c = 0; c < NC && st == GCVO_OK; ++c) {
+                const int sub_c = cands[c] & 0xff;
                 st = pack(ctx, P, cands[c]);
                 packed = cands[c];
-                const int g = pair_grid(ctx, P, PAIR_EVAL, cands[c]);
+                const int g = pair_grid(ctx, P, PAIR_EVAL, sub_c);
                 for (int rep = 0; rep < 2 && st == GCVO_OK; ++rep) {
                     cudaError_t e = cudaMemsetAsync(b.work, 0, sizeof(int), ctx->stream);
                     if (e == cudaSuccess && rep == 1) e = cudaEventRecord(ev[2 * c], ctx->stream);
-                    if (e == cudaSuccess) e = launch_pair(b.pa, PAIR_EVAL, P.iso, P.feat_dim, cands[c], g, ctx->stream);
+                    if (e == cudaSuccess) e = launch_pair(b.pa, PAIR_EVAL, P.iso, P.feat_dim, sub_c, g, ctx->stream);
                     if (e == cudaSuccess && rep == 1) e = cudaEventRecord(ev[2 * c + 1], ctx->stream);
                     if (e != cudaSuccess) {
                         set_last_cuda_error(e, "schedule timing pass", __LINE__);
@@ -355,20 +360,21 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
                 }
             }
             if (st == GCVO_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = GCVO_ERR_CUDA;
-            for (int c = 0; c < 4 && st == GCVO_OK; ++c) {
+            for (int c = 0; c < NC && st == GCVO_OK; ++c) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, ev[2 * c], ev[2 * c + 1]) != cudaSuccess) st = GCVO_ERR_CUDA;
                 if (c == 0 || ms < best) {
                     best = ms;
-                    sub = cands[c];
+                    sched = cands[c];
                 }
             }
             for (auto &e : ev) cudaEventDestroy(e);
             if (st != GCVO_OK) return st;
-            ctx->tuned.emplace_back(key, sub);
+            ctx->tuned.emplace_back(key, sched);
         }
     }
-    if (packed != sub) GCVO_TRY(pack(ctx, P, sub));
+    if (packed != sched) GCVO_TRY(pack(ctx, P, sched));
+    const int sub = sched & 0xff;
     b.sub = sub;
     b.grid = pair_grid(ctx, P, PAIR_EVAL, sub);
     ctx->last_sub = sub;

@@ -11,6 +11,7 @@ namespace gcvo {
 // points PAIR_WCAP at a time in its own shared memory.
 constexpr int PAIR_WARPS = 4;
 constexpr int PAIR_WCAP = 160;
+constexpr int PAIR_GRAB = 16;   // work items a warp takes per atomic
 constexpr int PAIR_SLOTS = 28;
 
 enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1 };
@@ -101,13 +102,13 @@ cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStrea
 cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
                               int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s);
 // Work items (sub-tiles of at most `sub` points inside one Morton voxel of
-// edge rho) over the n sorted source points (keys as sorted; problem p's
+// level `level`: edge rho / 4 * 2^level) over the n sorted source points (keys as sorted; problem p's
 // points start at point_off[p]): items[it] = first point << 6 | points,
 // item_prob the problem, probs[p].w0 / w1 each problem's item range and
 // *d_nitems the count (device side, no synchronisation).
 // tmp: 3 x round_up(n, 64) ints.
-gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
-                       const int *n_pts, int *tmp, int *items, int *item_prob, int *d_nitems, ProbDev *probs,
-                       void *scan_tmp, cudaStream_t s);
+gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, int level,
+                       const int64_t *point_off, const int *n_pts, int *tmp, int *items, int *item_prob,
+                       int *d_nitems, ProbDev *probs, void *scan_tmp, cudaStream_t s);
 
 }  // namespace gcvo

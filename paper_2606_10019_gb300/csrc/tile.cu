@@ -4,9 +4,11 @@
 // every active problem within the Euclidean radius rho.
 //
 // The source points of a problem are sorted by Morton code and cut into
-// sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho.
-// Every warp works alone on one sub-tile at a time (a work item), taken from
-// a global counter; no warp waits for another.
+// sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho
+// (or 2 rho, the coarser cut the autotuner may pick).  Every warp works alone
+// on one sub-tile at a time (a work item); it takes PAIR_GRAB items per
+// atomic on the global counter, so the counter is touched rarely, and no warp
+// waits for another.
 //  1. Every point is moved into the target grid's frame with T^-1
 //     (Algorithm 1): p_j - o = R^T (z_j - z_g) + a_g, where a_g =
 //     R^T (z_g - t) - o is its group's anchor, computed in FP64 by the
@@ -139,21 +141,32 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
     unsigned parity = 0;
     const int n_items = *a.n_items;
 
+    int gbase = 0;          // first item of the current grab
+    unsigned pending = 0;   // lanes of the grab whose item is still to do
+    int my_word = 0, my_prob = 0;
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(a.work, 1);
-        it = __shfl_sync(FULL, it, 0);
-        if (it >= n_items) break;
-        const int prob = a.item_prob[it];
-        const ProbDev *P = a.probs + prob;
-        if (P->status != 0) {
-            // skip the rest of this finished problem's items in one step
-            if (lane == 0) atomicMax(a.work, P->w1);
-            continue;
+        if (!pending) {
+            // grab PAIR_GRAB items; lane l looks at item gbase + l
+            if (lane == 0) gbase = atomicAdd(a.work, PAIR_GRAB);
+            gbase = __shfl_sync(FULL, gbase, 0);
+            if (gbase >= n_items) break;
+            bool live = false;
+            if (lane < PAIR_GRAB && gbase + lane < n_items) {
+                my_prob = a.item_prob[gbase + lane];
+                my_word = a.items[gbase + lane];
+                live = a.probs[my_prob].status == 0;   // finished problems are skipped
+            }
+            pending = __ballot_sync(FULL, live);
+            if (!pending) continue;
         }
+        const int src_lane = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const int it = gbase + src_lane;
+        const int prob = __shfl_sync(FULL, my_prob, src_lane);
+        const unsigned word = (unsigned)__shfl_sync(FULL, my_word, src_lane);
+        const ProbDev *P = a.probs + prob;
         const GridDev *G = a.grids + prob;
         // the sub-tile: first point << 6 | points
-        const unsigned word = (unsigned)a.items[it];
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
         const bool sval = si < cnt;
 
@@ -520,7 +533,7 @@ __global__ void k_seg_heads(const unsigned long long *keys, int64_t n, int shift
     seg[i] = head ? (int)i : 0;
 }
 
-// Sub-tile heads: every sub-th point of a level-2 run.
+// Sub-tile heads: every sub-th point of a run of one voxel.
 __global__ void k_sub_heads(const int *seg2, int64_t n, int sub, int *sid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -600,14 +613,15 @@ cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, 
     return cudaErrorInvalidValue;
 }
 
-gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, const int64_t *point_off,
-                       const int *n_pts, int *tmp, int *items, int *item_prob, int *d_nitems, ProbDev *probs,
-                       void *scan_tmp, cudaStream_t s) {
-    if (n >= (1LL << 26) || (sub != 4 && sub != 8 && sub != 16 && sub != 32)) return GCVO_ERR_CAPACITY;
+gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, int level,
+                       const int64_t *point_off, const int *n_pts, int *tmp, int *items, int *item_prob,
+                       int *d_nitems, ProbDev *probs, void *scan_tmp, cudaStream_t s) {
+    if (n >= (1LL << 26) || (sub != 4 && sub != 8 && sub != 16 && sub != 32) || level < 0 || level > 3)
+        return GCVO_ERR_CAPACITY;
     const size_t stride = ((size_t)n + 63) / 64 * 64;
     int *seg2 = tmp, *sid = tmp + stride, *cnt = tmp + 2 * stride;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 6, seg2);
+    k_seg_heads<<<blocks, 256, 0, s>>>(keys, n, 3 * level, seg2);
     count_launches(1);
     GCVO_CUDA(cudaGetLastError());
     GCVO_TRY(scan_inclusive_max(seg2, n, scan_tmp, s));
