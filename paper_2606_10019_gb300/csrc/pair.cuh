@@ -6,12 +6,11 @@
 namespace gcvo {
 
 // Pair-kernel tiling (tile.cu): blocks of PAIR_WARPS independent warps; a
-// warp takes one work item, a sub-tile of at most 32 source points (one per
-// lane; the packing cuts sub-tiles of at most SUB = 4, 8, 16 or 32 points,
-// the schedule), and stages target points PAIR_WCAP at a time in its own
-// shared memory.
+// warp takes one work item, a sub-tile of at most SUB = 4, 8, 16 or 32 source
+// points (the schedule: 8, 4, 2 or 1 lanes per point), and stages target
+// points PAIR_WCAP at a time in its own shared memory.
 constexpr int PAIR_WARPS = 4;
-constexpr int PAIR_WCAP = 128;
+constexpr int PAIR_WCAP = 160;
 constexpr int PAIR_GRAB = 16;   // work items a warp takes per atomic
 constexpr int PAIR_SLOTS = 28;
 

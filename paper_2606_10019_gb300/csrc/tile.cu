@@ -4,8 +4,8 @@
 // every active problem within the Euclidean radius rho.
 //
 // The source points of a problem are sorted by Morton code and cut into
-// sub-tiles: runs of at most SUB <= 32 points inside one Morton voxel of edge
-// rho or 2 rho (the packing the autotuner picks).  Every warp works alone
+// sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho
+// (or 2 rho, the coarser cut the autotuner may pick).  Every warp works alone
 // on one sub-tile at a time (a work item); it takes PAIR_GRAB items per
 // atomic on the global counter, so the counter is touched rarely, and no warp
 // waits for another.
@@ -20,21 +20,21 @@
 //     two loads.  The runs are staged into the warp's shared memory
 //     PAIR_WCAP points at a time by cp.async.bulk copies completing on the
 //     warp's mbarrier.
-//  3. Lane i holds point i of the sub-tile (at most 32).  The warp keeps the
-//     staged targets that lie within rho of the sub-tile's box (one test per
-//     target), then tests |r| <= rho for every (point, kept target), point by
-//     point, and queues the hits.
-//  4. Every 32 queued pairs run one per lane (Eq. 7): Sigma_ij = Sigma_i +
-//     Sigma'_j, its adjugate and determinant, d^2 = r^T Sigma_ij^-1 r,
-//     w = c_ij sigma^2 exp(-d^2 / 2) for d^2 <= c^2, else 0; and
-//       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1
-//     per point: the queue is in point order, so a segmented warp sum hands
-//     each point's share to one lane, which adds it to the point's sums in
-//     shared memory (a fixed order: the result is deterministic).
-//  5. Per point: f += S_f, g = -(p x S_u, S_u), M += J^T S_A J with
-//     J = [-p^, I]; the warp adds its points' 28 values with compensated
-//     (TwoSum) FP32 sums and writes one (hi, lo) partial per sub-tile for the
-//     FP64 finalize.
+//  3. SUB = 4, 8, 16 or 32 (8, 4, 2 or 1 lanes per point) is the schedule the
+//     autotuner picks.  The warp holds its sub-tile's points one per lane of
+//     each group of SUB lanes, keeps the staged targets that lie within rho
+//     of the sub-tile's box (one test per target) and walks them 32 / SUB at
+//     a time: lane (q, i) pairs target q of the step with point i.  A target
+//     is read by SUB lanes at once (a broadcast), a point stays in
+//     registers, and no lane waits on another's branch.
+//  4. Per pair (Eq. 7): Sigma_ij = Sigma_i + Sigma'_j, its adjugate and
+//     determinant, d^2 = r^T Sigma_ij^-1 r, w = c_ij sigma^2 exp(-d^2 / 2)
+//     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
+//       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1.
+//  5. Per point, after the lanes that share it are added: f += S_f,
+//     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the warp adds
+//     its points' 28 values with compensated (TwoSum) FP32 sums and writes
+//     one (hi, lo) partial per sub-tile for the FP64 finalize.
 // With no cutoff (dense mode) rho and the cutoff are infinite and every
 // staged target meets every point: the same code visits all pairs.
 #include "common.cuh"
@@ -44,25 +44,60 @@
 namespace gcvo {
 namespace {
 
-static_assert(PAIR_WCAP <= 256, "queue entries hold a staged index in 8 bits");
+static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
 
-constexpr int PAIR_QCAP = 64;   // queued pairs per warp (two batches)
-
-// Per warp: staged target points, the list of those near the sub-tile, the
-// sub-tile's points (PTS float4 each), their sums, the pair queue, and the
-// mbarrier the bulk copies complete on.
-template <int PTS, int NT>
+// Per warp: staged target points, the list of those near the sub-tile, and
+// the mbarrier the bulk copies complete on.
 struct __align__(16) WarpStage {
     float4 pos[PAIR_WCAP];
     float4 ca[PAIR_WCAP];
     float4 cb[PAIR_WCAP];
-    float4 pt[32 * PTS];
-    float acc[32 * NT];
     unsigned short list[PAIR_WCAP];
-    unsigned short queue[PAIR_QCAP];
     uint64_t bar;
 };
+
+// One anisotropic pair (Eq. 7) into the lane sums t[10].
+template <int FD>
+__device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, const float4 cbv, float px, float py,
+                                           float pz, float l0, float l1, float l2, const float q[6], float rho2,
+                                           float c2, bool act, float *t, int &n_pairs, int &n_kept) {
+    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+    const bool in = act && rr <= rho2;
+    float cij = x.w * l0;
+    if (FD > 1) cij += cbv.z * l1 + cbv.w * l2;
+    const float s00 = ca.x + q[0], s01 = ca.y + q[1], s02 = ca.z + q[2];
+    const float s11 = ca.w + q[3], s12 = cbv.x + q[4], s22 = cbv.y + q[5];
+    const float c00 = s11 * s22 - s12 * s12;
+    const float c01 = s02 * s12 - s01 * s22;
+    const float c02 = s01 * s12 - s02 * s11;
+    const float c11 = s00 * s22 - s02 * s02;
+    const float c12 = s01 * s02 - s00 * s12;
+    const float c22 = s00 * s11 - s01 * s01;
+    const float det = s00 * c00 + s01 * c01 + s02 * c02;
+    const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+    const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+    const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+    const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+    const float rdet = rcp_approx(det);
+    const float d2 = qf * rdet;
+    const bool keep = in && d2 <= c2;
+    const float wgt = cij * ex2_approx(d2 * NEG_HALF_LOG2E);
+    const float wd = keep ? wgt * rdet : 0.f;
+    n_pairs += in;
+    n_kept += keep;
+    t[0] += keep ? wgt : 0.f;
+    t[1] += wd * y0;
+    t[2] += wd * y1;
+    t[3] += wd * y2;
+    t[4] += wd * c00;
+    t[5] += wd * c01;
+    t[6] += wd * c02;
+    t[7] += wd * c11;
+    t[8] += wd * c12;
+    t[9] += wd * c22;
+}
 
 // Line-search sums of one pair (Appendix B): with beta, gamma, delta, eps the
 // coefficients of the exponent's expansion along t xi, the kernel value
@@ -89,151 +124,26 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
     t[4] += wgt * (ep + be * de + 0.5f * be * be * ga + 0.5f * ga * ga + be * be * be * be * (1.f / 24.f));
 }
 
-// One pair of Eq. (7) (or its line-search terms) into the lane sums t:
-// target (x, ca, cb) staged, point (p0: p and l0, p1, p2: Sigma'_j and l1,
-// l2; pl: a_1..a_4 for the line search).  Evaluation sums: S_f = sum w,
-// S_u = sum w Sigma^-1 r, S_A = sum w Sigma^-1 (anisotropic; isotropic:
-// S_f and sum w r).
-template <int MODE, bool ISO, int FD>
-__device__ __forceinline__ void pair_one(const float4 x, const float4 ca, const float4 cb, const float4 p0,
-                                         const float4 p1, const float4 p2, const float4 *pl, float c2, float iso_inv,
-                                         bool act, int literal, float *t, int &n_kept) {
-    const float r0 = x.x - p0.x, r1 = x.y - p0.y, r2 = x.z - p0.z;
-    float cij = x.w * p0.w;
-    if (FD > 1) cij += cb.z * p2.z + cb.w * p2.w;
-    if (ISO) {
-        const float d2 = (r0 * r0 + r1 * r1 + r2 * r2) * iso_inv;
-        const bool keep = act && d2 <= c2;
-        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-        n_kept += keep;
-        if (MODE == PAIR_EVAL) {
-            t[0] += wgt;
-            t[1] += wgt * r0;
-            t[2] += wgt * r1;
-            t[3] += wgt * r2;
-        } else {
-            const float4 u0 = pl[0], u1 = pl[1], u2 = pl[2];
-            const float b1[3] = {u0.x, u0.y, u0.z}, b2[3] = {u0.w, u1.x, u1.y}, b3[3] = {u1.z, u1.w, u2.x},
-                        b4[3] = {u2.y, u2.z, u2.w};
-            // A = I / ell^2
-            const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
-            const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
-            const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
-            const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
-            const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
-            const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
-            const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
-            const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
-            ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, literal, t);
-        }
-        return;
-    }
-    const float s00 = ca.x + p1.x, s01 = ca.y + p1.y, s02 = ca.z + p1.z;
-    const float s11 = ca.w + p1.w, s12 = cb.x + p2.x, s22 = cb.y + p2.y;
-    const float c00 = s11 * s22 - s12 * s12;
-    const float c01 = s02 * s12 - s01 * s22;
-    const float c02 = s01 * s12 - s02 * s11;
-    const float c11 = s00 * s22 - s02 * s02;
-    const float c12 = s01 * s02 - s00 * s12;
-    const float c22 = s00 * s11 - s01 * s01;
-    const float det = s00 * c00 + s01 * c01 + s02 * c02;
-    const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
-    const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
-    const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
-    const float qf = r0 * y0 + r1 * y1 + r2 * y2;
-    const float rdet = rcp_approx(det);
-    const float d2 = qf * rdet;
-    const bool keep = act && d2 <= c2;
-    const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-    n_kept += keep;
-    if (MODE == PAIR_EVAL) {
-        const float wd = wgt * rdet;
-        t[0] += wgt;
-        t[1] += wd * y0;
-        t[2] += wd * y1;
-        t[3] += wd * y2;
-        t[4] += wd * c00;
-        t[5] += wd * c01;
-        t[6] += wd * c02;
-        t[7] += wd * c11;
-        t[8] += wd * c12;
-        t[9] += wd * c22;
-    } else {
-        const float4 u0 = pl[0], u1 = pl[1], u2 = pl[2];
-        const float b1[3] = {u0.x, u0.y, u0.z}, b2[3] = {u0.w, u1.x, u1.y}, b3[3] = {u1.z, u1.w, u2.x},
-                    b4[3] = {u2.y, u2.z, u2.w};
-        // bilinear forms of A = adj / det with r and a_k
-        const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
-        const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
-        const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
-        const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
-        const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
-        const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
-        const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
-        const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
-        const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
-        const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
-        const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
-        const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
-        const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
-        const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
-        ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, literal, t);
-    }
-}
-
-// Evaluate the first n queued pairs, one per lane, and add them to their
-// points' sums.  The queue is in point order, so the lanes of one point are
-// contiguous: a segmented suffix sum leaves each point's batch total in its
-// first lane, which adds it to the point's accumulator (one writer per point
-// per batch, in a fixed order).
-template <int MODE, bool ISO, int FD, int PTS, int NT>
-__device__ __forceinline__ void eval_batch(WarpStage<PTS, NT> &S, int n, int lane, float c2, float iso_inv,
-                                           int literal, int &n_kept) {
-    const unsigned FULL = 0xffffffffu;
-    const bool act = lane < n;
-    const int e = S.queue[act ? lane : n - 1];
-    const int i = e >> 8, k = e & 255;
-    float t[NT];
-#pragma unroll
-    for (int q = 0; q < NT; ++q) t[q] = 0.f;
-    const float4 *pi = S.pt + i * PTS;
-    pair_one<MODE, ISO, FD>(S.pos[k], S.ca[k], S.cb[k], pi[0], pi[1], pi[2], pi + 3, c2, iso_inv, act, literal, t,
-                            n_kept);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int io = __shfl_down_sync(FULL, i, o);
-        const bool same = lane + o < 32 && io == i;
-#pragma unroll
-        for (int q = 0; q < NT; ++q) {
-            const float v = __shfl_down_sync(FULL, t[q], o);
-            t[q] += same ? v : 0.f;
-        }
-    }
-    const int iu = __shfl_up_sync(FULL, i, 1);
-    if (act && (lane == 0 || iu != i))
-#pragma unroll
-        for (int q = 0; q < NT; ++q) S.acc[i * NT + q] += t[q];
-    __syncwarp();
-}
-
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
+    static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
+    constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
-    constexpr int PTS = MODE == PAIR_EVAL ? 3 : 6;
-    __shared__ WarpStage<PTS, NT> stage[PAIR_WARPS];
+    __shared__ WarpStage stage[PAIR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    WarpStage<PTS, NT> &S = stage[w];
+    WarpStage &S = stage[w];
     if (lane == 0) mbar_init(&S.bar, 1);
     __syncwarp();
     unsigned parity = 0;
     const int n_items = *a.n_items;
+
     int gbase = 0;          // first item of the current grab
     unsigned pending = 0;   // lanes of the grab whose item is still to do
     int my_word = 0, my_prob = 0;
-
     for (;;) {
         if (!pending) {
             // grab PAIR_GRAB items; lane l looks at item gbase + l
@@ -256,15 +166,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const unsigned word = (unsigned)__shfl_sync(FULL, my_word, src_lane);
         const ProbDev *P = a.probs + prob;
         const GridDev *G = a.grids + prob;
-        // the sub-tile: first point << 6 | points (<= 32, one per lane)
+        // the sub-tile: first point << 6 | points
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
-        const bool sval = lane < cnt;
+        const bool sval = si < cnt;
 
         // ---- 1. the lane's source point in the grid frame
         float Rf[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
-        const int jj = j0 + (sval ? lane : 0);
+        const int jj = j0 + (sval ? si : 0);
         const int grp = a.pgroup[jj];
         const float4 anc = a.anchor[grp];
         const float4 zg = a.spos[a.gstart[grp]];
@@ -292,14 +202,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             qv[5] = Rf[2] * T1[2] + Rf[5] * T1[5] + Rf[8] * T1[8];
         }
         const float sg = P->sigma2;
+        const float l0 = sg * z.w;
+        const float l1 = FD > 1 ? sg * zb.z : 0.f;
+        const float l2 = FD > 1 ? sg * zb.w : 0.f;
         const float rho2 = P->rho2, c2 = P->c2, iso_inv = P->iso_inv;
-        S.pt[lane * PTS + 0] = make_float4(px, py, pz, sg * z.w);
-        S.pt[lane * PTS + 1] = make_float4(qv[0], qv[1], qv[2], qv[3]);
-        S.pt[lane * PTS + 2] = make_float4(qv[4], qv[5], FD > 1 ? sg * zb.z : 0.f, FD > 1 ? sg * zb.w : 0.f);
+
+        // G-CVO-1 second pass: a_k = (xi^)^k p, xi the search direction
+        float b1[3], b2[3], b3[3], b4[3];
         if (MODE == PAIR_LINESEARCH) {
-            // G-CVO-1 second pass: a_k = (xi^)^k p, xi the search direction
             const float om0 = P->dir32[0], om1 = P->dir32[1], om2 = P->dir32[2];
-            float b1[3], b2[3], b3[3], b4[3];
             b1[0] = om1 * pz - om2 * py + P->dir32[3];
             b1[1] = om2 * px - om0 * pz + P->dir32[4];
             b1[2] = om0 * py - om1 * px + P->dir32[5];
@@ -311,12 +222,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             CROSS_W(b3, b2)
             CROSS_W(b4, b3)
 #undef CROSS_W
-            S.pt[lane * PTS + 3] = make_float4(b1[0], b1[1], b1[2], b2[0]);
-            S.pt[lane * PTS + 4] = make_float4(b2[1], b2[2], b3[0], b3[1]);
-            S.pt[lane * PTS + 5] = make_float4(b3[2], b4[0], b4[1], b4[2]);
         }
-#pragma unroll
-        for (int q = 0; q < NT; ++q) S.acc[lane * NT + q] = 0.f;
 
         // ---- bounding box of the sub-tile
         float bmin[3], bmax[3];
@@ -328,7 +234,6 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 bmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
             }
         }
-        __syncwarp();
         const float rho = sqrtf(rho2);
         const float h = G->h, ih = G->inv_h;
         // culling radius: rho plus a margin for the float voxel assignment
@@ -349,6 +254,9 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const int ncy = empty ? 0 : hi[1] - lo[1] + 1;
         const int n_cols = empty ? 0 : (hi[0] - lo[0] + 1) * ncy;
 
+        float t[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) t[k] = 0.f;
         int n_pairs = 0, n_kept = 0, n_cand = 0;
         const int dy = G->dims[1], dzs = G->dims[2];
 
@@ -434,54 +342,104 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     L += __popc(bal);
                 }
                 __syncwarp();
-                n_cand += cnt * L;
+                if (qi == 0 && sval) n_cand += L;
 
-                // ---- 4. |r| <= rho for every (point, listed target), point
-                // by point; the hits queue up and run 32 at a time
-                int nq = 0;
-                for (int i = 0; i < cnt; ++i) {
-                    const float4 pi = S.pt[i * PTS];
-                    for (int t0 = 0; t0 < L; t0 += 32) {
-                        const int tt = t0 + lane;
-                        int k = 0;
-                        bool hit = false;
-                        if (tt < L) {
-                            k = S.list[tt];
-                            const float4 x = S.pos[k];
-                            const float r0 = x.x - pi.x, r1 = x.y - pi.y, r2 = x.z - pi.z;
-                            hit = r0 * r0 + r1 * r1 + r2 * r2 <= rho2;
-                        }
-                        const unsigned bal = __ballot_sync(FULL, hit);
-                        if (hit) S.queue[nq + __popc(bal & lt_mask)] = (unsigned short)((i << 8) | k);
-                        nq += __popc(bal);
-                        __syncwarp();
-                        if (nq >= 32) {
-                            n_pairs += 32;
-                            eval_batch<MODE, ISO, FD, PTS, NT>(S, 32, lane, c2, iso_inv, a.ls_literal, n_kept);
-                            nq -= 32;
-                            const unsigned short rest = lane < nq ? S.queue[32 + lane] : 0;
-                            __syncwarp();
-                            if (lane < nq) S.queue[lane] = rest;
-                            __syncwarp();
-                        }
+                // ---- 4. TQ targets per step, one per group of lanes
+                for (int j = 0; j < L; j += TQ) {
+                    const int idx = j + qi;
+                    const bool act = sval && idx < L;
+                    const int k = S.list[min(idx, L - 1)];
+                    const float4 x = S.pos[k];
+                    if (MODE == PAIR_EVAL && !ISO) {
+                        pair_aniso<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                                       n_kept);
+                        continue;
                     }
-                }
-                if (nq > 0) {
-                    n_pairs += nq;
-                    eval_batch<MODE, ISO, FD, PTS, NT>(S, nq, lane, c2, iso_inv, a.ls_literal, n_kept);
+                    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+                    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                    const bool in = act && rr <= rho2;
+                    float cij = x.w * l0;
+                    if (FD > 1) {
+                        const float4 cbv = S.cb[k];
+                        cij += cbv.z * l1 + cbv.w * l2;
+                    }
+                    if (ISO) {
+                        const float d2 = rr * iso_inv;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        if (MODE == PAIR_EVAL) {
+                            t[0] += wgt;
+                            t[1] += wgt * r0;
+                            t[2] += wgt * r1;
+                            t[3] += wgt * r2;
+                        } else {
+                            // A = I / ell^2
+                            const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
+                            const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
+                            const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
+                            const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
+                            const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
+                            const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
+                            const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
+                            const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
+                            ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
+                        }
+                    } else {
+                        // anisotropic line search (MODE == PAIR_LINESEARCH)
+                        const float4 ca = S.ca[k];
+                        const float4 cbv = S.cb[k];
+                        const float s00 = ca.x + qv[0], s01 = ca.y + qv[1], s02 = ca.z + qv[2];
+                        const float s11 = ca.w + qv[3], s12 = cbv.x + qv[4], s22 = cbv.y + qv[5];
+                        const float c00 = s11 * s22 - s12 * s12;
+                        const float c01 = s02 * s12 - s01 * s22;
+                        const float c02 = s01 * s12 - s02 * s11;
+                        const float c11 = s00 * s22 - s02 * s02;
+                        const float c12 = s01 * s02 - s00 * s12;
+                        const float c22 = s00 * s11 - s01 * s01;
+                        const float det = s00 * c00 + s01 * c01 + s02 * c02;
+                        const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+                        const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+                        const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+                        const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+                        const float rdet = rcp_approx(det);
+                        const float d2 = qf * rdet;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        // bilinear forms of A = adj / det with r and a_k
+                        const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
+                        const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
+                        const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
+                        const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
+                        const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
+                        const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
+                        const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
+                        const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
+                        const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
+                        const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
+                        const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
+                        const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
+                        const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
+                        const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
+                        ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
+                    }
                 }
                 __syncwarp();   // the list and staged points are reused by the next chunk
             }
         }
 
-        // ---- 5. per point: (f, g, M) contributions from its sums
-        float t[NT];
+        // ---- 5. per point: add the TQ lanes that share it
 #pragma unroll
-        for (int q = 0; q < NT; ++q) t[q] = S.acc[lane * NT + q];
+        for (int k = 0; k < NT; ++k)
+#pragma unroll
+            for (int o = SUB; o < 32; o <<= 1) t[k] += __shfl_xor_sync(FULL, t[k], o);
         float v[NSLOT];
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) v[k] = 0.f;
-        if (sval) {
+        if (qi == 0 && sval) {
             if (MODE == PAIR_EVAL) {
                 float Sf = t[0], Su0 = t[1], Su1 = t[2], Su2 = t[3];
                 float A00 = t[4], A01 = t[5], A02 = t[6], A11 = t[7], A12 = t[8], A22 = t[9];
@@ -534,14 +492,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         // warp's staging area (free now), lane k adds slot k
         float *tr = reinterpret_cast<float *>(S.pos);
         __syncwarp();
+        if (qi == 0)
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) tr[k * 33 + lane] = v[k];
+            for (int k = 0; k < NSLOT; ++k) tr[k * (SUB + 1) + si] = v[k];
         __syncwarp();
         float *out = a.part + (size_t)it * 64;
         if (lane < NSLOT) {
             float hs = 0.f, ls = 0.f;
-            for (int i2 = 0; i2 < cnt; ++i2) {
-                const float x = tr[lane * 33 + i2];
+#pragma unroll
+            for (int i2 = 0; i2 < SUB; ++i2) {
+                const float x = tr[lane * (SUB + 1) + i2];
                 const float sm = hs + x;
                 const float bp = sm - hs;
                 ls += (hs - (sm - bp)) + (x - bp);
@@ -550,12 +510,14 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             out[lane] = hs;
             out[32 + lane] = ls;
         }
+        const int tp = __reduce_add_sync(FULL, n_pairs);
         const int tk = __reduce_add_sync(FULL, n_kept);
+        const int tc = __reduce_add_sync(FULL, n_cand);
         if (lane == 0) {
             long long *cnts = a.counts + (size_t)it * 4;
-            cnts[0] = n_pairs;   // warp-uniform
+            cnts[0] = tp;
             cnts[1] = tk;
-            cnts[2] = n_cand;    // warp-uniform
+            cnts[2] = tc;
         }
         __syncwarp();
     }
@@ -609,38 +571,43 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
-    k_tile<MODE, ISO, FD><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
+    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 static int occupancy_t() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD>, PAIR_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32, 0);
     return nb;
 }
 
-#define PAIR_VARIANTS(X)                                                                                  \
-    X(PAIR_EVAL, false, 1) X(PAIR_EVAL, false, 3) X(PAIR_EVAL, true, 1) X(PAIR_EVAL, true, 3)             \
-    X(PAIR_LINESEARCH, false, 1) X(PAIR_LINESEARCH, false, 3) X(PAIR_LINESEARCH, true, 1)                 \
-    X(PAIR_LINESEARCH, true, 3)
+// Both passes in all four schedules (the line-search pass of G-CVO-1 runs
+// over the same items as the evaluation pass).
+#define PAIR_VARIANTS_M(X, M)                                                                 \
+    X(M, false, 1, 4) X(M, false, 3, 4) X(M, true, 1, 4) X(M, true, 3, 4) X(M, false, 1, 8)    \
+    X(M, false, 3, 8) X(M, true, 1, 8) X(M, true, 3, 8) X(M, false, 1, 16) X(M, false, 3, 16) \
+    X(M, true, 1, 16) X(M, true, 3, 16) X(M, false, 1, 32) X(M, false, 3, 32) X(M, true, 1, 32) X(M, true, 3, 32)
+#define PAIR_VARIANTS(X) PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH)
 
 int pair_sub_for(int, int sub) { return sub == 4 || sub == 16 || sub == 32 ? sub : 8; }
 
-int pair_blocks_per_sm(int mode, bool iso, int fd, int) {
-#define OCC(M, I, F) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1)) return occupancy_t<M, I, F>();
+int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
+    sub = pair_sub_for(mode, sub);
+#define OCC(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return occupancy_t<M, I, F, U>();
     PAIR_VARIANTS(OCC)
 #undef OCC
     return 1;
 }
 
-cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int, int grid, cudaStream_t s) {
-#define L(M, I, F) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1)) return launch_tile_t<M, I, F>(a, grid, s);
+cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s) {
+    sub = pair_sub_for(mode, sub);
+#define L(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return launch_tile_t<M, I, F, U>(a, grid, s);
     PAIR_VARIANTS(L)
 #undef L
     return cudaErrorInvalidValue;
