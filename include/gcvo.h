@@ -319,14 +319,16 @@ typedef struct {
                                 recorded on the context's stream around each launch */
 } gcvo_profile;
 
-/* Schedule of the evaluation pair pass (the autotuner; not in the paper):
- * points per sub-tile, 4, 8, 16 or 32, i.e. 8, 4, 2 or 1 threads per source
- * point.  set = 0 lets the autotuner pick per problem shape (the default:
- * on the first call for a shape it times one pass with each schedule and
- * keeps the fastest for the context); set = 4, 8, 16 or 32 forces one; set =
- * -1 changes nothing.  *last_used (may be NULL) receives the schedule of the
- * last evaluation pass (0 before any).  Results do not depend on the
- * schedule beyond FP32 summation order. */
+/* Schedule of the pair passes (the autotuner; not in the paper): the source
+ * points are cut into sub-tiles of at most `sub` = 4, 8, 16 or 32 points
+ * (8, 4, 2 or 1 threads per point) that never cross a Morton voxel of edge
+ * rho (level 2) or 2 rho (level 3); a schedule is sub | level << 8, and a
+ * bare sub means level 2.  set = 0 lets the autotuner pick per problem shape
+ * (the default: on the first call for a shape it times one pass with each
+ * candidate and keeps the fastest for the context); any other valid value
+ * forces that schedule; set = -1 changes nothing.  *last_used (may be NULL)
+ * receives the points per sub-tile of the last evaluation pass (0 before
+ * any).  Results do not depend on the schedule beyond FP32 summation order. */
 gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used);
 
 /* Turn profiling on (enable != 0) or off and reset the counters.

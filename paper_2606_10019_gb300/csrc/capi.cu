@@ -327,7 +327,7 @@ gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sched) {
 // shape is the kernel mode, the feature count and the log2 buckets of the
 // problem count and of the mean source size.
 gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
-    int sched = ctx->forced_sub ? (ctx->forced_sub | 2 << 8) : 0;
+    int sched = ctx->forced_sub ? (ctx->forced_sub < 256 ? ctx->forced_sub | 2 << 8 : ctx->forced_sub) : 0;
     int packed = 0;
     if (!sched) {
         int lb_n = 0, lb_p = 0;
@@ -752,8 +752,9 @@ gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
 }
 
 gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used) {
-    if (!ctx || (set != -1 && set != 0 && set != 4 && set != 8 && set != 16 && set != 32))
-        return GCVO_ERR_INVALID_ARG;
+    const int sub = set & 0xff, level = set >> 8;
+    const bool ok_sub = sub == 4 || sub == 8 || sub == 16 || sub == 32, ok_level = level == 0 || level == 2 || level == 3;
+    if (!ctx || (set != -1 && set != 0 && !(ok_sub && ok_level))) return GCVO_ERR_INVALID_ARG;
     if (set >= 0) ctx->forced_sub = set;
     if (last_used) *last_used = ctx->last_sub;
     return GCVO_OK;
