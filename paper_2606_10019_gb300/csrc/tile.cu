@@ -20,18 +20,18 @@
 //     two loads.  The runs are staged into the warp's shared memory
 //     PAIR_WCAP points at a time by cp.async.bulk copies completing on the
 //     warp's mbarrier.
-//  3. With cnt points in the sub-tile, lane (q, i) = (lane / cnt, lane % cnt)
-//     holds point i, for q < 32 / cnt, so nearly every lane works whatever
-//     cnt is.  The warp keeps the staged targets that lie within rho of the
-//     sub-tile's box (one test per target) and walks them 32 / cnt at a time:
-//     lane (q, i) pairs target q of the step with point i.  A target is read
-//     by cnt lanes at once (a broadcast), a point stays in registers, and no
-//     lane waits on another's branch.
+//  3. SUB = 4, 8, 16 or 32 (8, 4, 2 or 1 lanes per point) is the schedule the
+//     autotuner picks.  The warp holds its sub-tile's points one per lane of
+//     each group of SUB lanes, keeps the staged targets that lie within rho
+//     of the sub-tile's box (one test per target) and walks them 32 / SUB at
+//     a time: lane (q, i) pairs target q of the step with point i.  A target
+//     is read by SUB lanes at once (a broadcast), a point stays in
+//     registers, and no lane waits on another's branch.
 //  4. Per pair (Eq. 7): Sigma_ij = Sigma_i + Sigma'_j, its adjugate and
 //     determinant, d^2 = r^T Sigma_ij^-1 r, w = c_ij sigma^2 exp(-d^2 / 2)
 //     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
 //       S_f = sum w,  S_u = sum w Sigma^-1 r,  S_A = sum w Sigma^-1.
-//  5. Per point, after its lanes are added (in a fixed order): f += S_f,
+//  5. Per point, after the lanes that share it are added: f += S_f,
 //     g = -(p x S_u, S_u), M += J^T S_A J with J = [-p^, I]; the warp adds
 //     its points' 28 values with compensated (TwoSum) FP32 sums and writes
 //     one (hi, lo) partial per sub-tile for the FP64 finalize.
@@ -124,12 +124,15 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
     t[4] += wgt * (ep + be * de + 0.5f * be * be * ga + 0.5f * ga * ga + be * be * be * be * (1.f / 24.f));
 }
 
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
+    static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
+    constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
     __shared__ WarpStage stage[PAIR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     WarpStage &S = stage[w];
@@ -147,12 +150,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             if (lane == 0) gbase = atomicAdd(a.work, PAIR_GRAB);
             gbase = __shfl_sync(FULL, gbase, 0);
             if (gbase >= n_items) break;
-            bool live = false;
+            bool live = false, last = false;
             if (lane < PAIR_GRAB && gbase + lane < n_items) {
                 my_prob = a.item_prob[gbase + lane];
                 my_word = a.items[gbase + lane];
                 live = a.probs[my_prob].status == 0;   // finished problems are skipped
+                last = lane == PAIR_GRAB - 1 || gbase + lane == n_items - 1;
             }
+            // the grab ends in a finished problem: move the counter past the
+            // rest of that problem's items in one step
+            if (last && !live) atomicMax(a.work, a.probs[my_prob].w1);
             pending = __ballot_sync(FULL, live);
             if (!pending) continue;
         }
@@ -165,15 +172,13 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const GridDev *G = a.grids + prob;
         // the sub-tile: first point << 6 | points
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
-        const int tq = 32 / cnt;                    // targets per warp step
-        const int qi = lane / cnt, si = lane % cnt;
-        const bool sval = qi < tq;                  // the lane holds point si
+        const bool sval = si < cnt;
 
         // ---- 1. the lane's source point in the grid frame
         float Rf[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
-        const int jj = j0 + si;
+        const int jj = j0 + (sval ? si : 0);
         const int grp = a.pgroup[jj];
         const float4 anc = a.anchor[grp];
         const float4 zg = a.spos[a.gstart[grp]];
@@ -343,8 +348,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 __syncwarp();
                 if (qi == 0 && sval) n_cand += L;
 
-                // ---- 4. tq targets per step, one per group of lanes
-                for (int j = 0; j < L; j += tq) {
+                // ---- 4. TQ targets per step, one per group of lanes
+                for (int j = 0; j < L; j += TQ) {
                     const int idx = j + qi;
                     const bool act = sval && idx < L;
                     const int k = S.list[min(idx, L - 1)];
@@ -430,27 +435,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             }
         }
 
-        // ---- 5. per point: add its tq lanes in order, through the warp's
-        // staging area (free now)
-        {
-            float *red = reinterpret_cast<float *>(S.pos);
-            __syncwarp();
+        // ---- 5. per point: add the TQ lanes that share it
 #pragma unroll
-            for (int k = 0; k < NT; ++k) red[lane * (NT + 1) + k] = sval ? t[k] : 0.f;
-            __syncwarp();
-            if (lane < cnt)
+        for (int k = 0; k < NT; ++k)
 #pragma unroll
-                for (int k = 0; k < NT; ++k) {
-                    float x = red[lane * (NT + 1) + k];
-                    for (int q = 1; q < tq; ++q) x += red[(q * cnt + lane) * (NT + 1) + k];
-                    t[k] = x;
-                }
-            __syncwarp();
-        }
+            for (int o = SUB; o < 32; o <<= 1) t[k] += __shfl_xor_sync(FULL, t[k], o);
         float v[NSLOT];
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) v[k] = 0.f;
-        if (lane < cnt) {
+        if (qi == 0 && sval) {
             if (MODE == PAIR_EVAL) {
                 float Sf = t[0], Su0 = t[1], Su1 = t[2], Su2 = t[3];
                 float A00 = t[4], A01 = t[5], A02 = t[6], A11 = t[7], A12 = t[8], A22 = t[9];
@@ -503,14 +496,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         // warp's staging area (free now), lane k adds slot k
         float *tr = reinterpret_cast<float *>(S.pos);
         __syncwarp();
+        if (qi == 0)
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) tr[k * 33 + lane] = v[k];
+            for (int k = 0; k < NSLOT; ++k) tr[k * (SUB + 1) + si] = v[k];
         __syncwarp();
         float *out = a.part + (size_t)it * 64;
         if (lane < NSLOT) {
             float hs = 0.f, ls = 0.f;
-            for (int i2 = 0; i2 < cnt; ++i2) {
-                const float x = tr[lane * 33 + i2];
+#pragma unroll
+            for (int i2 = 0; i2 < SUB; ++i2) {
+                const float x = tr[lane * (SUB + 1) + i2];
                 const float sm = hs + x;
                 const float bp = sm - hs;
                 ls += (hs - (sm - bp)) + (x - bp);
@@ -580,40 +575,43 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
-    k_tile<MODE, ISO, FD><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
+    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int MODE, bool ISO, int FD>
+template <int MODE, bool ISO, int FD, int SUB>
 static int occupancy_t() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD>, PAIR_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32, 0);
     return nb;
 }
 
-#define PAIR_VARIANTS(X)                                                                                  \
-    X(PAIR_EVAL, false, 1) X(PAIR_EVAL, false, 3) X(PAIR_EVAL, true, 1) X(PAIR_EVAL, true, 3)             \
-    X(PAIR_LINESEARCH, false, 1) X(PAIR_LINESEARCH, false, 3) X(PAIR_LINESEARCH, true, 1)                 \
-    X(PAIR_LINESEARCH, true, 3)
+// Both passes in all four schedules (the line-search pass of G-CVO-1 runs
+// over the same items as the evaluation pass).
+#define PAIR_VARIANTS_M(X, M)                                                                 \
+    X(M, false, 1, 4) X(M, false, 3, 4) X(M, true, 1, 4) X(M, true, 3, 4) X(M, false, 1, 8)    \
+    X(M, false, 3, 8) X(M, true, 1, 8) X(M, true, 3, 8) X(M, false, 1, 16) X(M, false, 3, 16) \
+    X(M, true, 1, 16) X(M, true, 3, 16) X(M, false, 1, 32) X(M, false, 3, 32) X(M, true, 1, 32) X(M, true, 3, 32)
+#define PAIR_VARIANTS(X) PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH)
 
-// The kernel adapts its lane layout to each sub-tile; sub only shapes the
-// packing.
 int pair_sub_for(int, int sub) { return sub == 4 || sub == 16 || sub == 32 ? sub : 8; }
 
-int pair_blocks_per_sm(int mode, bool iso, int fd, int) {
-#define OCC(M, I, F) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1)) return occupancy_t<M, I, F>();
+int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
+    sub = pair_sub_for(mode, sub);
+#define OCC(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return occupancy_t<M, I, F, U>();
     PAIR_VARIANTS(OCC)
 #undef OCC
     return 1;
 }
 
-cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int, int grid, cudaStream_t s) {
-#define L(M, I, F) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1)) return launch_tile_t<M, I, F>(a, grid, s);
+cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s) {
+    sub = pair_sub_for(mode, sub);
+#define L(M, I, F, U) \
+    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return launch_tile_t<M, I, F, U>(a, grid, s);
     PAIR_VARIANTS(L)
 #undef L
     return cudaErrorInvalidValue;
