@@ -6,7 +6,7 @@
 // The source points of a problem are sorted by Morton code and cut into
 // sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho
 // (or 2 rho, the coarser cut the autotuner may pick).  Every warp works alone
-// on one sub-tile at a time (a work item); it takes PAIR_GRAB items per
+// on one sub-tile at a time (a work item); it takes up to PAIR_GRAB items per
 // atomic on the global counter, so the counter is touched rarely, and no warp
 // waits for another.
 //  1. Every point is moved into the target grid's frame with T^-1
@@ -140,22 +140,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
     __syncwarp();
     unsigned parity = 0;
     const int n_items = *a.n_items;
-
+    // items per grab: up to PAIR_GRAB, fewer when there are few items per
+    // warp, so that small problems still spread over the whole GPU
+    const int grab = max(1, min(PAIR_GRAB, n_items / (int)(gridDim.x * PAIR_WARPS * 4)));
     int gbase = 0;          // first item of the current grab
     unsigned pending = 0;   // lanes of the grab whose item is still to do
     int my_word = 0, my_prob = 0;
     for (;;) {
         if (!pending) {
-            // grab PAIR_GRAB items; lane l looks at item gbase + l
-            if (lane == 0) gbase = atomicAdd(a.work, PAIR_GRAB);
+            // grab `grab` items; lane l looks at item gbase + l
+            if (lane == 0) gbase = atomicAdd(a.work, grab);
             gbase = __shfl_sync(FULL, gbase, 0);
             if (gbase >= n_items) break;
             bool live = false, last = false;
-            if (lane < PAIR_GRAB && gbase + lane < n_items) {
+            if (lane < grab && gbase + lane < n_items) {
                 my_prob = a.item_prob[gbase + lane];
                 my_word = a.items[gbase + lane];
                 live = a.probs[my_prob].status == 0;   // finished problems are skipped
-                last = lane == PAIR_GRAB - 1 || gbase + lane == n_items - 1;
+                last = lane == grab - 1 || gbase + lane == n_items - 1;
             }
             // the grab ends in a finished problem: move the counter past the
             // rest of that problem's items in one step
