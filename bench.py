@@ -33,7 +33,12 @@ if ROOT not in sys.path:
 
 METRIC = "G-CVO kernel pair-evals/s & registrations/s at equal pose error vs plain"
 UNIT = "pair-evals/s"
-FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation, see the design doc
+FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
+# DRAM bytes per pair-eval of the pair kernel, from one ncu capture of the
+# kernel whose source hashes to PAIR_KERNEL_SHA (profiles/k_tile_lidar20.md);
+# the traffic is reported only while the kernel source still matches
+PAIR_DRAM_BYTES_PER_PAIR = 5.13
+PAIR_KERNEL_SHA = "4c668cfa266ec16f"
 EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
 KNN = 10
 
@@ -268,13 +273,21 @@ def run_gcvo(args, rank, world):
 
     # ---- roofline of the pair kernel
     n_launch = max(1, prof["n_pair_launches"])
+    schedule = G.gcvo_pair_schedule(ctx)
+    import hashlib
+    src = os.path.join(ROOT, "paper_2606_10019_gb300", "csrc", "tile.cu")
+    same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == PAIR_KERNEL_SHA
+    traffic = PAIR_DRAM_BYTES_PER_PAIR * pair_evals / n_launch if same_kernel else None
     t_pair = prof["pair_kernel_ms"] / 1e3
     achieved = pair_evals * FLOP_PER_PAIR / t_pair / 1e12 if t_pair > 0 else 0.0
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_ghz = (clk or {}).get("sm_max_mhz", 2070.0) / 1e3
     peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pair (EVAL)", "launches": prof["n_pair_launches"],
+                "traffic": traffic, "traffic_basis": "DRAM bytes per pair-eval from an ncu capture of k_tile on 20 "
+                "frames (5.13 B) x mean pair-evals per launch; null if the kernel changed since",
+                "kernel": "k_tile (evaluation pass)", "launches": prof["n_pair_launches"],
+                "points_per_subtile": schedule,
                 "avg_launch_ms": prof["pair_kernel_ms"] / n_launch,
                 "pair_kernel_share_of_step": t_pair / t_dev if t_dev > 0 else None,
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz (max SM clock)"}

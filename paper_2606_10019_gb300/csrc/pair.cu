@@ -459,7 +459,9 @@ __device__ void refresh_anchors(const FinalizeArgs &a, int prob, ProbDev *P) {
         for (int k = 0; k < 9; ++k) P->R32[k] = (float)R[k];
 }
 
-__global__ void __launch_bounds__(256) k_finalize(FinalizeArgs a) {
+constexpr int FIN_THREADS = 512;   // 16 parts x 32 slots of the partial sums
+
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(FinalizeArgs a) {
     const int prob = blockIdx.x;
     if (prob >= a.n_problems) return;
     ProbDev *P = a.probs + prob;
@@ -468,8 +470,8 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeArgs a) {
         refresh_anchors(a, prob, P);
         return;
     }
-    __shared__ double red[256];
-    __shared__ long long cred[256];
+    __shared__ double red[FIN_THREADS];
+    __shared__ long long cred[FIN_THREADS];
     __shared__ double tot[32];
     __shared__ long long ctot[4];
     const int g0 = P->w0, g1 = P->w1;   // packed work items of this problem
@@ -477,7 +479,8 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeArgs a) {
     // compensated FP32 sum of the (hi, lo) group partials, one FP64 combine
     float H = 0.f, Lo = 0.f;
     long long cacc = 0;
-    for (int g = g0 + part; g < g1; g += 8) {
+#pragma unroll 4
+    for (int g = g0 + part; g < g1; g += FIN_THREADS / 32) {
         const float *p = a.part + (size_t)g * 64;
         float h = p[slot], l = p[32 + slot];
         float sm = H + h;
@@ -493,8 +496,8 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeArgs a) {
     if (threadIdx.x < 32) {
         double sm = 0.0;
         long long cs = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
+#pragma unroll 8
+        for (int q = 0; q < FIN_THREADS / 32; ++q) {
             sm += red[q * 32 + threadIdx.x];
             cs += cred[q * 32 + threadIdx.x];
         }
@@ -610,7 +613,7 @@ __global__ void k_src_groups(SrcArgs a, const unsigned long long *keys, const in
 // Host launchers.
 // ---------------------------------------------------------------------------
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
-    k_finalize<<<a.n_problems, 256, 0, s>>>(a);
+    k_finalize<<<a.n_problems, FIN_THREADS, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
