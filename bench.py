@@ -176,11 +176,20 @@ def run_gcvo(args, rank, world):
     grids = [None] * (F - 1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(xyz_in, feat_in):
+    def step(xyz_in, feat_in, marks=None):
+        # marks: three CUDA events recorded after the covariances, the grids
+        # and the registration (phase times of the timed steps)
         G.gcvo_estimate_covariances_batched(ctx, xyz_in, kp, cov)
+        if marks:
+            marks[0].record(stream)
         grids[:] = G.gcvo_build_grids_batched(ctx, xyz_in[:-1], cov[:-1], feat_in[:-1], kp, grids)
+        if marks:
+            marks[1].record(stream)
         probs = [(grids[k], xyz_in[k + 1], cov[k + 1], feat_in[k + 1], np.eye(4)) for k in range(F - 1)]
-        return G.gcvo_register_batched(ctx, probs, sp, want_log=True)
+        out = G.gcvo_register_batched(ctx, probs, sp, want_log=True)
+        if marks:
+            marks[2].record(stream)
+        return out
 
     for _ in range(args.warmup):
         out = step(xyz, feat)
@@ -198,16 +207,21 @@ def run_gcvo(args, rank, world):
     kept = 0
     regs = 0
     t_wall0 = time.perf_counter()
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     for s in range(args.steps):
         flush.zero_()                       # L2 flush, outside the events
         ev[s][0].record(stream)
-        T_est, logs, n_iter, status = step(xyz, feat)
+        T_est, logs, n_iter, status = step(xyz, feat, marks[s])
         ev[s][1].record(stream)
         pair_evals += sum(L["n_pairs"] for lg in logs for L in lg)
         kept += sum(L["n_kept"] for lg in logs for L in lg)
         regs += len(T_est)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
+    schedule = G.gcvo_pair_schedule(ctx)     # the autotuner's choice for this workload
+    phases = {"covariances": float(np.mean([ev[s][0].elapsed_time(marks[s][0]) for s in range(args.steps)])),
+              "grids": float(np.mean([marks[s][0].elapsed_time(marks[s][1]) for s in range(args.steps)])),
+              "registration": float(np.mean([marks[s][1].elapsed_time(marks[s][2]) for s in range(args.steps)]))}
     clk = clocks.stop()
     prof = G.gcvo_profile_read(ctx)
     G.gcvo_profile_enable(ctx, False)
@@ -273,7 +287,6 @@ def run_gcvo(args, rank, world):
 
     # ---- roofline of the pair kernel
     n_launch = max(1, prof["n_pair_launches"])
-    schedule = G.gcvo_pair_schedule(ctx)
     import hashlib
     src = os.path.join(ROOT, "paper_2606_10019_gb300", "csrc", "tile.cu")
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == PAIR_KERNEL_SHA
@@ -312,6 +325,7 @@ def run_gcvo(args, rank, world):
                        "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
                        "parallelism": f"{world} independent replica(s), no collective"},
             "registrations_per_s": regs_all / t_dev,
+            "phase_ms_per_step": phases,
             "pair_evals_per_step": pair_evals / args.steps, "kept_pairs_per_step": kept / args.steps,
             "iterations_mean": float(np.mean(iters)), "converged": f"{n_conv}/{len(iters)}",
             "pose_error_vs_truth": errs,
