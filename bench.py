@@ -73,7 +73,8 @@ def make_frames(n_frames: int, rank: int):
     touched).  Each rank gets its own street and trajectory."""
     import multiprocessing as mp
     from paper_2606_10019_gb300 import datagen as D
-    config = 2 + 100 * rank
+    from paper_2606_10019_gb300 import replicas as R
+    config = R.rank_config(2, rank)
     seq = D.LidarSequence(n_frames=n_frames, config=config)
     nproc = max(1, min(16, os.cpu_count() or 1))
     with mp.get_context("spawn").Pool(nproc) as pool:
@@ -227,16 +228,10 @@ def run_gcvo(args, rank, world):
     G.gcvo_profile_enable(ctx, False)
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(ms_steps) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = torch.tensor([float(pair_evals), float(regs)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tot)
-        t_dev = float(t.item())
-        pair_evals_all, regs_all = tot.tolist()
-    else:
-        pair_evals_all, regs_all = float(pair_evals), float(regs)
+    from paper_2606_10019_gb300 import replicas as R
+    pair_evals_all, t_max = R.combine(pair_evals, t_dev, dev)
+    regs_all, _ = R.combine(regs, t_dev, dev)
+    t_dev = t_max
     value = pair_evals_all / t_dev
     errs = pose_errors(list(T_est), T_true)
     n_conv = int(np.sum(status == 0))
