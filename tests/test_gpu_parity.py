@@ -306,6 +306,31 @@ def test_profiled_register_counts_and_times_pair_launches(env):
 
 
 @pytest.mark.slow
+def test_batched_lidar_launch_configuration_sampled(env):
+    """The benchmark's launch configuration -- several full-size voxelised
+    LiDAR frame pairs in one batched call, schedule left to the autotuner --
+    checked on sampled problems: the first two iterations' f and g against
+    the oracle at the GPU's own iterates."""
+    O, G, ctx, dev = env
+    seq = D.LidarSequence(n_frames=5)
+    frames = [seq.frame(k) for k in range(5)]
+    covs = [O.covariances(x, 10, 0.09, 100.0).astype(np.float32) for x, _ in frames]
+    kp = G.kernel_params(eig_max=0.09)
+    xyz = [soa(x, dev) for x, _ in frames]
+    feat = [soa(f, dev) for _, f in frames]
+    cv = [soa(c, dev) for c in covs]
+    grids = G.gcvo_build_grids_batched(ctx, xyz[:-1], cv[:-1], feat[:-1], kp)
+    probs = [(grids[k], xyz[k + 1], cv[k + 1], feat[k + 1], np.eye(4)) for k in range(4)]
+    T, logs, n_iter, st = G.gcvo_register_batched(ctx, probs, G.solver_params(k_max=2, eps_tol=1e-8), want_log=True)
+    for k in (0, 3):
+        prob = O.Problem.make(frames[k][0], covs[k], frames[k][1], frames[k + 1][0], covs[k + 1], frames[k + 1][1])
+        for it in range(2):
+            o = O.evaluate(prob, logs[k][it]["T"], O.KernelParams(cutoff=3.0))
+            assert rel_f(logs[k][it]["f"], o.f) <= TOL
+            assert rel_g(logs[k][it]["g"], o.g, o.gabs) <= TOL
+
+
+@pytest.mark.slow
 def test_register_lidar_frame_pair(env):
     """Config 2 at full size (one voxelised LiDAR frame pair, ~14k points):
     GPU vs oracle at sampled iterates and at the final pose."""
