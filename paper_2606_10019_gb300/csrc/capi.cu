@@ -177,6 +177,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->grp_start.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->grp_count.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->grp_prob.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->grp_first.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->items.ensure(N * sizeof(int4), s));
     GCVO_TRY(ctx->item_prob.ensure(N * sizeof(int), s));
     GCVO_TRY(ctx->pgroup.ensure(N * sizeof(int), s));
@@ -208,6 +209,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sa.sca = ctx->src_ca.as<float4>();
     sa.scb = ctx->src_cb.as<float4>();
     sa.pgroup = ctx->pgroup.as<int>();
+    sa.gfirst = ctx->grp_first.as<float4>();
     sa.feat_dim = P.feat_dim;
     sa.iso = P.iso;
     GCVO_CUDA(launch_src_keys(sa, np, max_n, s));
@@ -398,6 +400,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     a.items = ctx->items.as<int>();
     a.item_prob = ctx->item_prob.as<int>();
     a.pgroup = ctx->pgroup.as<int>();
+    a.gfirst = ctx->grp_first.as<float4>();
     a.n_items = P.d_nitems;
     a.probs = ctx->probs.as<ProbDev>();
     a.grids = ctx->grids.as<GridDev>();
@@ -720,13 +723,13 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->sort_keys, &ctx->sort_vals, &ctx->sort_tmp, &ctx->scan_tmp, &ctx->small,
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
-                      &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g,
+                      &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g, &ctx->grp_first,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
                       &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup, &ctx->pack_tmp};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
         DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
-                        &kg->col_range, &kg->cell_z, &kg->vox_first};
+                        &kg->vox_first};
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
@@ -855,8 +858,6 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
     s.cell_start.release();
     s.hkeys.release();
     s.hval.release();
-    s.col_range.release();
-    s.cell_z.release();
     s.vox_first.release();
     delete grid;
     return GCVO_OK;

@@ -77,9 +77,7 @@ struct GridDev {
     const int *cell_start;    // n_cells + 1 offsets into the sorted points
     const unsigned long long *hkeys;  // open-addressing table of voxel keys
     const int *hval;          // voxel index of each table slot
-    const int2 *col_range;    // per (cx, cy) column: its voxels [x, y) in sorted order
     const int *vox_first;     // target grids: first sorted point of every voxel, dense (+1 entry)
-    const int *cell_z;        // cz of each occupied voxel
     unsigned long long hmask; // table size - 1 (power of two)
     double origin[3];         // o (target grid) or 0 (kNN grid), double
     float corner[3];          // lowest voxel corner, in the coordinates of pos
@@ -157,7 +155,7 @@ __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, f
 // ---------------------------------------------------------------------------
 struct GridStore {
     GridDev d{};
-    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval, col_range, cell_z, vox_first;
+    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval, vox_first;
 };
 
 // Build a grid from SoA inputs.  absolute: keep absolute coordinates and no
@@ -187,7 +185,7 @@ struct gcvo_ctx {
     gcvo::DevBuf sort_keys, sort_vals, sort_tmp, scan_tmp, small;
     gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
     gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
-    gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g;
+    gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g, grp_first;
     gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup, pack_tmp;
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_retry;

@@ -30,17 +30,14 @@ __global__ void k_heads(const unsigned long long *keys, int64_t n, int *head) {
     head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
-__global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t n, int dz, int *cell_start,
-                        unsigned long long *hkeys, int *hval, unsigned long long hmask, int2 *col_range,
-                        int *cell_z) {
+__global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t n, int *cell_start,
+                        unsigned long long *hkeys, int *hval, unsigned long long hmask) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned long long k = keys[i];
-    const unsigned long long col = k / (unsigned long long)dz;
     if (i == 0 || k != keys[i - 1]) {
         int c = incl[i] - 1;
         cell_start[c] = (int)i;
-        cell_z[c] = (int)(k - col * (unsigned long long)dz);
         unsigned long long s = hash_key(k) & hmask;
         for (;;) {
             unsigned long long prev = atomicCAS(hkeys + s, EMPTY_KEY, k);
@@ -50,22 +47,8 @@ __global__ void k_cells(const unsigned long long *keys, const int *incl, int64_t
             }
             s = (s + 1) & hmask;
         }
-        // voxels of one (cx, cy) column are consecutive: record where each
-        // column starts and where the previous one ends
-        if (i == 0) {
-            col_range[col].x = c;
-        } else {
-            const unsigned long long pcol = keys[i - 1] / (unsigned long long)dz;
-            if (pcol != col) {
-                col_range[col].x = c;
-                col_range[pcol].y = c;
-            }
-        }
     }
-    if (i == n - 1) {
-        cell_start[incl[i]] = (int)n;
-        col_range[col].y = incl[i];
-    }
+    if (i == n - 1) cell_start[incl[i]] = (int)n;
 }
 
 // Points per voxel, stored one slot up: after an inclusive scan, entry v is
@@ -179,8 +162,6 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
         }
     }
     if (prod > 4.0e18) return GCVO_ERR_CAPACITY;
-    const double n_columns = (double)g.dims[0] * (double)g.dims[1];
-    if (n_columns > (double)(1 << 27)) return GCVO_ERR_CAPACITY;
     int bits = 1;
     while ((double)(1ull << bits) < prod && bits < 62) ++bits;
 
@@ -214,14 +195,10 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(out.cell_start.ensure((n_cells + 1) * sizeof(int), s));
     GCVO_TRY(out.hkeys.ensure(H * sizeof(unsigned long long), s));
     GCVO_TRY(out.hval.ensure(H * sizeof(int), s));
-    GCVO_TRY(out.col_range.ensure((size_t)n_columns * sizeof(int2), s));
-    GCVO_TRY(out.cell_z.ensure((size_t)(n_cells + 1) * sizeof(int), s));
-    GCVO_CUDA(cudaMemsetAsync(out.col_range.ptr, 0, (size_t)n_columns * sizeof(int2), s));
     k_fill_u64<<<(unsigned)((H + 255) / 256), 256, 0, s>>>(out.hkeys.as<unsigned long long>(), (int64_t)H,
                                                           EMPTY_KEY);
-    k_cells<<<blocks, 256, 0, s>>>(keys, incl, n, g.dims[2], out.cell_start.as<int>(),
-                                   out.hkeys.as<unsigned long long>(), out.hval.as<int>(), H - 1,
-                                   out.col_range.as<int2>(), out.cell_z.as<int>());
+    k_cells<<<blocks, 256, 0, s>>>(keys, incl, n, out.cell_start.as<int>(), out.hkeys.as<unsigned long long>(),
+                                   out.hval.as<int>(), H - 1);
     k_reorder<<<blocks, 256, 0, s>>>(xyz, kp.kernel_mode == 0 ? cov : nullptr, feat, kp.feat_dim, n, vals, g,
                                      absolute, out.pos.as<float4>(), out.ca.as<float4>(), out.cb.as<float4>(),
                                      out.orig.as<int>());
@@ -243,8 +220,6 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.cell_start = out.cell_start.as<int>();
     g.hkeys = out.hkeys.as<unsigned long long>();
     g.hval = out.hval.as<int>();
-    g.col_range = out.col_range.as<int2>();
-    g.cell_z = out.cell_z.as<int>();
     g.vox_first = absolute ? nullptr : out.vox_first.as<int>();
     g.hmask = H - 1;
     g.n = (int)n;

@@ -218,6 +218,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.anchor = fa.anchor;
     pa.gstart = fa.gstart;
     pa.pgroup = reinterpret_cast<const int *>(base + NA_PGROUP);
+    pa.gfirst = pa.spos;   // every point is its own group
     pa.items = reinterpret_cast<const int *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
     pa.n_items = words + 1;

@@ -603,6 +603,7 @@ __global__ void k_src_groups(SrcArgs a, const unsigned long long *keys, const in
     if (!a.iso && d.cov)
         for (int k = 0; k < 6; ++k) s[k] = d.cov[k * d.n + li];
     a.spos[i] = make_float4(x, y, z, f0);
+    if (head) a.gfirst[g] = make_float4(x, y, z, 0.f);
     a.sca[i] = make_float4(s[0], s[1], s[2], s[3]);
     a.scb[i] = make_float4(s[4], s[5], f1, f2);
 }

@@ -43,6 +43,7 @@ struct PairArgs {
     const float4 *anchor;      // per group: R^T (z_g - t) - o, z_g its first point
     const int *gstart;         // first point of each group
     const int *pgroup;         // group of each point
+    const float4 *gfirst;      // position of each group's first point
     const int *items;          // per item (sub-tile): first point << 6 | points
     const int *item_prob;
     const int *n_items;
@@ -86,6 +87,7 @@ struct SrcArgs {
     unsigned *status_word;
     float4 *spos, *sca, *scb;
     int *pgroup;
+    float4 *gfirst;
     int feat_dim;
     int iso;
 };

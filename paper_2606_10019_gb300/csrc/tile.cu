@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const int jj = j0 + (sval ? si : 0);
         const int grp = a.pgroup[jj];
         const float4 anc = a.anchor[grp];
-        const float4 zg = a.spos[a.gstart[grp]];
+        const float4 zg = a.gfirst[grp];
         const float4 z = a.spos[jj];
         const float4 zb = a.scb[jj];
         const float e0 = z.x - zg.x, e1 = z.y - zg.y, e2 = z.z - zg.z;
