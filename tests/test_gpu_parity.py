@@ -331,6 +331,57 @@ def test_batched_lidar_launch_configuration_sampled(env):
 
 
 @pytest.mark.slow
+def test_rgbd_frame_pair_full_size(env):
+    """Config 3: an RGB-D frame pair (2 cm voxels, RGB features, c_ij the dot
+    product) subsampled to the configured ~20k points, evaluated at the
+    identity and at the true pose against the oracle."""
+    O, G, ctx, dev = env
+    seq = D.RgbdSequence(n_frames=2)
+    pr = seq.pair(0)
+    rng = np.random.default_rng(33)
+    tx, tf = D.subsample(rng, pr.tgt_xyz, pr.tgt_feat, 20000)
+    sx, sf = D.subsample(rng, pr.src_xyz, pr.src_feat, 20000)
+    pair = D.Pair(tx, tf, sx, sf, pr.T_true)
+    lam = 4e-4
+    case = Case(O, pair, O.KernelParams(cutoff=3.0), eig_max=lam)
+    case.gpu(G, ctx, dev, G.kernel_params(eig_max=lam, feat_dim=3))
+    for T in (np.eye(4), pair.T_true):
+        _check_eval(O, G, ctx, case, T)
+
+
+@pytest.mark.slow
+def test_uneven_batch_sampled(env):
+    """Config 4 style: problems of uneven size (1k to 20k points; corner
+    scenes and a LiDAR pair) from perturbed starts in one batched call; the
+    first two iterations of sampled problems against the oracle at the GPU's
+    iterates."""
+    O, G, ctx, dev = env
+    rng = np.random.default_rng(44)
+    cases, probs = [], []
+    specs = [("corner", 1000), ("corner", 20000), ("lidar", 6000), ("corner", 4000)]
+    seq = D.LidarSequence(n_frames=2)
+    for k, (kind, n) in enumerate(specs):
+        if kind == "corner":
+            pair = D.make_corner_pair(frame=500 + k, n_src=n, n_tgt=n)
+            lam = 0.01
+        else:
+            lp = seq.pair(0)
+            tx, tf = D.subsample(rng, lp.tgt_xyz, lp.tgt_feat, n)
+            sx, sf = D.subsample(rng, lp.src_xyz, lp.src_feat, n)
+            pair = D.Pair(tx, tf, sx, sf, lp.T_true)
+            lam = 0.09
+        c = Case(O, pair, O.KernelParams(cutoff=3.0), eig_max=lam).gpu(G, ctx, dev, G.kernel_params(eig_max=lam))
+        cases.append(c)
+        probs.append((c.grid, *c.src, D.perturb(rng, 30.0, 0.5) @ pair.T_true))
+    T, logs, n_iter, st = G.gcvo_register_batched(ctx, probs, G.solver_params(k_max=2, eps_tol=1e-8), want_log=True)
+    for k in (1, 2):
+        for it in range(2):
+            o = O.evaluate(cases[k].prob, logs[k][it]["T"], cases[k].kp_o)
+            assert rel_f(logs[k][it]["f"], o.f) <= TOL
+            assert rel_g(logs[k][it]["g"], o.g, o.gabs) <= TOL
+
+
+@pytest.mark.slow
 def test_register_lidar_frame_pair(env):
     """Config 2 at full size (one voxelised LiDAR frame pair, ~14k points):
     GPU vs oracle at sampled iterates and at the final pose."""
