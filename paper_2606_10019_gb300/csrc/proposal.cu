@@ -335,7 +335,7 @@ __global__ void k_head_fwd(Net net, const float *feat, float *y1, float *y2, flo
 __global__ void k_head_bwd(Net net, int B, const float *feat, const float *y1, const float *y2, const float *out,
                            const float *label, float *d_out, float *d_y1, float *d_y2, float *d_feat, float *loss) {
     const int b = blockIdx.x;
-    __shared__ float dz2[128], dy2[128], dy1[256], sd_out[6];
+    __shared__ float dy2[128], dy1[256], sd_out[6];
     if (threadIdx.x < 6) {
         float d = out[(size_t)b * 6 + threadIdx.x] - label[(size_t)b * 6 + threadIdx.x];
         sd_out[threadIdx.x] = 2.0f * d / (float)B;
@@ -347,7 +347,6 @@ __global__ void k_head_bwd(Net net, int B, const float *feat, const float *y1, c
         const int i = threadIdx.x;
         float s = 0.f;
         for (int o = 0; o < 6; ++o) s += __bfloat162float(net.w[net.off[H3] + o * 128 + i]) * sd_out[o];
-        dz2[i] = s;
         float d = y2[(size_t)b * 128 + i] > 0.f ? s : 0.f;
         dy2[i] = d;
         d_y2[(size_t)b * 128 + i] = d;
