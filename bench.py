@@ -236,6 +236,8 @@ def run_gcvo(args, rank, world):
     errs = pose_errors(list(T_est), T_true)
     n_conv = int(np.sum(status == 0))
     iters = n_iter.tolist()
+    # the paper evaluates every pair: N_X * N_Z per problem and iteration
+    dense_pairs = float(sum(int(n_iter[k]) * n_pts[k] * n_pts[k + 1] for k in range(F - 1)))
 
     # ---- end to end: host (pinned) inputs copied in every step, poses read back
     hx = [torch.from_numpy(np.ascontiguousarray(x.T)).pin_memory() for x, _ in frames]
@@ -322,6 +324,7 @@ def run_gcvo(args, rank, world):
             "registrations_per_s": regs_all / t_dev,
             "phase_ms_per_step": phases,
             "pair_evals_per_step": pair_evals / args.steps, "kept_pairs_per_step": kept / args.steps,
+            "dense_equivalent_pairs_per_s": dense_pairs * args.steps / t_dev,
             "iterations_mean": float(np.mean(iters)), "converged": f"{n_conv}/{len(iters)}",
             "pose_error_vs_truth": errs,
             "roofline": roofline,
