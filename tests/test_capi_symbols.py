@@ -55,3 +55,24 @@ def test_invalid_arguments_are_rejected_before_any_device_work(libpath):
     assert L.gcvo_grid_destroy(None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_eval(None, None, None, None, None, 0, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_register(None, None, None, None, None, 0, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_register_batched(None, 0, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_estimate_covariances_batched(None, 1, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_build_grids_batched(None, 1, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_pair_schedule(None, 8, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_profile_enable(None, 1) == G.GCVO_ERR_INVALID_ARG
+
+
+def test_eval_static_rejects_bad_arguments_without_touching_a_device(libpath):
+    """The no-allocation entry point checks its arguments (missing inputs,
+    empty input, more points than its static scratch holds) before any CUDA
+    call."""
+    from paper_2606_10019_gb300 import gcvo as G
+    L = G.lib()
+    P = ctypes.c_void_p
+    L.gcvo_eval_static.argtypes = [P, P, P, P, ctypes.c_int64, P, P, P, P, P]
+    f = ctypes.c_double()
+    g = (ctypes.c_double * 6)()
+    H = (ctypes.c_double * 36)()
+    T = (ctypes.c_double * 16)(*[1.0 if k % 5 == 0 else 0.0 for k in range(16)])
+    assert L.gcvo_eval_static(None, None, None, None, 10, T, None, ctypes.byref(f), g, H) == G.GCVO_ERR_INVALID_ARG
+
