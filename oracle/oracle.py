@@ -303,6 +303,77 @@ def gn_step(res: EvalResult) -> np.ndarray:
     return np.linalg.solve(-res.H, res.g)
 
 
+def _sym6_mats(c: np.ndarray) -> np.ndarray:
+    """(n, 6) covariances (xx, xy, xz, yy, yz, zz) as (n, 3, 3) matrices."""
+    m = np.empty((len(c), 3, 3))
+    m[:, 0, 0], m[:, 0, 1], m[:, 0, 2] = c[:, 0], c[:, 1], c[:, 2]
+    m[:, 1, 0], m[:, 1, 1], m[:, 1, 2] = c[:, 1], c[:, 3], c[:, 4]
+    m[:, 2, 0], m[:, 2, 1], m[:, 2, 2] = c[:, 2], c[:, 4], c[:, 5]
+    return m
+
+
+def grad_derivative(prob: Problem, T, kp: KernelParams, terms: bool = False):
+    """G-CVO-E (Sec. 3.4, the directional derivative of Eq. (10) with all
+    four terms): the 6x6 matrix D with D @ xi = D(g)[xi], g the gradient of
+    Lemma 1, under the right perturbation T exp(xi^).  Per pair, with
+    p = R^T (z - t), r = x - p, Sigma' = R^T Sigma_z R, A = (Sigma_x +
+    Sigma')^-1, y = A r, w = c_ij sigma^2 exp(-r^T A r / 2) and g = -sum w
+    J^T y, J = [-p^, I]:
+        dp = -(omega x p + v),  dr = -dp,
+        dSigma' = Sigma' omega^ - omega^ Sigma',  dA = -A dSigma' A,
+        dw = -w (y . dr + r . dA r / 2),
+        D(g) = -sum [dw J^T y + w (dp x y, 0) + w J^T dA r + w J^T A dr].
+    The last term alone is -M (the Gauss-Newton part).  Pairs beyond the
+    cutoff contribute nothing.  All pairs at once in NumPy (small clouds).
+    With terms=True also returns the four terms' matrices."""
+    T = _d(T)
+    R, t = T[:3, :3], T[:3, 3]
+    p = (prob.src - t) @ R                               # rows R^T (z - t)
+    r = prob.tgt[:, None, :] - p[None, :, :]             # (nt, ns, 3)
+    nt, ns = len(prob.tgt), len(prob.src)
+    if kp.kernel_mode == 1:
+        Szr = np.zeros((ns, 3, 3))
+        Sig = np.broadcast_to(np.eye(3) * kp.iso_ell ** 2, (nt, ns, 3, 3))
+    else:
+        Szr = np.einsum("ba,nbc,cd->nad", R, _sym6_mats(prob.src_cov), R)
+        Sig = _sym6_mats(prob.tgt_cov)[:, None] + Szr[None]
+    A = np.linalg.inv(Sig)
+    y = np.einsum("ijab,ijb->ija", A, r)
+    d2 = np.einsum("ija,ija->ij", r, y)
+    cij = prob.tgt_feat @ prob.src_feat.T
+    w = cij * kp.sigma2 * np.exp(-0.5 * d2)
+    if kp.cutoff > 0:
+        w = np.where(d2 <= kp.cutoff ** 2, w, 0.0)
+    Jty = np.concatenate([np.cross(p[None], y), y], axis=-1)          # J^T y
+    parts = np.zeros((4, 6, 6))
+    for k in range(6):
+        xi = np.eye(6)[k]
+        om, v = xi[:3], xi[3:]
+        dp = -(np.cross(om, p) + v)                                   # (ns, 3)
+        dr = -dp
+        W = hat3(om)
+        dS = Szr @ W - W @ Szr                                        # (ns, 3, 3)
+        dA = -np.einsum("ijab,jbc,ijcd->ijad", A, dS, A)
+        dAr = np.einsum("ijab,ijb->ija", dA, r)
+        dw = -w * (np.einsum("ija,ja->ij", y, dr) + 0.5 * np.einsum("ija,ija->ij", r, dAr))
+        Adr = np.einsum("ijab,jb->ija", A, dr)
+        t1 = dw[..., None] * Jty
+        t2 = w[..., None] * np.concatenate([np.cross(dp[None], y), np.zeros_like(y)], axis=-1)
+        t3 = w[..., None] * np.concatenate([np.cross(p[None], dAr), dAr], axis=-1)
+        t4 = w[..., None] * np.concatenate([np.cross(p[None], Adr), Adr], axis=-1)
+        for q, tq in enumerate((t1, t2, t3, t4)):
+            parts[q, :, k] = -tq.sum(axis=(0, 1))
+    D = parts.sum(axis=0)
+    return (D, parts) if terms else D
+
+
+def exact_step(prob: Problem, T, kp: KernelParams, res: EvalResult) -> np.ndarray:
+    """G-CVO-E step: Newton with the exact Riemannian Hessian
+    H_E = D(g) + Gamma (Eq. 12), xi = -H_E^-1 g."""
+    H = grad_derivative(prob, T, kp) + res.Gamma
+    return np.linalg.solve(-H, res.g)
+
+
 def linesearch_poly(prob: Problem, T, xi, kp: KernelParams, literal: bool = False) -> np.ndarray:
     """c_k = sum_ij f_ij g^k_ij, k = 0..4, so that G(t) ~ sum_k c_k t^k."""
     P = _params(kp, prob.tgt_feat.shape[1])
@@ -350,7 +421,8 @@ def register(prob: Problem, T0, kp: KernelParams, order: int = 2, k_max: int = 2
              eps_tol: float = 1e-8, mu0: float = 1e-10, literal_ls: bool = False) -> RegisterResult:
     """Alg. 1: repeat {evaluate f, grad f (and H_GN) at T^(k); step xi^(k);
     T^(k+1) = T^(k) exp(xi^(k))} while ||xi^(k)||_1 >= eps_tol and k < k_max.
-    The first iteration always runs."""
+    order 2: G-CVO-2 (Eq. 13); 1: G-CVO-1 (Eq. 9); 3: G-CVO-E (Newton with
+    the exact Hessian).  The first iteration always runs."""
     T = _d(T0).copy()
     out = RegisterResult(T)
     xi_l1 = np.inf
@@ -359,6 +431,8 @@ def register(prob: Problem, T0, kp: KernelParams, order: int = 2, k_max: int = 2
         res = evaluate(prob, T, kp)
         if order == 2:
             xi = gn_step(res)
+        elif order == 3:
+            xi = exact_step(prob, T, kp, res)
         else:
             c = linesearch_poly(prob, T, res.g, kp, literal_ls)
             xi = linesearch_step(c, mu0) * res.g

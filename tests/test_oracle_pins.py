@@ -508,3 +508,61 @@ def test_first_order_minimum_step_must_be_small(oracle_mod):
     assert sum(O.pose_error(stay.T, ref.T)) < 1e-9
     leave = O.register(prob, ref.T, kp, order=1, k_max=20, eps_tol=0.0, mu0=1e-4)
     assert sum(O.pose_error(leave.T, ref.T)) > 1e-3
+
+
+def _small_problem(O, seed, n_t=70, n_s=60, iso=False):
+    rng = np.random.default_rng(seed)
+    pair = D.make_corner_pair(frame=900 + seed, n_src=n_s, n_tgt=n_t)
+    if iso:
+        return O.Problem.make(pair.tgt_xyz, None, pair.tgt_feat, pair.src_xyz, None, pair.src_feat), pair, rng
+    tc = O.covariances(pair.tgt_xyz, 10, 0.05, 20.0)
+    sc = O.covariances(pair.src_xyz, 10, 0.05, 20.0)
+    return O.Problem.make(pair.tgt_xyz, tc, pair.tgt_feat, pair.src_xyz, sc, pair.src_feat), pair, rng
+
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_exact_hessian_matches_fd_of_gradient(oracle_mod, iso):
+    """G-CVO-E: D(g)[e_k] against central differences of the Lemma-1
+    gradient along T exp(+-h e_k) (dense objective, so no pair crosses a
+    cutoff; Sigma' follows the rotation in both)."""
+    O = oracle_mod
+    prob, pair, rng = _small_problem(O, 3, iso=iso)
+    kp = O.KernelParams(cutoff=0.0, kernel_mode=1 if iso else 0, iso_ell=0.15)
+    T = pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)
+    Dg = O.grad_derivative(prob, T, kp)
+    h = 1e-5
+    for k in range(6):
+        e = np.eye(6)[k] * h
+        gp = O.evaluate(prob, T @ O.exp_se3(e), kp).g
+        gm = O.evaluate(prob, T @ O.exp_se3(-e), kp).g
+        fd = (gp - gm) / (2 * h)
+        assert np.abs(Dg[:, k] - fd).max() <= 1e-6 * np.abs(Dg).max(), (k, Dg[:, k], fd)
+
+
+def test_exact_hessian_last_term_is_gauss_newton(oracle_mod):
+    """Of the four terms of D(g), the one in D(r) alone is -M of Eq. (11)
+    (computed independently by the C oracle); the others are not zero for an
+    anisotropic kernel away from the optimum."""
+    O = oracle_mod
+    prob, pair, rng = _small_problem(O, 4)
+    kp = O.KernelParams(cutoff=3.0)
+    T = pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)
+    D, parts = O.grad_derivative(prob, T, kp, terms=True)
+    M = O.evaluate(prob, T, kp).M
+    assert np.allclose(parts[3], -M, rtol=1e-10, atol=1e-12 * np.abs(M).max())
+    assert np.abs(parts[0] + parts[1] + parts[2]).max() > 1e-3 * np.abs(M).max()
+
+
+def test_gcvo_e_reaches_the_gcvo2_solution(oracle_mod):
+    """Sec. 5.4: G-CVO-E (exact Hessian) and G-CVO-2 (Gauss-Newton) share the
+    stationary point; started near it, Newton with the exact Hessian
+    converges there in a few iterations."""
+    O = oracle_mod
+    prob, pair, rng = _small_problem(O, 5, n_t=120, n_s=110)
+    kp = O.KernelParams(cutoff=0.0)
+    ref = O.register(prob, np.eye(4), kp, order=2, k_max=200, eps_tol=1e-12)
+    start = ref.T @ O.exp_se3(rng.normal(size=6) * 0.01)
+    e = O.register(prob, start, kp, order=3, k_max=30, eps_tol=1e-12)
+    # compare the matrices: an arccos angle cannot resolve below ~1e-8 rad
+    assert np.abs(e.T - ref.T).max() < 1e-9, (np.abs(e.T - ref.T).max(), len(e.log))
+    assert len(e.log) < 15
