@@ -510,7 +510,7 @@ def test_first_order_minimum_step_must_be_small(oracle_mod):
     assert sum(O.pose_error(leave.T, ref.T)) > 1e-3
 
 
-def _small_problem(O, seed, n_t=70, n_s=60, iso=False):
+def _e_problem(O, seed, n_t=70, n_s=60, iso=False):
     rng = np.random.default_rng(seed)
     pair = D.make_corner_pair(frame=900 + seed, n_src=n_s, n_tgt=n_t)
     if iso:
@@ -526,7 +526,7 @@ def test_exact_hessian_matches_fd_of_gradient(oracle_mod, iso):
     gradient along T exp(+-h e_k) (dense objective, so no pair crosses a
     cutoff; Sigma' follows the rotation in both)."""
     O = oracle_mod
-    prob, pair, rng = _small_problem(O, 3, iso=iso)
+    prob, pair, rng = _e_problem(O, 3, iso=iso)
     kp = O.KernelParams(cutoff=0.0, kernel_mode=1 if iso else 0, iso_ell=0.15)
     T = pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)
     Dg = O.grad_derivative(prob, T, kp)
@@ -544,7 +544,7 @@ def test_exact_hessian_last_term_is_gauss_newton(oracle_mod):
     (computed independently by the C oracle); the others are not zero for an
     anisotropic kernel away from the optimum."""
     O = oracle_mod
-    prob, pair, rng = _small_problem(O, 4)
+    prob, pair, rng = _e_problem(O, 4)
     kp = O.KernelParams(cutoff=3.0)
     T = pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)
     D, parts = O.grad_derivative(prob, T, kp, terms=True)
@@ -558,7 +558,7 @@ def test_gcvo_e_reaches_the_gcvo2_solution(oracle_mod):
     stationary point; started near it, Newton with the exact Hessian
     converges there in a few iterations."""
     O = oracle_mod
-    prob, pair, rng = _small_problem(O, 5, n_t=120, n_s=110)
+    prob, pair, rng = _e_problem(O, 5, n_t=120, n_s=110)
     kp = O.KernelParams(cutoff=0.0)
     ref = O.register(prob, np.eye(4), kp, order=2, k_max=200, eps_tol=1e-12)
     start = ref.T @ O.exp_se3(rng.normal(size=6) * 0.01)
