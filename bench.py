@@ -277,10 +277,12 @@ def run_gcvo(args, rank, world):
 
     first = None
     batched = None
+    exact = None
     if not args.no_plain and rank == 0:
         fo = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(min(8, F - 1))]
         first = first_order_block(G, ctx, dev, fo, T_true[:len(fo)])
         batched = batched_block(G, ctx, dev, frames, T_true)
+        exact = exact_hessian_block(G, ctx, dev, probs, Tb)
 
     # ---- roofline of the pair kernel
     n_launch = max(1, prof["n_pair_launches"])
@@ -334,6 +336,7 @@ def run_gcvo(args, rank, world):
             "plain_vs_batched": plain,
             "first_order": first,
             "batched_uneven": batched,
+            "exact_hessian": exact,
             "learned_proposal": proposal,
             "cpu_baseline": cpu,
             "wall_s_timed": t_wall,
@@ -379,6 +382,37 @@ def first_order_block(G, ctx, dev, probs, T_true, k_max=20000):
                 "time_ratio_first_over_second": out["first_order"]["seconds"] / out["second_order"]["seconds"],
                 "first_vs_second_pose_diff_max": {"rot_deg": float(max(d_rot)), "trans_m": float(max(d_t))},
                 "paper": "up to 10x second-order over first-order, RTX 4090 (Sec. 5.4)"})
+    return out
+
+
+def exact_hessian_block(G, ctx, dev, probs, T_gn, iters=8):
+    """Cost of an iteration of G-CVO-E (Newton with the exact Hessian
+    H_E = D(g) + Gamma) against one of G-CVO-2 on the same batched frame
+    pairs, both started at the batched G-CVO-2 solutions and run for a fixed
+    number of iterations (eps_tol 0), where the exact Hessian is negative
+    definite and Newton stays put."""
+    import torch
+    out = {}
+    poses = {}
+    starts = [p[:4] + (T,) for p, T in zip(probs, T_gn)]
+    for name, order in (("second_order", 2), ("exact", 3)):
+        sp = G.solver_params(order=order, k_max=iters, eps_tol=0.0)
+        G.gcvo_register_batched(ctx, starts, sp)           # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        T, logs, n_iter, status = G.gcvo_register_batched(ctx, starts, sp, want_log=True)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        poses[name] = T
+        n_pairs = sum(sum(r["n_pairs"] for r in lg) for lg in logs)
+        out[name] = {"ms_per_iteration": t * 1e3 / iters, "pair_evals_per_s": n_pairs / t,
+                     "iterations": int(np.max(n_iter)),
+                     "failed": int(np.sum((status != G.GCVO_OK) & (status != G.GCVO_ERR_NOT_CONVERGED)))}
+    d = [float(np.abs(a - b).max()) for a, b in zip(poses["exact"], T_gn)]
+    out.update({"workload": f"{len(probs)} LiDAR frame pairs at their G-CVO-2 solutions, {iters} iterations, batched",
+                "exact_over_second_order_time": out["exact"]["ms_per_iteration"] /
+                out["second_order"]["ms_per_iteration"],
+                "exact_pose_drift_max": max(d)})
     return out
 
 

@@ -84,7 +84,9 @@ typedef struct {
 /* Solver parameters (Algorithm 1 inputs mu_0, k_max, eps_tol). */
 typedef struct {
     int order;          /* 2: G-CVO-2, Gauss-Newton step of Eq. (13);
-                           1: G-CVO-1, gradient step with the line search of Eq. (9) */
+                           1: G-CVO-1, gradient step with the line search of Eq. (9);
+                           3: G-CVO-E, Newton step xi = -H_E^{-1} g with the exact
+                              Riemannian Hessian H_E = D(g) + Gamma (Sec. 3.4, Eq. 12) */
     int k_max;          /* iteration limit, 1..GCVO_MAX_KMAX */
     double eps_tol;     /* stop when ||xi^(k)||_1 < eps_tol */
     double mu0;         /* G-CVO-1 minimum step of Eq. (9) */
@@ -209,9 +211,25 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
                       const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
                       double H[36], double *M_out, gcvo_eval_stats *stats);
 
+/* The G-CVO-E evaluation at pose T (row-major 4x4, host): f and g as in
+ * gcvo_eval, and H_E = D(g) + Gamma (row-major 6x6, host), where D(g) is
+ * the exact directional derivative of the gradient field of Lemma 1 under
+ * the right perturbation T exp(xi^) -- all four terms of the derivative of
+ * g = -sum f_ij J_j^T Sigma_ij^{-1} r_ij: the change of the kernel weight,
+ * of the lever arm p_j, of Sigma_ij^{-1} as R turns Sigma_j, and of r_ij
+ * (the last alone is the -M of Gauss-Newton) -- and Gamma is the
+ * connection term of Eq. (12).  D_out (host 6x6, may be NULL) receives
+ * D(g), which is not symmetric away from a critical point; stats may be
+ * NULL.  One pair pass (a third more partial storage and about twice the
+ * arithmetic per pair of gcvo_eval).  Synchronises the stream. */
+gcvo_status gcvo_eval_exact(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                            const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
+                            double H_E[36], double *D_out, gcvo_eval_stats *stats);
+
 /* Algorithm 1 from T0: at most k_max iterations of transform, pair
  * evaluation, reduction and update (G-CVO-2 solves (M - Gamma) xi = g, Eq.
- * (13); G-CVO-1 takes xi = mu g with mu from Eq. (9)), stopping when
+ * (13); G-CVO-1 takes xi = mu g with mu from Eq. (9); G-CVO-E solves
+ * -(D(g) + Gamma) xi = g, see gcvo_eval_exact), stopping when
  * ||xi||_1 < eps_tol.  T_out receives the final pose (row-major, host);
  * log (host, capacity k_max rows, may be NULL) the per-iteration values;
  * n_iter the number of iterations run.  Returns GCVO_ERR_NOT_CONVERGED (with
@@ -246,7 +264,7 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
  * for every input (host pointers are rejected, since copying them would need
  * a buffer), the target grid (built earlier with gcvo_build_grid), the
  * stream, and host outputs.  Source points are processed in the caller's
- * order, 32 per work item.
+ * order, 8 per work item.
  *  - n_src above 65536 returns GCVO_ERR_CAPACITY.
  *  - The first call on a device looks up the array's device address (a
  *    one-time set-up); make that first call before capturing a stream.

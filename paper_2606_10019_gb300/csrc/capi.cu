@@ -479,14 +479,27 @@ gcvo_status collect_profile(gcvo_ctx *ctx, bool keep = false) {
     return GCVO_OK;
 }
 
+// The second partial row that the G-CVO-E pass writes (slots 32..).
+gcvo_status exact_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
+    GCVO_TRY(ctx->partial2.ensure((size_t)std::max(P.n_items, 1) * 64 * sizeof(float), ctx->stream));
+    b.pa.part2 = ctx->partial2.as<float>();
+    b.fa.part2 = b.pa.part2;
+    return GCVO_OK;
+}
+
 // One iteration of Algorithm 1 on stream s: G-CVO-2 is a pair pass and the
 // Gauss-Newton finalize; G-CVO-1 a gradient pass, its finalize (direction),
-// the line-search pass and the step.
+// the line-search pass and the step; G-CVO-E the exact pass and the Newton
+// step with H_E = D(g) + Gamma.
 gcvo_status enqueue_iteration(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int order, cudaStream_t s,
                               bool capturing) {
     if (order == 2) {
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
         b.fa.mode = FIN_GN;
+        GCVO_CUDA(launch_finalize(b.fa, s));
+    } else if (order == 3) {
+        GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EXACT, s, capturing));
+        b.fa.mode = FIN_EXACT;
         GCVO_CUDA(launch_finalize(b.fa, s));
     } else {
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
@@ -538,7 +551,7 @@ gcvo_status capture_chunk(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int ord
 
 gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gcvo_solver_params *sp,
                          double *T_out, gcvo_iter_log *logs, int *n_iter, int *status) {
-    if (!sp || !T_out || (sp->order != 1 && sp->order != 2) || sp->k_max < 1 || sp->k_max > GCVO_MAX_KMAX ||
+    if (!sp || !T_out || sp->order < 1 || sp->order > 3 || sp->k_max < 1 || sp->k_max > GCVO_MAX_KMAX ||
         !(sp->eps_tol >= 0) || (sp->order == 1 && !(sp->mu0 > 0)))
         return GCVO_ERR_INVALID_ARG;
     cudaStream_t s = ctx->stream;
@@ -553,6 +566,7 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
     }
     IterBufs b{};
     GCVO_TRY(iter_bufs(ctx, P, b, dlogs, sp->k_max));
+    if (sp->order == 3) GCVO_TRY(exact_bufs(ctx, P, b));
     b.fa.eps_tol = sp->eps_tol;
     b.fa.mu0 = sp->mu0;
     int *n_active = b.fa.n_active;
@@ -725,7 +739,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
                       &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g, &ctx->grp_first,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
-                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup, &ctx->pack_tmp};
+                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup, &ctx->pack_tmp, &ctx->partial2};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
         DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
@@ -908,6 +922,48 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
     }
     bool fin = std::isfinite(e.f);
     for (int k = 0; k < 6; ++k) fin = fin && std::isfinite(e.g[k]);
+    if (!fin) return GCVO_ERR_NONFINITE;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_eval_exact(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                            const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
+                            double H_E[36], double *D_out, gcvo_eval_stats *stats) {
+    if (!ctx || !target || !src_xyz || !src_feat || !T || !f || !g || !H_E) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    gcvo_problem pr{};
+    pr.target = target;
+    pr.src_xyz = src_xyz;
+    pr.src_cov = src_cov;
+    pr.src_feat = src_feat;
+    pr.n_src = n_src;
+    memcpy(pr.T0, T, 16 * sizeof(double));
+    Prepared P;
+    GCVO_TRY(prepare(ctx, 1, &pr, P));
+    IterBufs b{};
+    GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
+    GCVO_TRY(exact_bufs(ctx, P, b));
+    int one = 1;
+    GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EXACT, ctx->stream));
+    b.fa.mode = FIN_EXACT_EVAL;
+    GCVO_CUDA(launch_finalize(b.fa, ctx->stream));
+    EvalOut e{};
+    GCVO_CUDA(cudaMemcpyAsync(&e, ctx->evalout.ptr, sizeof(EvalOut), cudaMemcpyDeviceToHost, ctx->stream));
+    GCVO_TRY(check_status_word(ctx));
+    *f = e.f;
+    memcpy(g, e.g, 6 * sizeof(double));
+    memcpy(H_E, e.H, 36 * sizeof(double));
+    if (D_out) memcpy(D_out, e.M, 36 * sizeof(double));
+    if (stats) {
+        stats->n_pairs = e.n_pairs;
+        stats->n_kept = e.n_kept;
+        stats->n_candidates = e.n_cand;
+        stats->rho = std::sqrt((double)P.probs[0].rho2);
+    }
+    bool fin = std::isfinite(e.f);
+    for (int k = 0; k < 6; ++k) fin = fin && std::isfinite(e.g[k]);
+    for (int k = 0; k < 36; ++k) fin = fin && std::isfinite(e.H[k]);
     if (!fin) return GCVO_ERR_NONFINITE;
     return GCVO_OK;
 }

@@ -187,6 +187,7 @@ struct gcvo_ctx {
     gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
     gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g, grp_first;
     gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup, pack_tmp;
+    gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_retry;
     void *host_pinned = nullptr;

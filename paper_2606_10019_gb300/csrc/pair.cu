@@ -2,8 +2,9 @@
 // grouping done once per call:
 //   k_finalize -- FP64 sum of the item partials of each problem, change of
 //                 frame, connection term (Eq. 12), the 6x6 solve of Eq. (13)
-//                 and the update T <- T exp(xi); per-group anchors for the
-//                 pair kernel (tile.cu) at the new pose.
+//                 (or the G-CVO-E Newton step with the exact Hessian) and
+//                 the update T <- T exp(xi); per-group anchors for the pair
+//                 kernel (tile.cu) at the new pose.
 // Source grouping sorts each source cloud by a Morton code of its own voxels
 // and cuts it into groups of at most 32 points that never straddle a coarse
 // voxel; every group gets an FP64 anchor, every point its group index.
@@ -59,6 +60,50 @@ __device__ void exp_twist(const double xi[6], double Rout[9], double tout[3]) {
         }
         tout[r] = s;
     }
+}
+
+// Solve A x = b (6x6, row-major) by LU with partial pivoting.  Returns 0,
+// or 1 when a pivot is exactly zero.
+__device__ int solve_lu6(const double Ain[36], const double b[6], double x[6]) {
+    double A[42];
+    for (int r = 0; r < 6; ++r) {
+        for (int c = 0; c < 6; ++c) A[7 * r + c] = Ain[6 * r + c];
+        A[7 * r + 6] = b[r];
+    }
+    for (int c = 0; c < 6; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 6; ++r)
+            if (fabs(A[7 * r + c]) > fabs(A[7 * piv + c])) piv = r;
+        if (A[7 * piv + c] == 0.0) return 1;
+        if (piv != c)
+            for (int k = 0; k < 7; ++k) {
+                double tmp = A[7 * c + k];
+                A[7 * c + k] = A[7 * piv + k];
+                A[7 * piv + k] = tmp;
+            }
+        for (int r = c + 1; r < 6; ++r) {
+            double f = A[7 * r + c] / A[7 * c + c];
+            for (int k = c; k < 7; ++k) A[7 * r + k] -= f * A[7 * c + k];
+        }
+    }
+    for (int r = 5; r >= 0; --r) {
+        double sm = A[7 * r + 6];
+        for (int k = r + 1; k < 6; ++k) sm -= A[7 * r + k] * x[k];
+        x[r] = sm / A[7 * r + r];
+    }
+    return 0;
+}
+
+// Gamma of Eq. (12) as a 6x6 row-major matrix: [[-1/2 g_w^, 0], [-g_v^, 0]].
+__device__ void gamma6(const double g[6], double Gam[36]) {
+#pragma unroll
+    for (int k = 0; k < 36; ++k) Gam[k] = 0.0;
+    Gam[1] = 0.5 * g[2];   Gam[2] = -0.5 * g[1];
+    Gam[6] = -0.5 * g[2];  Gam[8] = 0.5 * g[0];
+    Gam[12] = 0.5 * g[1];  Gam[13] = -0.5 * g[0];
+    Gam[19] = g[5];  Gam[20] = -g[4];
+    Gam[24] = -g[5]; Gam[26] = g[3];
+    Gam[30] = g[4];  Gam[31] = -g[3];
 }
 
 // Solve (M - Gamma) xi = g (Eq. 13).  M is symmetric positive definite for a
@@ -149,34 +194,57 @@ __device__ int solve_gn(const double M[36], const double g[6], double xi[6]) {
             return 0;
         }
     }
-    // LU with partial pivoting of A = M - Gamma (Gamma = Gc in the first 3 columns)
-    double A[42];
-    for (int r = 0; r < 6; ++r) {
-        for (int c = 0; c < 6; ++c) A[7 * r + c] = M[6 * r + c] - (c < 3 ? Gc[3 * r + c] : 0.0);
-        A[7 * r + 6] = g[r];
-    }
-    for (int c = 0; c < 6; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 6; ++r)
-            if (fabs(A[7 * r + c]) > fabs(A[7 * piv + c])) piv = r;
-        if (A[7 * piv + c] == 0.0) return 1;
-        if (piv != c)
-            for (int k = 0; k < 7; ++k) {
-                double tmp = A[7 * c + k];
-                A[7 * c + k] = A[7 * piv + k];
-                A[7 * piv + k] = tmp;
-            }
-        for (int r = c + 1; r < 6; ++r) {
-            double f = A[7 * r + c] / A[7 * c + c];
-            for (int k = c; k < 7; ++k) A[7 * r + k] -= f * A[7 * c + k];
+    // LU with partial pivoting of M - Gamma (Gamma = Gc in the first 3 columns)
+    double A[36];
+    for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) A[6 * r + c] = M[6 * r + c] - (c < 3 ? Gc[3 * r + c] : 0.0);
+    return solve_lu6(A, g, xi);
+}
+
+// G-CVO-E: D(g) in the caller's frame from the grid-frame sums of the exact
+// pass.  Qm is B^T (Q - M)_o B, already moved by the code that moves M; the
+// rest is N_o = [[C, S_y^], [S_B, 0]] with S_y = -g_v, and
+// D = Qm - B^T N_o B for B = [[I, 0], [-o^, I]].
+__device__ void exact_derivative(const double *tot, const double Qm[36], const double o[3], double D[36]) {
+    double N[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) N[k] = 0.0;
+    const double s0 = -tot[4], s1 = -tot[5], s2 = -tot[6];   // S_y
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            N[6 * r + c] = tot[28 + 3 * r + c];
+            N[6 * (r + 3) + c] = tot[37 + 3 * r + c];
         }
-    }
-    for (int r = 5; r >= 0; --r) {
-        double sm = A[7 * r + 6];
-        for (int k = r + 1; k < 6; ++k) sm -= A[7 * r + k] * xi[k];
-        xi[r] = sm / A[7 * r + r];
-    }
-    return 0;
+    N[4] = -s2;  N[5] = s1;
+    N[9] = s2;   N[11] = -s0;
+    N[15] = -s1; N[16] = s0;
+    double O[9];
+    hat3d(o, O);
+    // X = N B: columns 0..2 get -N[:, 3:6] o^
+    double X[36];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double v = N[6 * r + c];
+            if (c < 3)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v -= N[6 * r + 3 + k] * O[3 * k + c];
+            X[6 * r + c] = v;
+        }
+    // B^T X: rows 0..2 get +o^ X[3:6, :]  (B^T = [[I, o^], [0, I]])
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double v = X[6 * r + c];
+            if (r < 3)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v += O[3 * r + k] * X[6 * (3 + k) + c];
+            D[6 * r + c] = Qm[6 * r + c] - v;
+        }
 }
 
 // Smallest positive real root of the cubic d3 t^3 + d2 t^2 + d1 t + d0
@@ -362,6 +430,15 @@ __device__ int finalize_thread0(const FinalizeArgs &a, int prob, ProbDev *P, con
     for (int k = 0; k < 6; ++k) finite = finite && isfinite(g[k]);
 #pragma unroll
     for (int k = 0; k < 36; ++k) finite = finite && isfinite(M[k]);
+    // G-CVO-E: M above holds B^T (Q - M)_o B; D(g) replaces -M
+    const bool exact = a.mode == FIN_EXACT || a.mode == FIN_EXACT_EVAL;
+    double D[36];
+    if (exact) {
+        const double o[3] = {o0, o1, o2};
+        exact_derivative(tot, M, o, D);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) finite = finite && isfinite(D[k]);
+    }
 
     if (lg) {
         lg->f = f;
@@ -379,25 +456,18 @@ __device__ int finalize_thread0(const FinalizeArgs &a, int prob, ProbDev *P, con
         lg->n_kept = ctot[1];
     }
 
-    if (a.mode == FIN_EVAL) {
-        // H_GN = -M + Gamma, Gamma = [[-1/2 g_w^, 0], [-g_v^, 0]] (Eq. 12)
+    if (a.mode == FIN_EVAL || a.mode == FIN_EXACT_EVAL) {
+        // H_GN = -M + Gamma (Eq. 12); G-CVO-E: H_E = D(g) + Gamma, M <- D(g)
         EvalOut *e = a.evalout + prob;
         e->f = f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) e->g[k] = g[k];
         double Gam[36];
-#pragma unroll
-        for (int k = 0; k < 36; ++k) Gam[k] = 0.0;
-        Gam[1] = 0.5 * g[2];   Gam[2] = -0.5 * g[1];
-        Gam[6] = -0.5 * g[2];  Gam[8] = 0.5 * g[0];
-        Gam[12] = 0.5 * g[1];  Gam[13] = -0.5 * g[0];
-        Gam[19] = g[5];  Gam[20] = -g[4];
-        Gam[24] = -g[5]; Gam[26] = g[3];
-        Gam[30] = g[4];  Gam[31] = -g[3];
+        gamma6(g, Gam);
 #pragma unroll
         for (int k = 0; k < 36; ++k) {
-            e->M[k] = M[k];
-            e->H[k] = -M[k] + Gam[k];
+            e->M[k] = exact ? D[k] : M[k];
+            e->H[k] = (exact ? D[k] : -M[k]) + Gam[k];
         }
         e->n_pairs = ctot[0];
         e->n_kept = ctot[1];
@@ -425,8 +495,21 @@ __device__ int finalize_thread0(const FinalizeArgs &a, int prob, ProbDev *P, con
         P->dir32[5] = (float)(g[0] * o1 - g[1] * o0 + g[5]);
         return 0;
     }
-    // G-CVO-2 step, Eq. (13)
     double xi[6];
+    if (exact) {
+        // G-CVO-E: Newton step xi = -H_E^-1 g, H_E = D(g) + Gamma (Eq. 12)
+        double Gam[36], nH[36];
+        gamma6(g, Gam);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) nH[k] = -(D[k] + Gam[k]);
+        if (solve_lu6(nH, g, xi) != 0) {
+            set_inactive(P, -(int)GCVO_ERR_SINGULAR, a.n_active);
+            return 0;
+        }
+        apply_step(P, xi, lg, a, it);
+        return P->status == 0;
+    }
+    // G-CVO-2 step, Eq. (13)
     if (solve_gn(M, g, xi) != 0) {
         set_inactive(P, -(int)GCVO_ERR_SINGULAR, a.n_active);
         return 0;
@@ -472,39 +555,45 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(FinalizeArgs a) {
     }
     __shared__ double red[FIN_THREADS];
     __shared__ long long cred[FIN_THREADS];
-    __shared__ double tot[32];
+    __shared__ double tot[64];
     __shared__ long long ctot[4];
     const int g0 = P->w0, g1 = P->w1;   // packed work items of this problem
     const int slot = threadIdx.x & 31, part = threadIdx.x >> 5;
-    // compensated FP32 sum of the (hi, lo) group partials, one FP64 combine
-    float H = 0.f, Lo = 0.f;
-    long long cacc = 0;
+    // the G-CVO-E pass leaves slots 32..45 in a second partial row per item
+    // (its slots 46..63 are never written, and their sums never read)
+    const int rows = (a.mode == FIN_EXACT || a.mode == FIN_EXACT_EVAL) ? 2 : 1;
+    for (int row = 0; row < rows; ++row) {
+        const float *src = row == 0 ? a.part : a.part2;
+        // compensated FP32 sum of the (hi, lo) group partials, one FP64 combine
+        float H = 0.f, Lo = 0.f;
+        long long cacc = 0;
 #pragma unroll 4
-    for (int g = g0 + part; g < g1; g += FIN_THREADS / 32) {
-        const float *p = a.part + (size_t)g * 64;
-        float h = p[slot], l = p[32 + slot];
-        float sm = H + h;
-        float bp = sm - H;
-        float err = (H - (sm - bp)) + (h - bp);
-        H = sm;
-        Lo += l + err;
-        if (slot < 3) cacc += a.counts[(size_t)g * 4 + slot];
-    }
-    red[threadIdx.x] = (double)H + (double)Lo;
-    cred[threadIdx.x] = cacc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double sm = 0.0;
-        long long cs = 0;
-#pragma unroll 8
-        for (int q = 0; q < FIN_THREADS / 32; ++q) {
-            sm += red[q * 32 + threadIdx.x];
-            cs += cred[q * 32 + threadIdx.x];
+        for (int g = g0 + part; g < g1; g += FIN_THREADS / 32) {
+            const float *p = src + (size_t)g * 64;
+            float h = p[slot], l = p[32 + slot];
+            float sm = H + h;
+            float bp = sm - H;
+            float err = (H - (sm - bp)) + (h - bp);
+            H = sm;
+            Lo += l + err;
+            if (row == 0 && slot < 3) cacc += a.counts[(size_t)g * 4 + slot];
         }
-        tot[threadIdx.x] = sm;
-        if (threadIdx.x < 4) ctot[threadIdx.x] = cs;
+        red[threadIdx.x] = (double)H + (double)Lo;
+        cred[threadIdx.x] = cacc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double sm = 0.0;
+            long long cs = 0;
+#pragma unroll 8
+            for (int q = 0; q < FIN_THREADS / 32; ++q) {
+                sm += red[q * 32 + threadIdx.x];
+                cs += cred[q * 32 + threadIdx.x];
+            }
+            tot[32 * row + threadIdx.x] = sm;
+            if (row == 0 && threadIdx.x < 4) ctot[threadIdx.x] = cs;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     __shared__ int s_upd;
     if (threadIdx.x == 0) s_upd = finalize_thread0(a, prob, P, tot, ctot);
     __syncthreads();

@@ -12,10 +12,21 @@ namespace gcvo {
 constexpr int PAIR_WARPS = 4;
 constexpr int PAIR_WCAP = 160;
 constexpr int PAIR_GRAB = 16;   // work items a warp takes per atomic
-constexpr int PAIR_SLOTS = 28;
+constexpr int PAIR_SLOTS = 28;         // f, g (6), M (21) per sub-tile
+constexpr int PAIR_SLOTS_EXACT = 46;   // f, g, Q - M (21), C (9), S_B (9): G-CVO-E
 
-enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1 };
-enum FinMode { FIN_EVAL = 0, FIN_GN = 1, FIN_GRAD = 2, FIN_LINESEARCH = 3, FIN_ANCHORS = 4 };
+enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1, PAIR_EXACT = 2 };
+// FIN_EXACT: the G-CVO-E Newton step with H_E = D(g) + Gamma;
+// FIN_EXACT_EVAL: f, g, D(g) and H_E into EvalOut (M holds D(g)).
+enum FinMode {
+    FIN_EVAL = 0,
+    FIN_GN = 1,
+    FIN_GRAD = 2,
+    FIN_LINESEARCH = 3,
+    FIN_ANCHORS = 4,
+    FIN_EXACT = 5,
+    FIN_EXACT_EVAL = 6
+};
 
 // Per-problem state kept on the device across iterations.
 struct ProbDev {
@@ -50,6 +61,7 @@ struct PairArgs {
     const ProbDev *probs;
     const GridDev *grids;
     float *part;               // n_items x 64 (hi[32], lo[32])
+    float *part2;              // PAIR_EXACT: slots 32.. in a second n_items x 64
     long long *counts;         // n_items x 4
     int *work;                 // dynamic item counter (zeroed before launch)
     unsigned *status_word;
@@ -63,6 +75,7 @@ struct FinalizeArgs {
     float4 *anchor;
     const GridDev *grids;
     const float *part;
+    const float *part2;        // FIN_EXACT*: slots 32..
     const long long *counts;
     EvalOut *evalout;
     gcvo_iter_log *logs;

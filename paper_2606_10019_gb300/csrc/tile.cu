@@ -37,6 +37,9 @@
 //     one (hi, lo) partial per sub-tile for the FP64 finalize.
 // With no cutoff (dense mode) rho and the cutoff are infinite and every
 // staged target meets every point: the same code visits all pairs.
+// The G-CVO-E pass (PAIR_EXACT) visits the same pairs and adds the sums of
+// the exact directional derivative of g (pair_exact); its 46 values per
+// sub-tile go to two partial rows.
 #include "common.cuh"
 #include "pair.cuh"
 #include "ptx.cuh"
@@ -46,6 +49,7 @@ namespace {
 
 static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
+static_assert(PAIR_SLOTS_EXACT * 33 * 4 <= PAIR_WCAP * 48, "exact epilogue transpose fits in pos, ca, cb");
 
 // Per warp: staged target points, the list of those near the sub-tile, and
 // the mbarrier the bulk copies complete on.
@@ -99,6 +103,120 @@ __device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, cons
     t[9] += wd * c22;
 }
 
+// One anisotropic pair of the G-CVO-E pass into t[25]: the sums of
+// pair_aniso (t[0..9]) and, with y = Sigma_ij^-1 r, s = Sigma'_j y,
+// u = y x s and K = Sigma_ij^-1 (Sigma'_j y^ - s^),
+//   S_yy = sum w y y^T (t[10..15], upper triangle),
+//   S_B  = sum w (y u^T + K) (t[16..24], row-major).
+// Along xi = (omega, v) the pair moves by dr = J xi, and the rotation of
+// Sigma'_j changes Sigma_ij^-1 r by K omega and r^T Sigma_ij^-1 r by
+// -2 u . omega (Sec. 3.4, the four terms of the derivative of Eq. 8).
+template <int FD>
+__device__ __forceinline__ void pair_exact(const float4 x, const float4 ca, const float4 cbv, float px, float py,
+                                           float pz, float l0, float l1, float l2, const float q[6], float rho2,
+                                           float c2, bool act, float *t, int &n_pairs, int &n_kept) {
+    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+    const bool in = act && rr <= rho2;
+    float cij = x.w * l0;
+    if (FD > 1) cij += cbv.z * l1 + cbv.w * l2;
+    const float s00 = ca.x + q[0], s01 = ca.y + q[1], s02 = ca.z + q[2];
+    const float s11 = ca.w + q[3], s12 = cbv.x + q[4], s22 = cbv.y + q[5];
+    const float c00 = s11 * s22 - s12 * s12;
+    const float c01 = s02 * s12 - s01 * s22;
+    const float c02 = s01 * s12 - s02 * s11;
+    const float c11 = s00 * s22 - s02 * s02;
+    const float c12 = s01 * s02 - s00 * s12;
+    const float c22 = s00 * s11 - s01 * s01;
+    const float det = s00 * c00 + s01 * c01 + s02 * c02;
+    const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+    const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+    const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+    const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+    const float rdet = rcp_approx(det);
+    const float d2 = qf * rdet;
+    const bool keep = in && d2 <= c2;
+    const float wk = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+    const float wd = wk * rdet;
+    n_pairs += in;
+    n_kept += keep;
+    t[0] += wk;
+    t[1] += wd * y0;
+    t[2] += wd * y1;
+    t[3] += wd * y2;
+    t[4] += wd * c00;
+    t[5] += wd * c01;
+    t[6] += wd * c02;
+    t[7] += wd * c11;
+    t[8] += wd * c12;
+    t[9] += wd * c22;
+    const float ya = y0 * rdet, yb = y1 * rdet, yc = y2 * rdet;
+    const float sa = q[0] * ya + q[1] * yb + q[2] * yc;
+    const float sb = q[1] * ya + q[3] * yb + q[4] * yc;
+    const float sc = q[2] * ya + q[4] * yb + q[5] * yc;
+    const float u[3] = {yb * sc - yc * sb, yc * sa - ya * sc, ya * sb - yb * sa};
+    const float wy[3] = {wk * ya, wk * yb, wk * yc};
+    t[10] += wy[0] * ya;
+    t[11] += wy[0] * yb;
+    t[12] += wy[0] * yc;
+    t[13] += wy[1] * yb;
+    t[14] += wy[1] * yc;
+    t[15] += wy[2] * yc;
+    // Gm = Sigma'_j y^ - s^, then K det = adj(Sigma_ij) Gm
+    const float Sp[9] = {q[0], q[1], q[2], q[1], q[3], q[4], q[2], q[4], q[5]};
+    float Gm[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        Gm[3 * r + 0] = Sp[3 * r + 1] * yc - Sp[3 * r + 2] * yb;
+        Gm[3 * r + 1] = Sp[3 * r + 2] * ya - Sp[3 * r + 0] * yc;
+        Gm[3 * r + 2] = Sp[3 * r + 0] * yb - Sp[3 * r + 1] * ya;
+    }
+    Gm[1] += sc;
+    Gm[2] -= sb;
+    Gm[3] -= sc;
+    Gm[5] += sa;
+    Gm[6] += sb;
+    Gm[7] -= sa;
+    const float adj[9] = {c00, c01, c02, c01, c11, c12, c02, c12, c22};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            t[16 + 3 * r + c] += wy[r] * u[c] +
+                                 wd * (adj[3 * r] * Gm[c] + adj[3 * r + 1] * Gm[3 + c] + adj[3 * r + 2] * Gm[6 + c]);
+}
+
+// J^T S J for J = [-p^, I] and a symmetric 3x3 S (xx, xy, xz, yy, yz, zz):
+// the 21 values of its upper triangle, row-major (Eq. 11 per point).
+__device__ __forceinline__ void jt_s_j(float A00, float A01, float A02, float A11, float A12, float A22, float px,
+                                       float py, float pz, float *v) {
+    // [[P^T S P, P S], [-S P, S]], P = p^
+    const float B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
+    const float B10 = A11 * pz - A12 * py, B11 = -A01 * pz + A12 * px, B12 = A01 * py - A11 * px;
+    const float B20 = A12 * pz - A22 * py, B21 = -A02 * pz + A22 * px, B22 = A02 * py - A12 * px;
+    v[0] = pz * B10 - py * B20;
+    v[1] = pz * B11 - py * B21;
+    v[2] = pz * B12 - py * B22;
+    v[3] = -pz * A01 + py * A02;
+    v[4] = -pz * A11 + py * A12;
+    v[5] = -pz * A12 + py * A22;
+    v[6] = -pz * B01 + px * B21;
+    v[7] = -pz * B02 + px * B22;
+    v[8] = pz * A00 - px * A02;
+    v[9] = pz * A01 - px * A12;
+    v[10] = pz * A02 - px * A22;
+    v[11] = py * B02 - px * B12;
+    v[12] = -py * A00 + px * A01;
+    v[13] = -py * A01 + px * A11;
+    v[14] = -py * A02 + px * A12;
+    v[15] = A00;
+    v[16] = A01;
+    v[17] = A02;
+    v[18] = A11;
+    v[19] = A12;
+    v[20] = A22;
+}
+
 // Line-search sums of one pair (Appendix B): with beta, gamma, delta, eps the
 // coefficients of the exponent's expansion along t xi, the kernel value
 // w e^(beta t + gamma t^2 + ...) contributes w * (1, beta, gamma + beta^2/2,
@@ -128,8 +246,8 @@ template <int MODE, bool ISO, int FD, int SUB>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
     static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
     constexpr int TQ = 32 / SUB;    // targets per warp step
-    constexpr int NT = MODE == PAIR_EVAL ? 10 : 5;
-    constexpr int NSLOT = MODE == PAIR_EVAL ? 28 : 5;
+    constexpr int NT = MODE == PAIR_EVAL ? 10 : MODE == PAIR_EXACT ? 25 : 5;
+    constexpr int NSLOT = MODE == PAIR_EVAL ? PAIR_SLOTS : MODE == PAIR_EXACT ? PAIR_SLOTS_EXACT : 5;
     __shared__ WarpStage stage[PAIR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
@@ -361,6 +479,11 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                                        n_kept);
                         continue;
                     }
+                    if constexpr (MODE == PAIR_EXACT && !ISO) {
+                        pair_exact<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                                       n_kept);
+                        continue;
+                    }
                     const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
                     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
                     const bool in = act && rr <= rho2;
@@ -375,11 +498,20 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
                         n_pairs += in;
                         n_kept += keep;
-                        if (MODE == PAIR_EVAL) {
+                        if constexpr (MODE == PAIR_EVAL || MODE == PAIR_EXACT) {
                             t[0] += wgt;
                             t[1] += wgt * r0;
                             t[2] += wgt * r1;
                             t[3] += wgt * r2;
+                            if constexpr (MODE == PAIR_EXACT) {
+                                // Sigma'_j = 0: y = r / ell^2, u = 0, K = 0
+                                t[10] += wgt * r0 * r0;
+                                t[11] += wgt * r0 * r1;
+                                t[12] += wgt * r0 * r2;
+                                t[13] += wgt * r1 * r1;
+                                t[14] += wgt * r1 * r2;
+                                t[15] += wgt * r2 * r2;
+                            }
                         } else {
                             // A = I / ell^2
                             const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
@@ -446,7 +578,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) v[k] = 0.f;
         if (qi == 0 && sval) {
-            if (MODE == PAIR_EVAL) {
+            if constexpr (MODE == PAIR_EVAL) {
                 float Sf = t[0], Su0 = t[1], Su1 = t[2], Su2 = t[3];
                 float A00 = t[4], A01 = t[5], A02 = t[6], A11 = t[7], A12 = t[8], A22 = t[9];
                 if (ISO) {
@@ -464,31 +596,54 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 v[4] = -Su0;
                 v[5] = -Su1;
                 v[6] = -Su2;
-                // M = [[P^T S_A P, P S_A], [-S_A P, S_A]], P = p^ (Eq. 11 with J = [-p^, I])
-                const float B01 = -A00 * pz + A02 * px, B02 = A00 * py - A01 * px;
-                const float B10 = A11 * pz - A12 * py, B11 = -A01 * pz + A12 * px, B12 = A01 * py - A11 * px;
-                const float B20 = A12 * pz - A22 * py, B21 = -A02 * pz + A22 * px, B22 = A02 * py - A12 * px;
-                v[7] = pz * B10 - py * B20;
-                v[8] = pz * B11 - py * B21;
-                v[9] = pz * B12 - py * B22;
-                v[10] = -pz * A01 + py * A02;
-                v[11] = -pz * A11 + py * A12;
-                v[12] = -pz * A12 + py * A22;
-                v[13] = -pz * B01 + px * B21;
-                v[14] = -pz * B02 + px * B22;
-                v[15] = pz * A00 - px * A02;
-                v[16] = pz * A01 - px * A12;
-                v[17] = pz * A02 - px * A22;
-                v[18] = py * B02 - px * B12;
-                v[19] = -py * A00 + px * A01;
-                v[20] = -py * A01 + px * A11;
-                v[21] = -py * A02 + px * A12;
-                v[22] = A00;
-                v[23] = A01;
-                v[24] = A02;
-                v[25] = A11;
-                v[26] = A12;
-                v[27] = A22;
+                // M = J^T S_A J (Eq. 11 with J = [-p^, I])
+                jt_s_j(A00, A01, A02, A11, A12, A22, px, py, pz, v + 7);
+            } else if constexpr (MODE == PAIR_EXACT) {
+                float Su0 = t[1], Su1 = t[2], Su2 = t[3];
+                float E[6], SB[9];
+                if (ISO) {
+                    Su0 *= iso_inv;
+                    Su1 *= iso_inv;
+                    Su2 *= iso_inv;
+                    const float i2 = iso_inv * iso_inv, a = t[0] * iso_inv;
+                    E[0] = t[10] * i2 - a;
+                    E[1] = t[11] * i2;
+                    E[2] = t[12] * i2;
+                    E[3] = t[13] * i2 - a;
+                    E[4] = t[14] * i2;
+                    E[5] = t[15] * i2 - a;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) SB[k] = 0.f;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) E[k] = t[10 + k] - t[4 + k];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) SB[k] = t[16 + k];
+                }
+                v[0] = t[0];
+                v[1] = -(py * Su2 - pz * Su1);
+                v[2] = -(pz * Su0 - px * Su2);
+                v[3] = -(px * Su1 - py * Su0);
+                v[4] = -Su0;
+                v[5] = -Su1;
+                v[6] = -Su2;
+                // Q - M = J^T (S_yy - S_A) J
+                jt_s_j(E[0], E[1], E[2], E[3], E[4], E[5], px, py, pz, v + 7);
+                // C = -S_y^ p^ + p^ S_B, with S_y^ p^ = p S_y^T - (S_y . p) I
+                const float pp[3] = {px, py, pz}, sy[3] = {Su0, Su1, Su2};
+                const float dp = px * Su0 + py * Su1 + pz * Su2;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    v[28 + c] = -pz * SB[3 + c] + py * SB[6 + c];
+                    v[31 + c] = pz * SB[c] - px * SB[6 + c];
+                    v[34 + c] = -py * SB[c] + px * SB[3 + c];
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[28 + 3 * r + c] += (r == c ? dp : 0.f) - pp[r] * sy[c];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[37 + k] = SB[k];
             } else {
 #pragma unroll
                 for (int k = 0; k < 5; ++k) v[k] = t[k];
@@ -502,19 +657,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
 #pragma unroll
             for (int k = 0; k < NSLOT; ++k) tr[k * (SUB + 1) + si] = v[k];
         __syncwarp();
-        float *out = a.part + (size_t)it * 64;
-        if (lane < NSLOT) {
-            float hs = 0.f, ls = 0.f;
+        // slots 0..31 to the partial row of a.part, 32.. to that of a.part2
 #pragma unroll
-            for (int i2 = 0; i2 < SUB; ++i2) {
-                const float x = tr[lane * (SUB + 1) + i2];
-                const float sm = hs + x;
-                const float bp = sm - hs;
-                ls += (hs - (sm - bp)) + (x - bp);
-                hs = sm;
+        for (int hh = 0; hh < (NSLOT + 31) / 32; ++hh) {
+            const int k = hh * 32 + lane;
+            if (k < NSLOT) {
+                float hs = 0.f, ls = 0.f;
+#pragma unroll
+                for (int i2 = 0; i2 < SUB; ++i2) {
+                    const float x = tr[k * (SUB + 1) + i2];
+                    const float sm = hs + x;
+                    const float bp = sm - hs;
+                    ls += (hs - (sm - bp)) + (x - bp);
+                    hs = sm;
+                }
+                float *out = (hh == 0 ? a.part : a.part2) + (size_t)it * 64;
+                out[lane] = hs;
+                out[32 + lane] = ls;
             }
-            out[lane] = hs;
-            out[32 + lane] = ls;
         }
         const int tp = __reduce_add_sync(FULL, n_pairs);
         const int tk = __reduce_add_sync(FULL, n_kept);
@@ -591,13 +751,14 @@ static int occupancy_t() {
     return nb;
 }
 
-// Both passes in all four schedules (the line-search pass of G-CVO-1 runs
-// over the same items as the evaluation pass).
+// All three passes in all four schedules (the line-search pass of G-CVO-1
+// and the G-CVO-E pass run over the same items as the evaluation pass).
 #define PAIR_VARIANTS_M(X, M)                                                                 \
     X(M, false, 1, 4) X(M, false, 3, 4) X(M, true, 1, 4) X(M, true, 3, 4) X(M, false, 1, 8)    \
     X(M, false, 3, 8) X(M, true, 1, 8) X(M, true, 3, 8) X(M, false, 1, 16) X(M, false, 3, 16) \
     X(M, true, 1, 16) X(M, true, 3, 16) X(M, false, 1, 32) X(M, false, 3, 32) X(M, true, 1, 32) X(M, true, 3, 32)
-#define PAIR_VARIANTS(X) PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH)
+#define PAIR_VARIANTS(X) \
+    PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH) PAIR_VARIANTS_M(X, PAIR_EXACT)
 
 int pair_sub_for(int, int sub) { return sub == 4 || sub == 16 || sub == 32 ? sub : 8; }
 

@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.gcvo_rebuild_grid.argtypes = [P, P, P, P, P, I64, P]
         L.gcvo_grid_info.argtypes = [P, P, P, P]
         L.gcvo_eval.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
+        L.gcvo_eval_exact.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
         L.gcvo_register.argtypes = [P, P, P, P, P, I64, P, P, P, P, P]
         L.gcvo_register_batched.argtypes = [P, I, P, P, P, P, P, P]
         L.gcvo_estimate_covariances_batched.argtypes = [P, I, P, P, P, P]
@@ -310,6 +311,32 @@ def gcvo_eval(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T) -> EvalRe
                            T.ctypes.data, ctypes.byref(f), g.ctypes.data, H.ctypes.data, M.ctypes.data,
                            ctypes.byref(st)), "gcvo_eval")
     return EvalResult(f.value, g, H.reshape(6, 6), M.reshape(6, 6), st.n_pairs, st.n_kept, st.n_candidates, st.rho)
+
+
+@dataclass
+class ExactEvalResult:
+    f: float
+    g: np.ndarray
+    H: np.ndarray       # H_E = D(g) + Gamma
+    D: np.ndarray       # D(g), the exact derivative of the gradient field
+    n_pairs: int
+    n_kept: int
+    n_candidates: int
+    rho: float
+
+
+def gcvo_eval_exact(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T) -> ExactEvalResult:
+    T = _pose(T)
+    f = ctypes.c_double()
+    g = np.zeros(6)
+    H = np.zeros(36)
+    D = np.zeros(36)
+    st = gcvo_eval_stats()
+    _check(lib().gcvo_eval_exact(ctx.handle, grid.handle, _ptr(src_xyz), _ptr(src_cov), _ptr(src_feat),
+                                 _n(src_xyz), T.ctypes.data, ctypes.byref(f), g.ctypes.data, H.ctypes.data,
+                                 D.ctypes.data, ctypes.byref(st)), "gcvo_eval_exact")
+    return ExactEvalResult(f.value, g, H.reshape(6, 6), D.reshape(6, 6), st.n_pairs, st.n_kept, st.n_candidates,
+                           st.rho)
 
 
 def _logs_to_list(logs, n):

@@ -54,6 +54,8 @@ def test_invalid_arguments_are_rejected_before_any_device_work(libpath):
     assert L.gcvo_destroy(None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_grid_destroy(None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_eval(None, None, None, None, None, 0, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_eval_exact(None, None, None, None, None, 0, None, None, None, None, None,
+                             None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_register(None, None, None, None, None, 0, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_register_batched(None, 0, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_estimate_covariances_batched(None, 1, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
