@@ -37,8 +37,8 @@ FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
 # DRAM bytes per pair-eval of the pair kernel, from one ncu capture of the
 # kernel whose source hashes to PAIR_KERNEL_SHA (profiles/k_tile_lidar20.md);
 # the traffic is reported only while the kernel source still matches
-PAIR_DRAM_BYTES_PER_PAIR = 5.36
-PAIR_KERNEL_SHA = "7a21a4e49e4dd278"
+PAIR_DRAM_BYTES_PER_PAIR = 5.37
+PAIR_KERNEL_SHA = "7342bd38eaa7b5d7"
 EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
 KNN = 10
 
@@ -297,7 +297,7 @@ def run_gcvo(args, rank, world):
     peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_basis": "DRAM bytes per pair-eval from an ncu capture of k_tile on 20 "
-                "frames (5.36 B) x mean pair-evals per launch; null if the kernel changed since",
+                "frames (5.37 B) x mean pair-evals per launch; null if the kernel changed since",
                 "kernel": "k_tile (evaluation pass)", "launches": prof["n_pair_launches"],
                 "points_per_subtile": schedule,
                 "avg_launch_ms": prof["pair_kernel_ms"] / n_launch,
