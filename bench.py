@@ -282,7 +282,7 @@ def run_gcvo(args, rank, world):
         fo = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(min(8, F - 1))]
         first = first_order_block(G, ctx, dev, fo, T_true[:len(fo)])
         batched = batched_block(G, ctx, dev, frames, T_true)
-        exact = exact_hessian_block(G, ctx, dev, probs, Tb)
+        exact = exact_hessian_block(G, ctx, dev, probs, T_true)
 
     # ---- roofline of the pair kernel
     n_launch = max(1, prof["n_pair_launches"])
@@ -385,16 +385,29 @@ def first_order_block(G, ctx, dev, probs, T_true, k_max=20000):
     return out
 
 
-def exact_hessian_block(G, ctx, dev, probs, T_gn, iters=8):
-    """Cost of an iteration of G-CVO-E (Newton with the exact Hessian
-    H_E = D(g) + Gamma) against one of G-CVO-2 on the same batched frame
-    pairs, both started at the batched G-CVO-2 solutions and run for a fixed
-    number of iterations (eps_tol 0), where the exact Hessian is negative
-    definite and Newton stays put."""
+def _pose_diff(Ta, Tb):
+    """Rotation (deg) and translation (m) between two poses."""
+    from scipy.spatial.transform import Rotation
+    Dm = np.linalg.inv(Ta) @ Tb
+    return math.degrees(np.linalg.norm(Rotation.from_matrix(Dm[:3, :3]).as_rotvec())), float(np.linalg.norm(Dm[:3, 3]))
+
+
+def exact_hessian_block(G, ctx, dev, probs, T_true, iters=8):
+    """G-CVO-E (Newton with the exact Hessian H_E = D(g) + Gamma) against
+    G-CVO-2 on the same batched LiDAR frame pairs, as in the paper's
+    ablation (Sec. 5.4: the exact Hessian gains little in convergence speed
+    and costs more per iteration).
+      per_iteration: both started at the G-CVO-2 solutions and run a fixed
+        number of iterations (eps_tol 0): the cost of one iteration, and how
+        far the undamped Newton step moves away from the G-CVO-2 solution.
+      from_identity: both from the identity to ||xi||_1 < 1e-6 (k_max 200):
+        iterations, time and success (rotation < 2 deg, translation < 5 cm)."""
     import torch
-    out = {}
-    poses = {}
+    sp2 = G.solver_params(order=2, k_max=200, eps_tol=1e-6)
+    T_gn, _, _, st_gn = G.gcvo_register_batched(ctx, probs, sp2)
     starts = [p[:4] + (T,) for p, T in zip(probs, T_gn)]
+    per_it = {}
+    poses = {}
     for name, order in (("second_order", 2), ("exact", 3)):
         sp = G.solver_params(order=order, k_max=iters, eps_tol=0.0)
         G.gcvo_register_batched(ctx, starts, sp)           # warm-up
@@ -405,15 +418,34 @@ def exact_hessian_block(G, ctx, dev, probs, T_gn, iters=8):
         t = time.perf_counter() - t0
         poses[name] = T
         n_pairs = sum(sum(r["n_pairs"] for r in lg) for lg in logs)
-        out[name] = {"ms_per_iteration": t * 1e3 / iters, "pair_evals_per_s": n_pairs / t,
-                     "iterations": int(np.max(n_iter)),
-                     "failed": int(np.sum((status != G.GCVO_OK) & (status != G.GCVO_ERR_NOT_CONVERGED)))}
-    d = [float(np.abs(a - b).max()) for a, b in zip(poses["exact"], T_gn)]
-    out.update({"workload": f"{len(probs)} LiDAR frame pairs at their G-CVO-2 solutions, {iters} iterations, batched",
-                "exact_over_second_order_time": out["exact"]["ms_per_iteration"] /
-                out["second_order"]["ms_per_iteration"],
-                "exact_pose_drift_max": max(d)})
-    return out
+        per_it[name] = {"ms_per_iteration": t * 1e3 / iters, "pair_evals_per_s": n_pairs / t,
+                        "stopped_by_error": int(np.sum((status != G.GCVO_OK) & (status != G.GCVO_ERR_NOT_CONVERGED)))}
+    drift = np.array([_pose_diff(a, b) for a, b in zip(T_gn, poses["exact"])])
+    gn_conv = st_gn == G.GCVO_OK
+    per_it.update({
+        "workload": f"{len(probs)} LiDAR frame pairs at their G-CVO-2 solutions, {iters} iterations, batched",
+        "exact_over_second_order_time": per_it["exact"]["ms_per_iteration"] / per_it["second_order"]["ms_per_iteration"],
+        "exact_drift_from_gn_solution": {
+            "rot_deg_median": float(np.median(drift[:, 0])), "trans_m_median": float(np.median(drift[:, 1])),
+            "trans_m_max": float(drift[:, 1].max()),
+            "pairs_moved_over_1cm": int(np.sum(drift[:, 1] > 0.01)),
+            "of_those_gn_converged": int(np.sum((drift[:, 1] > 0.01) & gn_conv)),
+            "gn_converged": int(np.sum(gn_conv))}})
+    ident = {}
+    for name, order in (("second_order", 2), ("exact", 3)):
+        sp = G.solver_params(order=order, k_max=200, eps_tol=1e-6)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        T, _, n_iter, status = G.gcvo_register_batched(ctx, probs, sp)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        err = np.array([_pose_diff(Tt, Te) for Te, Tt in zip(T, T_true)])
+        ok = (err[:, 0] < 2.0) & (err[:, 1] < 0.05)
+        ident[name] = {"seconds": t, "iterations_mean": float(np.mean(n_iter)),
+                       "converged": int(np.sum(status == G.GCVO_OK)), "success": float(ok.mean())}
+    ident["workload"] = f"{len(probs)} LiDAR frame pairs from the identity, batched, eps_tol 1e-6, k_max 200"
+    return {"per_iteration": per_it, "from_identity": ident,
+            "paper": "exact Hessian: marginal gains in convergence speed, higher per-iteration cost (Sec. 5.4)"}
 
 
 # ---------------------------------------------------------------------------
