@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 METRIC = "G-CVO kernel pair-evals/s & registrations/s at equal pose error vs plain"
 UNIT = "pair-evals/s"
 FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
+FLOP_PER_PAIR_EXACT = 232   # the G-CVO-E pass: the 76 above plus y, Sigma'y, u, K and the S_yy, S_B sums
 # DRAM bytes per pair-eval of the pair kernel, from one ncu capture of the
 # kernel whose source hashes to PAIR_KERNEL_SHA (profiles/k_tile_lidar20.md);
 # the traffic is reported only while the kernel source still matches
@@ -282,7 +283,9 @@ def run_gcvo(args, rank, world):
         fo = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(min(8, F - 1))]
         first = first_order_block(G, ctx, dev, fo, T_true[:len(fo)])
         batched = batched_block(G, ctx, dev, frames, T_true)
-        exact = exact_hessian_block(G, ctx, dev, probs, T_true)
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        exact = exact_hessian_block(G, ctx, dev, probs, T_true,
+                                    sm_count * 128 * 2 * (clk or {}).get("sm_max_mhz", 2070.0) / 1e6)
 
     # ---- roofline of the pair kernel
     n_launch = max(1, prof["n_pair_launches"])
@@ -392,13 +395,14 @@ def _pose_diff(Ta, Tb):
     return math.degrees(np.linalg.norm(Rotation.from_matrix(Dm[:3, :3]).as_rotvec())), float(np.linalg.norm(Dm[:3, 3]))
 
 
-def exact_hessian_block(G, ctx, dev, probs, T_true, iters=8):
+def exact_hessian_block(G, ctx, dev, probs, T_true, peak_tflops, iters=8):
     """G-CVO-E (Newton with the exact Hessian H_E = D(g) + Gamma) against
     G-CVO-2 on the same batched LiDAR frame pairs, as in the paper's
     ablation (Sec. 5.4: the exact Hessian gains little in convergence speed
     and costs more per iteration).
       per_iteration: both started at the G-CVO-2 solutions and run a fixed
-        number of iterations (eps_tol 0): the cost of one iteration, and how
+        number of iterations (eps_tol 0): the cost of one iteration, the pair
+        kernel's CUDA-event time and FP32 roofline fraction in each, and how
         far the undamped Newton step moves away from the G-CVO-2 solution.
       from_identity: both from the identity to ||xi||_1 < 1e-6 (k_max 200):
         iterations, time and success (rotation < 2 deg, translation < 5 cm)."""
@@ -411,14 +415,23 @@ def exact_hessian_block(G, ctx, dev, probs, T_true, iters=8):
     for name, order in (("second_order", 2), ("exact", 3)):
         sp = G.solver_params(order=order, k_max=iters, eps_tol=0.0)
         G.gcvo_register_batched(ctx, starts, sp)           # warm-up
+        G.gcvo_profile_enable(ctx, True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         T, logs, n_iter, status = G.gcvo_register_batched(ctx, starts, sp, want_log=True)
         torch.cuda.synchronize(dev)
         t = time.perf_counter() - t0
+        prof = G.gcvo_profile_read(ctx)
+        G.gcvo_profile_enable(ctx, False)
         poses[name] = T
         n_pairs = sum(sum(r["n_pairs"] for r in lg) for lg in logs)
+        t_k = prof["pair_kernel_ms"] / 1e3
+        flop = FLOP_PER_PAIR_EXACT if order == 3 else FLOP_PER_PAIR
+        achieved = n_pairs * flop / t_k / 1e12 if t_k > 0 else 0.0
         per_it[name] = {"ms_per_iteration": t * 1e3 / iters, "pair_evals_per_s": n_pairs / t,
+                        "pair_kernel_ms_per_launch": prof["pair_kernel_ms"] / max(1, prof["n_pair_launches"]),
+                        "pair_kernel_tflops": achieved, "pair_kernel_frac_of_fp32_peak": achieved / peak_tflops,
+                        "flop_per_pair_eval": flop,
                         "stopped_by_error": int(np.sum((status != G.GCVO_OK) & (status != G.GCVO_ERR_NOT_CONVERGED)))}
     drift = np.array([_pose_diff(a, b) for a, b in zip(T_gn, poses["exact"])])
     gn_conv = st_gn == G.GCVO_OK

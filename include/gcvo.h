@@ -332,7 +332,8 @@ gcvo_status gcvo_proposal_train_step(gcvo_ctx *ctx, gcvo_proposal *prop, int n_p
 typedef struct {
     int64_t n_launches;      /* kernels launched by the library in this process
                                 since gcvo_profile_enable */
-    int64_t n_pair_launches; /* pair-kernel launches (evaluation passes) timed */
+    int64_t n_pair_launches; /* pair-kernel launches timed: evaluation passes
+                                and G-CVO-E passes (not G-CVO-1 line searches) */
     double pair_kernel_ms;   /* their summed device time, from CUDA events
                                 recorded on the context's stream around each launch */
 } gcvo_profile;

@@ -442,14 +442,15 @@ gcvo_status check_status_word(gcvo_ctx *ctx) {
 }
 
 // One pair pass on stream s (the work counter is reset first).  With
-// profiling on, the launch is bracketed by two events from the pool; inside
-// a stream capture they become event-record nodes of the graph.
+// profiling on, an evaluation or G-CVO-E launch is bracketed by two events
+// from the pool; inside a stream capture they become event-record nodes of
+// the graph.
 gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode, cudaStream_t s,
                              bool capturing = false) {
     GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (ctx->profiling && mode == PAIR_EVAL) {
+    if (ctx->profiling && (mode == PAIR_EVAL || mode == PAIR_EXACT)) {
         while (ctx->ev_pool.size() < ctx->ev_used + 2) {
             cudaEvent_t e;
             GCVO_CUDA(cudaEventCreate(&e));
@@ -951,6 +952,7 @@ gcvo_status gcvo_eval_exact(gcvo_ctx *ctx, const gcvo_grid *target, const float 
     EvalOut e{};
     GCVO_CUDA(cudaMemcpyAsync(&e, ctx->evalout.ptr, sizeof(EvalOut), cudaMemcpyDeviceToHost, ctx->stream));
     GCVO_TRY(check_status_word(ctx));
+    GCVO_TRY(collect_profile(ctx));
     *f = e.f;
     memcpy(g, e.g, 6 * sizeof(double));
     memcpy(H_E, e.H, 36 * sizeof(double));
