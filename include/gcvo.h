@@ -49,7 +49,8 @@ typedef enum {
     GCVO_ERR_INVALID_ARG = 1,   /* null pointer, bad size or parameter */
     GCVO_ERR_CUDA = 2,          /* a CUDA runtime call failed */
     GCVO_ERR_WORKSPACE = 3,     /* device memory could not be allocated */
-    GCVO_ERR_SINGULAR = 4,      /* M - Gamma of Eq. (13) could not be factorised */
+    GCVO_ERR_SINGULAR = 4,      /* the 6x6 system of a step (M - Gamma of Eq. 13, or
+                                   H_E of G-CVO-E) could not be factorised */
     GCVO_ERR_NO_OVERLAP = 5,    /* no pair passed the kernel cutoff (f = 0) */
     GCVO_ERR_NOT_CONVERGED = 6, /* k_max iterations ran without ||xi||_1 < eps_tol */
     GCVO_ERR_NONFINITE = 7,     /* an input or a reduced value is NaN or Inf */
@@ -86,7 +87,9 @@ typedef struct {
     int order;          /* 2: G-CVO-2, Gauss-Newton step of Eq. (13);
                            1: G-CVO-1, gradient step with the line search of Eq. (9);
                            3: G-CVO-E, Newton step xi = -H_E^{-1} g with the exact
-                              Riemannian Hessian H_E = D(g) + Gamma (Sec. 3.4, Eq. 12) */
+                              Riemannian Hessian H_E = D(g) + Gamma (Sec. 3.4, Eq. 12);
+                              the step is not damped, so it heads for a maximum only
+                              where H_E is negative definite (near one) */
     int k_max;          /* iteration limit, 1..GCVO_MAX_KMAX */
     double eps_tol;     /* stop when ||xi^(k)||_1 < eps_tol */
     double mu0;         /* G-CVO-1 minimum step of Eq. (9) */
@@ -159,11 +162,14 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx);
 gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n,
                                       const gcvo_kernel_params *params, float *cov_out);
 
-/* Build the voxel hash of a target cloud X (Eq. 5's x_i with Sigma(x_i; X)
+/* Build the voxel grid of a target cloud X (Eq. 5's x_i with Sigma(x_i; X)
  * and features l_i^X): points are keyed by voxel, sorted, copied into a
- * grid-owned packed layout and indexed by an open-addressing hash of the
- * occupied voxels.  cov may be NULL in kernel_mode 1.  The grid keeps the
- * kernel parameters it was built with.  Synchronises the stream. */
+ * grid-owned packed layout relative to the box centre, and indexed by a
+ * dense per-voxel prefix table over the box (the pair kernel's index;
+ * voxels are coarsened while the box holds more than 2^26 of them) and an
+ * open-addressing hash of the occupied voxels.  cov may be NULL in
+ * kernel_mode 1.  The grid keeps the kernel parameters it was built with.
+ * Synchronises the stream. */
 gcvo_status gcvo_build_grid(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat,
                             int64_t n, const gcvo_kernel_params *params, gcvo_grid **grid_out);
 
@@ -220,8 +226,8 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
  * (the last alone is the -M of Gauss-Newton) -- and Gamma is the
  * connection term of Eq. (12).  D_out (host 6x6, may be NULL) receives
  * D(g), which is not symmetric away from a critical point; stats may be
- * NULL.  One pair pass (a third more partial storage and about twice the
- * arithmetic per pair of gcvo_eval).  Synchronises the stream. */
+ * NULL.  One pair pass, with twice the partial storage and about three
+ * times the arithmetic per pair of gcvo_eval.  Synchronises the stream. */
 gcvo_status gcvo_eval_exact(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
                             const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
                             double H_E[36], double *D_out, gcvo_eval_stats *stats);
