@@ -566,3 +566,25 @@ def test_gcvo_e_reaches_the_gcvo2_solution(oracle_mod):
     # compare the matrices: an arccos angle cannot resolve below ~1e-8 rad
     assert np.abs(e.T - ref.T).max() < 1e-9, (np.abs(e.T - ref.T).max(), len(e.log))
     assert len(e.log) < 15
+
+
+def test_exact_hessian_isotropic_is_self_adjoint(oracle_mod):
+    """Sec. 2 / Eq. (12): the Riemannian Hessian of the Levi-Civita
+    connection is self-adjoint, so in the orthonormal left-invariant
+    coordinates D(g) + Gamma is symmetric at every pose, not only at a
+    critical point.  With the isotropic kernel Lemma 1's g is the true
+    gradient of f, and the identity holds to rounding; with Gamma's sign
+    flipped, or Gamma left out, it fails.  (With the anisotropic kernel g
+    freezes Sigma_ij (Remark 2), is not a gradient field, and the identity
+    does not apply.)"""
+    O = oracle_mod
+    prob, pair, rng = _e_problem(O, 6, iso=True)
+    kp = O.KernelParams(cutoff=0.0, kernel_mode=1, iso_ell=0.15)
+    for T in (np.eye(4), pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.2)):
+        Dg = O.grad_derivative(prob, T, kp)
+        G = O.evaluate(prob, T, kp).Gamma
+        H = Dg + G
+        n = np.abs(H).max()
+        assert np.abs(H - H.T).max() <= 1e-12 * n
+        for wrong in (Dg - G, Dg):
+            assert np.abs(wrong - wrong.T).max() > 1e-3 * n
