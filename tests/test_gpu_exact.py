@@ -183,10 +183,14 @@ def test_exact_isotropic_lidar_frame_pair_is_self_adjoint(env):
     """Full size (one voxelised LiDAR frame pair of the bench's trajectory,
     about 14k points each) with the isotropic kernel, where Lemma 1's g is
     the true gradient: the GPU's H_E = D(g) + Gamma is symmetric at any pose
-    (the self-adjointness pinned in the oracle tests) to 1e-4 of its largest
-    entry, about 100x the FP32 rounding of the pass, while D(g) alone is
-    not (at the identity; near the optimum g and so D's skew part are
-    small).  The oracle's all-pair D(g) is out of reach at this size."""
+    (the self-adjointness pinned in the oracle tests), while D(g) alone is
+    not (checked at the identity; near the optimum g, and with it D's skew
+    part, is small).  The skew parts of D(g) and of Gamma are built from the
+    same FP32 per-point sums and cancel in the FP64 finalize (measured
+    1.4e-11 of the largest entry), so the 1e-8 bound checks the slot layout
+    of the exact pass, the change of frame of its N term and Gamma's sign
+    rather than the FP32 pair arithmetic.  The oracle's all-pair D(g) is out
+    of reach at this size."""
     O, G, ctx, dev = env
     pair = D.LidarSequence(n_frames=2).pair(0)
     case = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.3, cutoff=3.0), iso=True)
@@ -195,6 +199,6 @@ def test_exact_isotropic_lidar_frame_pair_is_self_adjoint(env):
         r = G.gcvo_eval_exact(ctx, case.grid, *case.src, T)
         n = np.abs(r.H).max()
         asym = np.abs(r.H - r.H.T).max() / n
-        assert asym <= 1e-4, asym
+        assert asym <= 1e-8, asym
         if T is not pair.T_true:
             assert np.abs(r.D - r.D.T).max() > 1e-3 * n
