@@ -886,10 +886,12 @@ gcvo_status gcvo_grid_info(const gcvo_grid *grid, int64_t *n_points, int64_t *n_
     return GCVO_OK;
 }
 
-gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
-                      const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
-                      double H[36], double *M_out, gcvo_eval_stats *stats) {
-    if (!ctx || !target || !src_xyz || !src_feat || !T || !f || !g || !H) return GCVO_ERR_INVALID_ARG;
+// One evaluation of a single problem at pose T: the pair pass `mode`
+// (PAIR_EVAL or PAIR_EXACT) and the finalize `fin` fill one EvalOut, which
+// is copied to the host outputs (H and M_out as the finalize wrote them).
+static gcvo_status eval_once(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                             const float *src_feat, int64_t n_src, const double T[16], int mode, int fin,
+                             double *f, double g[6], double H[36], double *M_out, gcvo_eval_stats *stats) {
     GCVO_CUDA(cudaSetDevice(ctx->device));
     gcvo_problem pr{};
     pr.target = target;
@@ -902,10 +904,11 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
     GCVO_TRY(prepare(ctx, 1, &pr, P));
     IterBufs b{};
     GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
+    if (mode == PAIR_EXACT) GCVO_TRY(exact_bufs(ctx, P, b));
     int one = 1;
     GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, ctx->stream));
-    b.fa.mode = FIN_EVAL;
+    GCVO_TRY(launch_pair_pass(ctx, P, b, mode, ctx->stream));
+    b.fa.mode = fin;
     GCVO_CUDA(launch_finalize(b.fa, ctx->stream));
     EvalOut e{};
     GCVO_CUDA(cudaMemcpyAsync(&e, ctx->evalout.ptr, sizeof(EvalOut), cudaMemcpyDeviceToHost, ctx->stream));
@@ -921,53 +924,27 @@ gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_x
         stats->n_candidates = e.n_cand;
         stats->rho = std::sqrt((double)P.probs[0].rho2);
     }
-    bool fin = std::isfinite(e.f);
-    for (int k = 0; k < 6; ++k) fin = fin && std::isfinite(e.g[k]);
-    if (!fin) return GCVO_ERR_NONFINITE;
-    return GCVO_OK;
+    bool finite = std::isfinite(e.f);
+    for (int k = 0; k < 6; ++k) finite = finite && std::isfinite(e.g[k]);
+    if (mode == PAIR_EXACT)
+        for (int k = 0; k < 36; ++k) finite = finite && std::isfinite(e.H[k]);
+    return finite ? GCVO_OK : GCVO_ERR_NONFINITE;
+}
+
+gcvo_status gcvo_eval(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
+                      const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
+                      double H[36], double *M_out, gcvo_eval_stats *stats) {
+    if (!ctx || !target || !src_xyz || !src_feat || !T || !f || !g || !H) return GCVO_ERR_INVALID_ARG;
+    return eval_once(ctx, target, src_xyz, src_cov, src_feat, n_src, T, PAIR_EVAL, FIN_EVAL, f, g, H, M_out,
+                     stats);
 }
 
 gcvo_status gcvo_eval_exact(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
                             const float *src_feat, int64_t n_src, const double T[16], double *f, double g[6],
                             double H_E[36], double *D_out, gcvo_eval_stats *stats) {
     if (!ctx || !target || !src_xyz || !src_feat || !T || !f || !g || !H_E) return GCVO_ERR_INVALID_ARG;
-    GCVO_CUDA(cudaSetDevice(ctx->device));
-    gcvo_problem pr{};
-    pr.target = target;
-    pr.src_xyz = src_xyz;
-    pr.src_cov = src_cov;
-    pr.src_feat = src_feat;
-    pr.n_src = n_src;
-    memcpy(pr.T0, T, 16 * sizeof(double));
-    Prepared P;
-    GCVO_TRY(prepare(ctx, 1, &pr, P));
-    IterBufs b{};
-    GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
-    GCVO_TRY(exact_bufs(ctx, P, b));
-    int one = 1;
-    GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EXACT, ctx->stream));
-    b.fa.mode = FIN_EXACT_EVAL;
-    GCVO_CUDA(launch_finalize(b.fa, ctx->stream));
-    EvalOut e{};
-    GCVO_CUDA(cudaMemcpyAsync(&e, ctx->evalout.ptr, sizeof(EvalOut), cudaMemcpyDeviceToHost, ctx->stream));
-    GCVO_TRY(check_status_word(ctx));
-    GCVO_TRY(collect_profile(ctx));
-    *f = e.f;
-    memcpy(g, e.g, 6 * sizeof(double));
-    memcpy(H_E, e.H, 36 * sizeof(double));
-    if (D_out) memcpy(D_out, e.M, 36 * sizeof(double));
-    if (stats) {
-        stats->n_pairs = e.n_pairs;
-        stats->n_kept = e.n_kept;
-        stats->n_candidates = e.n_cand;
-        stats->rho = std::sqrt((double)P.probs[0].rho2);
-    }
-    bool fin = std::isfinite(e.f);
-    for (int k = 0; k < 6; ++k) fin = fin && std::isfinite(e.g[k]);
-    for (int k = 0; k < 36; ++k) fin = fin && std::isfinite(e.H[k]);
-    if (!fin) return GCVO_ERR_NONFINITE;
-    return GCVO_OK;
+    return eval_once(ctx, target, src_xyz, src_cov, src_feat, n_src, T, PAIR_EXACT, FIN_EXACT_EVAL, f, g, H_E,
+                     D_out, stats);
 }
 
 gcvo_status gcvo_register(gcvo_ctx *ctx, const gcvo_grid *target, const float *src_xyz, const float *src_cov,
