@@ -451,6 +451,130 @@ int orc_linesearch_coeffs(const double *tgt, const double *tgt_cov, const double
     return 0;
 }
 
+/* ---------------------------------------------------------------------- */
+/* G-CVO-E (Sec. 3.4): the directional derivative D(g)[xi] of Lemma 1's    */
+/* gradient under the right perturbation T exp(xi^), all four terms of the  */
+/* product rule kept.  For xi = e_k (k = 0..5, omega first) and each pair:  */
+/*   dp = -(omega x p + v),  dr = -dp,                                      */
+/*   dSigma' = Sigma' omega^ - omega^ Sigma',  dA = -A dSigma' A,           */
+/*   dw = -w (y . dr + r . dA r / 2),  y = A r,  A = Sigma_ij^-1,           */
+/*   column k of D -= dw J^T y + w (dp x y, 0) + w J^T dA r + w J^T A dr,   */
+/* with J^T a = (p x a, a).  The last term alone is -M.  Pairs beyond the   */
+/* cutoff contribute nothing.  D_out: 6x6 row-major, D_out[6 r + k] is      */
+/* component r of D(g)[e_k].  Same inputs as orc_eval.                      */
+/* ---------------------------------------------------------------------- */
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void mat3_mul(const double A[9], const double B[9], double C[9]) {
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int b = 0; b < 3; ++b) s += A[3 * a + b] * B[3 * b + c];
+            C[3 * a + c] = s;
+        }
+}
+
+static void mat3_vec(const double A[9], const double x[3], double y[3]) {
+    for (int a = 0; a < 3; ++a) y[a] = A[3 * a] * x[0] + A[3 * a + 1] * x[1] + A[3 * a + 2] * x[2];
+}
+
+int orc_grad_derivative(const double *tgt, const double *tgt_cov, const double *tgt_feat, int64_t n_tgt,
+                        const double *src, const double *src_cov, const double *src_feat, int64_t n_src,
+                        const double *T, const orc_params *P, double *D_out) {
+    double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+    double t[3] = {T[3], T[7], T[11]};
+    double *part = (double *)calloc((size_t)(n_src > 0 ? n_src : 1) * 36, sizeof(double));
+    if (!part) return -2;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t j = 0; j < n_src; ++j) {
+        const double *z = src + 3 * j;
+        double dz[3] = {z[0] - t[0], z[1] - t[1], z[2] - t[2]};
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = R[0 + a] * dz[0] + R[3 + a] * dz[1] + R[6 + a] * dz[2];
+        /* Sigma'_j = R^T Sigma(z_j; Z) R (zero for the isotropic kernel) */
+        double Szr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (P->kernel_mode == 0) {
+            double Sz[9], SR[9], Rt[9];
+            sym6_to_mat(src_cov + 6 * j, Sz);
+            mat3_mul(Sz, R, SR);
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) Rt[3 * a + c] = R[3 * c + a];
+            mat3_mul(Rt, SR, Szr);
+        }
+        double *Dj = part + 36 * j;
+        const double *lz = src_feat + (int64_t)P->feat_dim * j;
+        for (int64_t i = 0; i < n_tgt; ++i) {
+            const double *x = tgt + 3 * i;
+            double r[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+            double Sig[9];
+            if (P->kernel_mode == 1) {
+                for (int q = 0; q < 9; ++q) Sig[q] = 0;
+                Sig[0] = Sig[4] = Sig[8] = P->iso_ell * P->iso_ell;
+            } else {
+                double Sx[9];
+                sym6_to_mat(tgt_cov + 6 * i, Sx);
+                for (int q = 0; q < 9; ++q) Sig[q] = Sx[q] + Szr[q];
+            }
+            double A[9];
+            if (inv3_lu(Sig, A) != 0) continue;
+            double y[3];
+            mat3_vec(A, r, y);
+            double d2 = r[0] * y[0] + r[1] * y[1] + r[2] * y[2];
+            if (P->cutoff > 0 && d2 > P->cutoff * P->cutoff) continue;
+            double cij = 0;
+            const double *lx = tgt_feat + (int64_t)P->feat_dim * i;
+            for (int q = 0; q < P->feat_dim; ++q) cij += lx[q] * lz[q];
+            double w = cij * P->sigma2 * exp(-0.5 * d2);
+            double pxy[3];
+            cross3(p, y, pxy);
+            for (int k = 0; k < 6; ++k) {
+                double om[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+                if (k < 3) om[k] = 1.0; else v[k - 3] = 1.0;
+                double oxp[3], dp[3], dr[3];
+                cross3(om, p, oxp);
+                for (int a = 0; a < 3; ++a) {
+                    dp[a] = -(oxp[a] + v[a]);
+                    dr[a] = -dp[a];
+                }
+                /* dSigma' = Sigma' W - W Sigma', W = omega^ */
+                double W[9] = {0, -om[2], om[1], om[2], 0, -om[0], -om[1], om[0], 0};
+                double SW[9], WS[9], dS[9], AdS[9], dA[9];
+                mat3_mul(Szr, W, SW);
+                mat3_mul(W, Szr, WS);
+                for (int q = 0; q < 9; ++q) dS[q] = SW[q] - WS[q];
+                mat3_mul(A, dS, AdS);
+                mat3_mul(AdS, A, dA);
+                for (int q = 0; q < 9; ++q) dA[q] = -dA[q];
+                double dAr[3], Adr[3];
+                mat3_vec(dA, r, dAr);
+                mat3_vec(A, dr, Adr);
+                double ydr = y[0] * dr[0] + y[1] * dr[1] + y[2] * dr[2];
+                double rdAr = r[0] * dAr[0] + r[1] * dAr[1] + r[2] * dAr[2];
+                double dw = -w * (ydr + 0.5 * rdAr);
+                double dpxy[3], pxdAr[3], pxAdr[3];
+                cross3(dp, y, dpxy);
+                cross3(p, dAr, pxdAr);
+                cross3(p, Adr, pxAdr);
+                for (int a = 0; a < 3; ++a) {
+                    /* rotation rows: (p x .) parts; translation rows: the vectors */
+                    Dj[6 * a + k] -= dw * pxy[a] + w * dpxy[a] + w * pxdAr[a] + w * pxAdr[a];
+                    Dj[6 * (3 + a) + k] -= dw * y[a] + w * dAr[a] + w * Adr[a];
+                }
+            }
+        }
+    }
+    for (int q = 0; q < 36; ++q) D_out[q] = 0;
+    for (int64_t j = 0; j < n_src; ++j)
+        for (int q = 0; q < 36; ++q) D_out[q] += part[36 * j + q];
+    free(part);
+    return 0;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

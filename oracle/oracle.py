@@ -19,6 +19,11 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   exp_se3             : scipy.linalg.expm of the 4x4 twist matrix.
   register            : exact recovery in the isotropic and sphere cases.
   linesearch          : polynomial vs direct evaluation of G(t) to O(t^5).
+  grad_derivative     : central finite differences of g; its fourth term is
+                        -M; isotropic D(g) + Gamma is self-adjoint; Newton on
+                        it reaches the G-CVO-2 stationary point.
+  grad_derivative_c   : the same D(g) as C loops, equal to grad_derivative
+                        and to finite differences of g.
 """
 from __future__ import annotations
 
@@ -77,6 +82,8 @@ def lib():
                                   ctypes.POINTER(_Params), ctypes.POINTER(_EvalOut), P]
         _lib.orc_linesearch_coeffs.argtypes = [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P, P,
                                                ctypes.POINTER(_Params), ctypes.c_int, P]
+        _lib.orc_grad_derivative.argtypes = [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P,
+                                             ctypes.POINTER(_Params), P]
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_set_threads.argtypes = [ctypes.c_int]
     return _lib
@@ -365,6 +372,22 @@ def grad_derivative(prob: Problem, T, kp: KernelParams, terms: bool = False):
             parts[q, :, k] = -tq.sum(axis=(0, 1))
     D = parts.sum(axis=0)
     return (D, parts) if terms else D
+
+
+def grad_derivative_c(prob: Problem, T, kp: KernelParams) -> np.ndarray:
+    """The D(g) of grad_derivative (same four terms per pair and unit
+    direction), as plain FP64 loops over every pair in gcvo_oracle.c, for
+    clouds too large for grad_derivative's (n_t, n_s, 3, 3) arrays."""
+    if kp.kernel_mode == 0 and (prob.tgt_cov is None or prob.src_cov is None):
+        raise ValueError("anisotropic mode needs covariances")
+    P = _params(kp, prob.tgt_feat.shape[1])
+    out = np.zeros(36)
+    rc = lib().orc_grad_derivative(_ptr(prob.tgt), _ptr(prob.tgt_cov), _ptr(prob.tgt_feat), len(prob.tgt),
+                                   _ptr(prob.src), _ptr(prob.src_cov), _ptr(prob.src_feat), len(prob.src),
+                                   _ptr(_d(T)), ctypes.byref(P), _ptr(out))
+    if rc != 0:
+        raise MemoryError("orc_grad_derivative")
+    return out.reshape(6, 6)
 
 
 def exact_step(prob: Problem, T, kp: KernelParams, res: EvalResult) -> np.ndarray:

@@ -524,19 +524,20 @@ def _e_problem(O, seed, n_t=70, n_s=60, iso=False):
 def test_exact_hessian_matches_fd_of_gradient(oracle_mod, iso):
     """G-CVO-E: D(g)[e_k] against central differences of the Lemma-1
     gradient along T exp(+-h e_k) (dense objective, so no pair crosses a
-    cutoff; Sigma' follows the rotation in both)."""
+    cutoff; Sigma' follows the rotation in both), for both restatements of
+    D(g): the NumPy one and the C loops."""
     O = oracle_mod
     prob, pair, rng = _e_problem(O, 3, iso=iso)
     kp = O.KernelParams(cutoff=0.0, kernel_mode=1 if iso else 0, iso_ell=0.15)
     T = pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)
-    Dg = O.grad_derivative(prob, T, kp)
     h = 1e-5
-    for k in range(6):
-        e = np.eye(6)[k] * h
-        gp = O.evaluate(prob, T @ O.exp_se3(e), kp).g
-        gm = O.evaluate(prob, T @ O.exp_se3(-e), kp).g
-        fd = (gp - gm) / (2 * h)
-        assert np.abs(Dg[:, k] - fd).max() <= 1e-6 * np.abs(Dg).max(), (k, Dg[:, k], fd)
+    for Dg in (O.grad_derivative(prob, T, kp), O.grad_derivative_c(prob, T, kp)):
+        for k in range(6):
+            e = np.eye(6)[k] * h
+            gp = O.evaluate(prob, T @ O.exp_se3(e), kp).g
+            gm = O.evaluate(prob, T @ O.exp_se3(-e), kp).g
+            fd = (gp - gm) / (2 * h)
+            assert np.abs(Dg[:, k] - fd).max() <= 1e-6 * np.abs(Dg).max(), (k, Dg[:, k], fd)
 
 
 def test_exact_hessian_last_term_is_gauss_newton(oracle_mod):
@@ -588,3 +589,17 @@ def test_exact_hessian_isotropic_is_self_adjoint(oracle_mod):
         assert np.abs(H - H.T).max() <= 1e-12 * n
         for wrong in (Dg - G, Dg):
             assert np.abs(wrong - wrong.T).max() > 1e-3 * n
+
+
+@pytest.mark.parametrize("mode", ["aniso_cutoff", "aniso_dense", "iso_cutoff"])
+def test_exact_hessian_c_loops_equal_numpy(oracle_mod, mode):
+    """The C restatement of D(g) (for full-size clouds) equals the NumPy one
+    to rounding, with and without the cutoff and for both kernels."""
+    O = oracle_mod
+    iso = mode.startswith("iso")
+    prob, pair, rng = _e_problem(O, 7, iso=iso)
+    kp = O.KernelParams(cutoff=0.0 if mode.endswith("dense") else 3.0, kernel_mode=1 if iso else 0, iso_ell=0.15)
+    for T in (np.eye(4), pair.T_true @ O.exp_se3(rng.normal(size=6) * 0.05)):
+        a = O.grad_derivative(prob, T, kp)
+        b = O.grad_derivative_c(prob, T, kp)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
