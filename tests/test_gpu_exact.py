@@ -37,11 +37,12 @@ def _poses(pair):
 
 
 def _oracle(O, key, case, T):
-    """D(g), H_E, f, g and gabs of the oracle at T (cached per module)."""
+    """D(g), H_E, f, g and gabs of the oracle at T (cached per module); D(g)
+    from the oracle's C loops, pinned equal to its NumPy restatement."""
     k = (key, np.asarray(T).tobytes())
     if k not in _ORACLE:
         o = O.evaluate(case.prob, T, case.kp_o)
-        Dm = O.grad_derivative(case.prob, T, case.kp_o)
+        Dm = O.grad_derivative_c(case.prob, T, case.kp_o)
         _ORACLE[k] = (Dm, Dm + o.Gamma, o)
     return _ORACLE[k]
 
@@ -51,8 +52,8 @@ def _check_exact(O, G, ctx, key, case, T, tol=TOL):
     Dm, He, o = _oracle(O, key, case, T)
     errs = (rel_f(r.f, o.f), rel_g(r.g, o.g, o.gabs), rel_H(r.D, Dm), rel_H(r.H, He))
     assert max(errs) <= tol, errs
-    # D(g) is not symmetric away from a critical point: the kernel must not
-    # have symmetrised it
+    # D(g) is not symmetric away from a critical point, so matching it to
+    # 1e-5 also shows that the kernel did not symmetrise it
     assert np.abs(Dm - Dm.T).max() > 1e-4 * np.abs(Dm).max()
     return r
 
