@@ -392,8 +392,9 @@ def grad_derivative_c(prob: Problem, T, kp: KernelParams) -> np.ndarray:
 
 def exact_step(prob: Problem, T, kp: KernelParams, res: EvalResult) -> np.ndarray:
     """G-CVO-E step: Newton with the exact Riemannian Hessian
-    H_E = D(g) + Gamma (Eq. 12), xi = -H_E^-1 g."""
-    H = grad_derivative(prob, T, kp) + res.Gamma
+    H_E = D(g) + Gamma (Eq. 12), xi = -H_E^-1 g.  D(g) from the C loops
+    (pinned equal to grad_derivative's NumPy restatement)."""
+    H = grad_derivative_c(prob, T, kp) + res.Gamma
     return np.linalg.solve(-H, res.g)
 
 
