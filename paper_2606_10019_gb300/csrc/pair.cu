@@ -202,9 +202,13 @@ __device__ int solve_gn(const double M[36], const double g[6], double xi[6]) {
 }
 
 // G-CVO-E: D(g) in the caller's frame from the grid-frame sums of the exact
-// pass.  Qm is B^T (Q - M)_o B, already moved by the code that moves M; the
-// rest is N_o = [[C, S_y^], [S_B, 0]] with S_y = -g_v, and
-// D = Qm - B^T N_o B for B = [[I, 0], [-o^, I]].
+// pass.  Per source point, with y = Sigma_ij^-1 r summed over its targets,
+// S_y = sum w y, S_B = sum w (y u^T + K) and P = p^ (tile.cu, pair_exact),
+// the pass leaves C = sum_points (-S_y^ P + P S_B) in tot[28..36] and
+// sum_points S_B in tot[37..45], row-major.  Qm is B^T (Q - M)_o B, already
+// moved by the code that moves M; the rest is N_o = [[C, S_y^], [S_B, 0]]
+// with S_y summed over all points = -g_v, and D = Qm - B^T N_o B for
+// B = [[I, 0], [-o^, I]].
 __device__ void exact_derivative(const double *tot, const double Qm[36], const double o[3], double D[36]) {
     double N[36];
 #pragma unroll
