@@ -116,6 +116,21 @@ def test_eval_exact_rgb_features_far_from_origin(env):
     _check_exact(O, G, ctx, "rgb_far", case, T, tol=3e-5)
 
 
+def test_eval_exact_dense_no_cutoff(env):
+    """The exact pass on the paper's dense objective (cutoff 0: every pair,
+    Sec. 5.4), anisotropic and isotropic, against the oracle without a
+    cutoff; every pair is a pair-eval."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=700, n_tgt=900, frame=11)
+    aniso = Case(O, pair, O.KernelParams(cutoff=0.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01, cutoff=0.0))
+    iso = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=0.0), iso=True)
+    iso.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08, cutoff=0.0))
+    for key, c in (("aniso_dense", aniso), ("iso_dense", iso)):
+        for T in _poses(pair):
+            r = _check_exact(O, G, ctx, key, c, T)
+            assert r.n_pairs == 700 * 900
+
+
 def _start(O, case, pair):
     """0.16 deg / 2.7 mm from the oracle's G-CVO-2 solution: inside the
     region where H_E is negative definite and Newton converges (from 0.4 deg
