@@ -257,23 +257,24 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
                                   int *n_iter, int *status);
 
 /* The evaluation of gcvo_eval (f, g and H = -M + Gamma at pose T) for
- * callers that cannot allocate device memory: code running while another
- * framework captures the stream into a CUDA graph, under a memory pool that
- * owns every device byte, in a real-time loop that must not meet an
- * allocation failure or the device-wide synchronisation of cudaMalloc /
- * cudaFree, or in a plug-in without a context to keep buffers in.  (The
- * paper has no counterpart; this is a deployment variant of one evaluation.)
+ * callers that must not allocate device memory: an application whose memory
+ * pool owns every device byte (a stray cudaMalloc would fail or fragment
+ * it), a real-time loop that must not meet an allocation failure or the
+ * device-wide synchronisation of cudaMalloc / cudaFree, or a plug-in without
+ * a context to keep buffers in.  (The paper has no counterpart; this is a
+ * deployment variant of one evaluation.)
  *
  * It needs no gcvo_ctx and allocates nothing: its scratch is one static
- * device array of about 5.5 MiB in the library, reserved on every device that loads
- * the library until the process exits.  The caller passes device pointers
- * for every input (host pointers are rejected, since copying them would need
- * a buffer), the target grid (built earlier with gcvo_build_grid), the
- * stream, and host outputs.  Source points are processed in the caller's
- * order, 8 per work item.
+ * device array of 5.3 MiB in the library, reserved on every device that
+ * loads the library until the process exits.  The caller passes device
+ * pointers on the grid's device for every input (host pointers and
+ * pointers to another device are rejected with GCVO_ERR_INVALID_ARG), the
+ * target grid (built earlier with gcvo_build_grid), the stream, and host
+ * outputs.  Source points are processed in the caller's order, 8 per work
+ * item.
  *  - n_src above 65536 returns GCVO_ERR_CAPACITY.
  *  - The first call on a device looks up the array's device address (a
- *    one-time set-up); make that first call before capturing a stream.
+ *    one-time set-up).
  *  - Every call reuses the same array and overwrites the previous call's
  *    contents; two calls whose GPU work overlaps (on different streams or
  *    from different host threads without ordering) race and both results

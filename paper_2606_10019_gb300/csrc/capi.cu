@@ -81,7 +81,6 @@ int ceil_log2(int64_t v) {
 // Everything the pair / finalize kernels need for a set of problems.
 struct Prepared {
     int n_problems = 0;
-    int n_groups = 0;
     int n_items = 0;            // upper bound of the work items
     int *d_nitems = nullptr;    // their count (device)
     const int64_t *d_poff = nullptr;
@@ -154,12 +153,6 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sp += al(np * sizeof(SrcDesc));
     int *d_lam = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
-    int *d_pg0 = reinterpret_cast<int *>(sp);
-    sp += al(np * sizeof(int));
-    int *d_pg1 = reinterpret_cast<int *>(sp);
-    sp += al(np * sizeof(int));
-    int *d_ngroups = reinterpret_cast<int *>(sp);
-    sp += 256;
     int *d_nitems = reinterpret_cast<int *>(sp);
     sp += 256;
     int *d_pcnt = reinterpret_cast<int *>(sp);
@@ -168,34 +161,28 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     P.d_nitems = d_nitems;
 
     GCVO_TRY(ctx->sort_keys.ensure(N * sizeof(unsigned long long), s));
-    GCVO_TRY(ctx->sort_vals.ensure(al(N * sizeof(int)) * 5, s));
+    GCVO_TRY(ctx->sort_vals.ensure(al(N * sizeof(int)) * 3, s));
     GCVO_TRY(ctx->sort_tmp.ensure(radix_sort_scratch_bytes(N), s));
     GCVO_TRY(ctx->scan_tmp.ensure(scan_scratch_bytes(N) + 1024, s));
     GCVO_TRY(ctx->src_pos.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->src_ca.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->src_cb.ensure(N * sizeof(float4), s));
-    GCVO_TRY(ctx->grp_start.ensure(N * sizeof(int), s));
-    GCVO_TRY(ctx->grp_count.ensure(N * sizeof(int), s));
-    GCVO_TRY(ctx->grp_prob.ensure(N * sizeof(int), s));
-    GCVO_TRY(ctx->grp_first.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->pprob.ensure(N * sizeof(int), s));
+    GCVO_TRY(ctx->t_pos.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->t_ca.ensure(N * sizeof(float4), s));
+    GCVO_TRY(ctx->t_cb.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->items.ensure(N * sizeof(int4), s));
     GCVO_TRY(ctx->item_prob.ensure(N * sizeof(int), s));
-    GCVO_TRY(ctx->pgroup.ensure(N * sizeof(int), s));
     if (N >= (1LL << 26)) return GCVO_ERR_CAPACITY;   // point index of a sub-tile word
     GCVO_TRY(ctx->status_word.ensure(256, s));
     char *vp = ctx->sort_vals.as<char>();
     int *vals = reinterpret_cast<int *>(vp);
     int *prob_of = reinterpret_cast<int *>(vp + al(N * sizeof(int)));
     int *local = reinterpret_cast<int *>(vp + 2 * al(N * sizeof(int)));
-    int *seg = reinterpret_cast<int *>(vp + 3 * al(N * sizeof(int)));
-    int *gid = reinterpret_cast<int *>(vp + 4 * al(N * sizeof(int)));
 
     GCVO_CUDA(cudaMemcpyAsync(d_desc, desc.data(), np * sizeof(SrcDesc), cudaMemcpyHostToDevice, s));
     GCVO_CUDA(cudaMemsetAsync(d_lam, 0, np * sizeof(int), s));
-    GCVO_CUDA(cudaMemsetAsync(d_pg0, 0x7f, np * sizeof(int), s));
-    GCVO_CUDA(cudaMemsetAsync(d_pg1, 0, np * sizeof(int), s));
     GCVO_CUDA(cudaMemsetAsync(ctx->status_word.ptr, 0, 256, s));
-    GCVO_CUDA(cudaMemsetAsync(ctx->grp_count.ptr, 0, N * sizeof(int), s));
 
     SrcArgs sa{};
     sa.desc = d_desc;
@@ -208,20 +195,13 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sa.spos = ctx->src_pos.as<float4>();
     sa.sca = ctx->src_ca.as<float4>();
     sa.scb = ctx->src_cb.as<float4>();
-    sa.pgroup = ctx->pgroup.as<int>();
-    sa.gfirst = ctx->grp_first.as<float4>();
+    sa.pprob = ctx->pprob.as<int>();
     sa.feat_dim = P.feat_dim;
     sa.iso = P.iso;
     GCVO_CUDA(launch_src_keys(sa, np, max_n, s));
     GCVO_TRY(radix_sort_pairs(sa.keys, vals, N, 30 + std::max(1, ceil_log2(np)), ctx->sort_tmp.ptr,
                               ctx->sort_tmp.bytes, s));
-    GCVO_CUDA(launch_src_segments(sa.keys, N, seg, s));
-    GCVO_TRY(scan_inclusive_max(seg, N, ctx->scan_tmp.ptr, s));
-    GCVO_CUDA(launch_src_group_heads(seg, N, gid, s));
-    GCVO_TRY(scan_inclusive_sum(gid, N, ctx->scan_tmp.ptr, s));
-    GCVO_CUDA(launch_src_groups(sa, sa.keys, gid, N, ctx->grp_start.as<int>(), ctx->grp_count.as<int>(),
-                                ctx->grp_prob.as<int>(), d_pg0, d_pg1, s));
-    GCVO_CUDA(cudaMemcpyAsync(d_ngroups, gid + N - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    GCVO_CUDA(launch_src_pack(sa, sa.keys, N, s));
     // per-problem point offsets and sizes for the work-item packing, which
     // depends on the pair schedule and is done by choose_schedule
     std::vector<int> hn(np);
@@ -237,18 +217,14 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_CUDA(cudaMemcpyAsync(d_poff, hoff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     GCVO_TRY(ctx->pack_tmp.ensure(5 * (((size_t)N + 63) / 64 * 64) * sizeof(int), s));
 
-    // read back group and item counts and ranges, source eigenvalue bounds
+    // read back the status word and the source eigenvalue bounds
     void *hp;
-    GCVO_TRY(host_pinned(ctx, (size_t)(5 * np + 8) * sizeof(int), &hp));
+    GCVO_TRY(host_pinned(ctx, (size_t)(np + 8) * sizeof(int), &hp));
     int *h = static_cast<int *>(hp);
-    GCVO_CUDA(cudaMemcpyAsync(h, d_ngroups, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 1, ctx->status_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8, d_lam, np * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GCVO_CUDA(cudaMemcpyAsync(h + 8 + np, d_pg0, np * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GCVO_CUDA(cudaMemcpyAsync(h + 8 + 2 * np, d_pg1, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaStreamSynchronize(s));
     if (h[1] & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
-    P.n_groups = h[0];
     P.probs.assign(np, ProbDev{});
     for (int p = 0; p < np; ++p) {
         ProbDev &d = P.probs[p];
@@ -260,8 +236,6 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         }
         d.status = 0;
         d.iter = 0;
-        d.g0 = h[8 + np + p];
-        d.g1 = h[8 + 2 * np + p];
         d.w0 = 0;   // set with the work items
         d.w1 = 0;
         int le = h[8 + p];
@@ -286,7 +260,6 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_items, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,
                                  s));
     GCVO_TRY(ctx->probs.ensure(np * sizeof(ProbDev), s));
-    GCVO_TRY(ctx->anchors.ensure((size_t)std::max(P.n_groups, 1) * sizeof(float4), s));
     GCVO_TRY(ctx->grids.ensure(np * sizeof(GridDev), s));
     GCVO_TRY(ctx->evalout.ensure(np * sizeof(EvalOut) + 256, s));
     std::vector<GridDev> gd(np);
@@ -301,6 +274,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
 struct IterBufs {
     PairArgs pa;
     FinalizeArgs fa;
+    TransformArgs ta;
     int *work;
     int grid;   // persistent blocks of the evaluation pass
     int sub;    // its schedule: points per sub-tile
@@ -383,7 +357,11 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
     return GCVO_OK;
 }
 
-gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max) {
+// The buffers of the per-iteration launches, the split pose constants and
+// the transformed source at the initial pose, and the pair schedule.  exact:
+// the G-CVO-E pass will run (second partial row, coordinate tails of p).
+gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max,
+                      bool exact) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     char *part = ctx->partial.as<char>();
     size_t ng = (size_t)std::max(P.n_items, 1);
@@ -391,31 +369,43 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     long long *pc = reinterpret_cast<long long *>(part + al(ng * 64 * sizeof(float)));
     int *work = reinterpret_cast<int *>(ctx->status_word.as<char>() + 64);
     int *n_active = work + 1;
+    if (exact) {
+        GCVO_TRY(ctx->partial2.ensure(ng * 64 * sizeof(float), ctx->stream));
+        GCVO_TRY(ctx->t_lo.ensure((size_t)std::max<int64_t>(P.n_points, 1) * sizeof(float4), ctx->stream));
+    }
+    TransformArgs &t = b.ta;
+    t.spos = ctx->src_pos.as<float4>();
+    t.sca = ctx->src_ca.as<float4>();
+    t.scb = ctx->src_cb.as<float4>();
+    t.pprob = ctx->pprob.as<int>();
+    t.probs = ctx->probs.as<ProbDev>();
+    t.tpos = ctx->t_pos.as<float4>();
+    t.tca = ctx->t_ca.as<float4>();
+    t.tcb = ctx->t_cb.as<float4>();
+    t.tlo = exact ? ctx->t_lo.as<float4>() : nullptr;
+    t.n = P.n_points;
+    t.iso = P.iso;
     PairArgs &a = b.pa;
-    a.spos = ctx->src_pos.as<float4>();
-    a.sca = ctx->src_ca.as<float4>();
-    a.scb = ctx->src_cb.as<float4>();
-    a.anchor = ctx->anchors.as<float4>();
-    a.gstart = ctx->grp_start.as<int>();
+    a.tpos = t.tpos;
+    a.tca = t.tca;
+    a.tcb = t.tcb;
+    a.tlo = t.tlo;
     a.items = ctx->items.as<int>();
     a.item_prob = ctx->item_prob.as<int>();
-    a.pgroup = ctx->pgroup.as<int>();
-    a.gfirst = ctx->grp_first.as<float4>();
     a.n_items = P.d_nitems;
     a.probs = ctx->probs.as<ProbDev>();
     a.grids = ctx->grids.as<GridDev>();
     a.part = pf;
+    a.part2 = exact ? ctx->partial2.as<float>() : nullptr;
     a.counts = pc;
     a.work = work;
     a.status_word = ctx->status_word.as<unsigned>();
     a.ls_literal = 0;
     FinalizeArgs &f = b.fa;
     f.probs = ctx->probs.as<ProbDev>();
-    f.spos = ctx->src_pos.as<float4>();
-    f.gstart = ctx->grp_start.as<int>();
-    f.anchor = ctx->anchors.as<float4>();
     f.grids = ctx->grids.as<GridDev>();
     f.part = pf;
+    f.part2 = a.part2;
     f.counts = pc;
     f.evalout = ctx->evalout.as<EvalOut>();
     f.logs = dlogs;
@@ -425,9 +415,10 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     f.eps_tol = 0;
     f.mu0 = 0;
     b.work = work;
-    // group anchors and float rotation at the initial pose
-    f.mode = FIN_ANCHORS;
+    // transform constants and the transformed source at the initial pose
+    f.mode = FIN_POSE;
     GCVO_CUDA(launch_finalize(f, ctx->stream));
+    GCVO_CUDA(launch_transform(t, ctx->stream));
     return choose_schedule(ctx, P, b);
 }
 
@@ -480,14 +471,6 @@ gcvo_status collect_profile(gcvo_ctx *ctx, bool keep = false) {
     return GCVO_OK;
 }
 
-// The second partial row that the G-CVO-E pass writes (slots 32..).
-gcvo_status exact_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
-    GCVO_TRY(ctx->partial2.ensure((size_t)std::max(P.n_items, 1) * 64 * sizeof(float), ctx->stream));
-    b.pa.part2 = ctx->partial2.as<float>();
-    b.fa.part2 = b.pa.part2;
-    return GCVO_OK;
-}
-
 // One iteration of Algorithm 1 on stream s: G-CVO-2 is a pair pass and the
 // Gauss-Newton finalize; G-CVO-1 a gradient pass, its finalize (direction),
 // the line-search pass and the step; G-CVO-E the exact pass and the Newton
@@ -510,6 +493,8 @@ gcvo_status enqueue_iteration(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int
         b.fa.mode = FIN_LINESEARCH;
         GCVO_CUDA(launch_finalize(b.fa, s));
     }
+    // the source at the new poses (problems that stopped keep theirs)
+    GCVO_CUDA(launch_transform(b.ta, s));
     return GCVO_OK;
 }
 
@@ -566,8 +551,7 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
         GCVO_CUDA(cudaMemsetAsync(dlogs, 0, (size_t)np * sp->k_max * sizeof(gcvo_iter_log), s));
     }
     IterBufs b{};
-    GCVO_TRY(iter_bufs(ctx, P, b, dlogs, sp->k_max));
-    if (sp->order == 3) GCVO_TRY(exact_bufs(ctx, P, b));
+    GCVO_TRY(iter_bufs(ctx, P, b, dlogs, sp->k_max, sp->order == 3));
     b.fa.eps_tol = sp->eps_tol;
     b.fa.mu0 = sp->mu0;
     int *n_active = b.fa.n_active;
@@ -738,12 +722,12 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->sort_keys, &ctx->sort_vals, &ctx->sort_tmp, &ctx->scan_tmp, &ctx->small,
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
-                      &ctx->src_cb, &ctx->grp_start, &ctx->grp_count, &ctx->grp_prob, &ctx->prob_g, &ctx->grp_first,
+                      &ctx->src_cb, &ctx->pprob, &ctx->t_pos, &ctx->t_ca, &ctx->t_cb, &ctx->t_lo,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
-                      &ctx->anchors, &ctx->items, &ctx->item_prob, &ctx->pgroup, &ctx->pack_tmp, &ctx->partial2};
+                      &ctx->items, &ctx->item_prob, &ctx->pack_tmp, &ctx->partial2};
     for (DevBuf *b : bufs) b->release();
     for (GridStore *kg : {&ctx->knn_grid, &ctx->knn_grid2}) {
-        DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
+        DevBuf *kb[] = {&kg->pos, &kg->ca, &kg->cb, &kg->plo, &kg->orig, &kg->cell_start, &kg->hkeys, &kg->hval,
                         &kg->vox_first};
         for (DevBuf *b : kb) b->release();
     }
@@ -869,6 +853,7 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
     s.pos.release();
     s.ca.release();
     s.cb.release();
+    s.plo.release();
     s.orig.release();
     s.cell_start.release();
     s.hkeys.release();
@@ -903,8 +888,7 @@ static gcvo_status eval_once(gcvo_ctx *ctx, const gcvo_grid *target, const float
     Prepared P;
     GCVO_TRY(prepare(ctx, 1, &pr, P));
     IterBufs b{};
-    GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1));
-    if (mode == PAIR_EXACT) GCVO_TRY(exact_bufs(ctx, P, b));
+    GCVO_TRY(iter_bufs(ctx, P, b, nullptr, 1, mode == PAIR_EXACT));
     int one = 1;
     GCVO_CUDA(cudaMemcpyAsync(b.fa.n_active, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     GCVO_TRY(launch_pair_pass(ctx, P, b, mode, ctx->stream));

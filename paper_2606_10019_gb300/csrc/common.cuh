@@ -64,7 +64,9 @@ struct DevBuf {
 // Points are sorted by voxel key.  pos[i] = (x - o, y - o, z - o, l0) for the
 // target grid (coordinates relative to the grid origin o, float32), and the
 // absolute coordinates for the internal kNN grid; ca[i] = (S00, S01, S02, S11),
-// cb[i] = (S12, S22, l1, l2).  Voxel (cx, cy, cz) holds the points whose
+// cb[i] = (S12, S22, l1, l2).  Target grids also keep the rounding tails of
+// the coordinates, plo[i] = (x - o) - pos[i].xyz (float), so that x - o =
+// pos + plo to about 2^-48 relative.  Voxel (cx, cy, cz) holds the points whose
 // coordinates c satisfy floor((c - corner) * inv_h) = (cx, cy, cz); its key is
 // (cx * ny + cy) * nz + cz, so the voxels of one (cx, cy) column with
 // consecutive cz are consecutive in the sorted order.
@@ -73,6 +75,7 @@ struct GridDev {
     const float4 *pos;
     const float4 *ca;
     const float4 *cb;
+    const float4 *plo;        // target grids: coordinate tails (x, y, z, 0)
     const int *orig;          // original index of each sorted point
     const int *cell_start;    // n_cells + 1 offsets into the sorted points
     const unsigned long long *hkeys;  // open-addressing table of voxel keys
@@ -155,7 +158,7 @@ __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, f
 // ---------------------------------------------------------------------------
 struct GridStore {
     GridDev d{};
-    DevBuf pos, ca, cb, orig, cell_start, hkeys, hval, vox_first;
+    DevBuf pos, ca, cb, plo, orig, cell_start, hkeys, hval, vox_first;
 };
 
 // Build a grid from SoA inputs.  absolute: keep absolute coordinates and no
@@ -184,9 +187,9 @@ struct gcvo_ctx {
     // scratch
     gcvo::DevBuf sort_keys, sort_vals, sort_tmp, scan_tmp, small;
     gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
-    gcvo::DevBuf src_pos, src_ca, src_cb;            // packed, grouped sources
-    gcvo::DevBuf grp_start, grp_count, grp_prob, prob_g, grp_first;
-    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, anchors, items, item_prob, pgroup, pack_tmp;
+    gcvo::DevBuf src_pos, src_ca, src_cb, pprob;     // packed sources (sorted) and their problems
+    gcvo::DevBuf t_pos, t_ca, t_cb, t_lo;            // the same at the current pose (k_transform)
+    gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, items, item_prob, pack_tmp;
     gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_retry;

@@ -66,15 +66,18 @@ __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long 
 
 __global__ void k_reorder(const float *xyz, const float *cov, const float *feat, int feat_dim, int64_t n,
                           const int *vals, GridDev g, bool absolute, float4 *pos, float4 *ca, float4 *cb,
-                          int *orig) {
+                          float4 *plo, int *orig) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int j = vals[i];
-    float p[3];
+    float p[3], t[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < 3; ++a) {
         float v = xyz[a * n + j];
-        p[a] = absolute ? v : (float)((double)v - g.origin[a]);
+        const double d = (double)v - g.origin[a];
+        p[a] = absolute ? v : (float)d;
+        if (!absolute) t[a] = (float)(d - (double)p[a]);
     }
+    if (plo) plo[i] = make_float4(t[0], t[1], t[2], 0.f);
     float l[3] = {0.f, 0.f, 0.f};
     for (int q = 0; q < feat_dim && feat; ++q) l[q] = feat[q * n + j];
     float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -191,6 +194,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(out.pos.ensure(n * sizeof(float4), s));
     GCVO_TRY(out.ca.ensure(n * sizeof(float4), s));
     GCVO_TRY(out.cb.ensure(n * sizeof(float4), s));
+    if (!absolute) GCVO_TRY(out.plo.ensure(n * sizeof(float4), s));
     GCVO_TRY(out.orig.ensure(n * sizeof(int), s));
     GCVO_TRY(out.cell_start.ensure((n_cells + 1) * sizeof(int), s));
     GCVO_TRY(out.hkeys.ensure(H * sizeof(unsigned long long), s));
@@ -201,7 +205,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
                                    out.hval.as<int>(), H - 1);
     k_reorder<<<blocks, 256, 0, s>>>(xyz, kp.kernel_mode == 0 ? cov : nullptr, feat, kp.feat_dim, n, vals, g,
                                      absolute, out.pos.as<float4>(), out.ca.as<float4>(), out.cb.as<float4>(),
-                                     out.orig.as<int>());
+                                     absolute ? nullptr : out.plo.as<float4>(), out.orig.as<int>());
     count_launches(3);
     GCVO_CUDA(cudaGetLastError());
     if (!absolute) {
@@ -216,6 +220,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.pos = out.pos.as<float4>();
     g.ca = out.ca.as<float4>();
     g.cb = out.cb.as<float4>();
+    g.plo = absolute ? nullptr : out.plo.as<float4>();
     g.orig = out.orig.as<int>();
     g.cell_start = out.cell_start.as<int>();
     g.hkeys = out.hkeys.as<unsigned long long>();

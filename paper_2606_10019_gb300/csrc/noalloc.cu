@@ -2,12 +2,11 @@
 // allocate device memory, with every scratch buffer carved out of one
 // file-scope device array instead of context-owned memory.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not
-// wanted -- inside a region another framework is capturing into a CUDA
-// graph, under a memory pool that owns all device memory, in a real-time
-// loop that must not risk an allocation failure or the implicit device
-// synchronisation of cudaMalloc / cudaFree, or in a plug-in that has no
-// context object to keep buffers in.
+// Who needs it: code that must not call cudaMalloc -- an application whose
+// memory pool owns every device byte (a stray allocation fails or fragments
+// the pool), a real-time loop that must not risk an allocation failure or
+// the device-wide synchronisation cudaMalloc / cudaFree can cause, or a
+// plug-in that has no context object to keep buffers in.
 //
 // The array is reserved once per device when the library is loaded and kept
 // until the process exits.  Host code never uses the symbol itself as a
@@ -30,13 +29,11 @@ constexpr int NA_MAX_ITEMS = (int)(NA_MAX_SRC / NA_ITEM);
 
 // Byte offsets of the pieces of the scratch array (each 256-aligned).
 constexpr size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+// The source records are transformed in place (one evaluation, one pose).
 constexpr size_t NA_SPOS = 0;
 constexpr size_t NA_SCA = NA_SPOS + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_SCB = NA_SCA + al256(NA_MAX_SRC * 16);
-constexpr size_t NA_ANCHOR = NA_SCB + al256(NA_MAX_SRC * 16);
-constexpr size_t NA_GSTART = NA_ANCHOR + al256(NA_MAX_SRC * 16);
-constexpr size_t NA_PGROUP = NA_GSTART + al256(NA_MAX_SRC * 4);
-constexpr size_t NA_ITEMS = NA_PGROUP + al256(NA_MAX_SRC * 4);
+constexpr size_t NA_ITEMS = NA_SCB + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_PART = NA_IPROB + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_COUNTS = NA_PART + al256((size_t)NA_MAX_ITEMS * 64 * 4);
@@ -45,20 +42,21 @@ constexpr size_t NA_GRID = NA_PROB + al256(sizeof(ProbDev));
 constexpr size_t NA_EVAL = NA_GRID + al256(sizeof(GridDev));
 constexpr size_t NA_WORDS = NA_EVAL + al256(sizeof(EvalOut));   // work, n_items, lam, status, n_active
 constexpr size_t NA_BYTES = NA_WORDS + 256;
+// 3 MiB of source records, 2 MiB of partials, 256 KiB of counters and 64 KiB
+// of work items: the 5.3 MiB the header documents
+static_assert(NA_BYTES >= size_t(5300) * 1048576 / 1000 && NA_BYTES <= size_t(5350) * 1048576 / 1000,
+              "the documented size of the static scratch (5.3 MiB)");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 // Pack the caller's SoA source (in its own order) into the float4 records of
-// the pair kernel and the largest covariance eigenvalue.  The caller's order
-// carries no spatial grouping, so every point is its own group (its own FP64
-// anchor) and a work item holds NA_ITEM consecutive points.
+// the pair kernel and the largest covariance eigenvalue.  A work item holds
+// NA_ITEM consecutive points of the caller's order.
 __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat, int feat_dim, int n, int iso,
                           unsigned char *base) {
     float4 *spos = reinterpret_cast<float4 *>(base + NA_SPOS);
     float4 *sca = reinterpret_cast<float4 *>(base + NA_SCA);
     float4 *scb = reinterpret_cast<float4 *>(base + NA_SCB);
-    int *gstart = reinterpret_cast<int *>(base + NA_GSTART);
-    int *pgroup = reinterpret_cast<int *>(base + NA_PGROUP);
     int *items = reinterpret_cast<int *>(base + NA_ITEMS);
     int *iprob = reinterpret_cast<int *>(base + NA_IPROB);
     int *words = reinterpret_cast<int *>(base + NA_WORDS);
@@ -85,8 +83,6 @@ __global__ void k_na_pack(const float *xyz, const float *cov, const float *feat,
         atomicMax(words + 2, e >= 0 ? e : e ^ 0x7fffffff);
     }
     if (bad) atomicOr(reinterpret_cast<unsigned *>(words + 3), DEV_ERR_NONFINITE);
-    gstart[i] = i;
-    pgroup[i] = i;
     if (i % NA_ITEM == 0) {
         // a work item of NA_ITEM consecutive points: first << 6 | points
         items[i / NA_ITEM] = (int)(((unsigned)i << 6) | (unsigned)min(NA_ITEM, n - i));
@@ -113,8 +109,6 @@ __global__ void k_na_setup(NaSetup a, unsigned char *base) {
     }
     P->status = 0;
     P->iter = 0;
-    P->g0 = 0;
-    P->g1 = a.n_src;
     P->w0 = 0;
     P->w1 = a.n_items;
     const int le = words[2];
@@ -150,7 +144,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
         if (!std::isfinite(T[k])) return GCVO_ERR_NONFINITE;
     const int dev = target->device;
     if (dev < 0 || dev >= 64) return GCVO_ERR_INVALID_ARG;
-    // inputs must already be on the device (a copy would need a buffer)
+    // inputs must already be on the grid's device (a copy would need a buffer)
     for (const float *p : {src_xyz, src_cov, src_feat}) {
         if (!p) continue;
         cudaPointerAttributes at{};
@@ -159,6 +153,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
             return GCVO_ERR_INVALID_ARG;
         }
         if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return GCVO_ERR_INVALID_ARG;
+        if (at.type == cudaMemoryTypeDevice && at.device != dev) return GCVO_ERR_INVALID_ARG;
     }
     GCVO_CUDA(cudaSetDevice(dev));
     unsigned char *base;
@@ -198,9 +193,6 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     int *words = reinterpret_cast<int *>(base + NA_WORDS);
     FinalizeArgs fa{};
     fa.probs = reinterpret_cast<ProbDev *>(base + NA_PROB);
-    fa.spos = reinterpret_cast<const float4 *>(base + NA_SPOS);
-    fa.gstart = reinterpret_cast<const int *>(base + NA_GSTART);
-    fa.anchor = reinterpret_cast<float4 *>(base + NA_ANCHOR);
     fa.grids = reinterpret_cast<const GridDev *>(base + NA_GRID);
     fa.part = reinterpret_cast<const float *>(base + NA_PART);
     fa.counts = reinterpret_cast<const long long *>(base + NA_COUNTS);
@@ -209,16 +201,24 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     fa.n_active = words + 4;
     fa.n_problems = 1;
     fa.k_max = 1;
-    fa.mode = FIN_ANCHORS;
+    fa.mode = FIN_POSE;
     GCVO_CUDA(launch_finalize(fa, s));
+    // the source in the grid's frame at T, in place
+    TransformArgs ta{};
+    ta.spos = ta.tpos = reinterpret_cast<float4 *>(base + NA_SPOS);
+    ta.sca = ta.tca = reinterpret_cast<float4 *>(base + NA_SCA);
+    ta.scb = ta.tcb = reinterpret_cast<float4 *>(base + NA_SCB);
+    ta.tlo = nullptr;
+    ta.pprob = nullptr;
+    ta.probs = fa.probs;
+    ta.n = n;
+    ta.iso = iso ? 1 : 0;
+    GCVO_CUDA(launch_transform(ta, s));
     PairArgs pa{};
-    pa.spos = fa.spos;
-    pa.sca = reinterpret_cast<const float4 *>(base + NA_SCA);
-    pa.scb = reinterpret_cast<const float4 *>(base + NA_SCB);
-    pa.anchor = fa.anchor;
-    pa.gstart = fa.gstart;
-    pa.pgroup = reinterpret_cast<const int *>(base + NA_PGROUP);
-    pa.gfirst = pa.spos;   // every point is its own group
+    pa.tpos = ta.tpos;
+    pa.tca = ta.tca;
+    pa.tcb = ta.tcb;
+    pa.tlo = nullptr;
     pa.items = reinterpret_cast<const int *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
     pa.n_items = words + 1;

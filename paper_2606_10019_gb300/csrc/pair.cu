@@ -1,13 +1,17 @@
-// The FP64 side of the per-iteration hot path of Algorithm 1, and the source
-// grouping done once per call:
-//   k_finalize -- FP64 sum of the item partials of each problem, change of
-//                 frame, connection term (Eq. 12), the 6x6 solve of Eq. (13)
-//                 (or the G-CVO-E Newton step with the exact Hessian) and
-//                 the update T <- T exp(xi); per-group anchors for the pair
-//                 kernel (tile.cu) at the new pose.
-// Source grouping sorts each source cloud by a Morton code of its own voxels
-// and cuts it into groups of at most 32 points that never straddle a coarse
-// voxel; every group gets an FP64 anchor, every point its group index.
+// The FP64 side of the per-iteration hot path of Algorithm 1, the transform
+// of the source points, and the source packing done once per call:
+//   k_finalize  -- FP64 sum of the item partials of each problem, change of
+//                  frame, connection term (Eq. 12), the 6x6 solve of Eq. (13)
+//                  (or the G-CVO-E Newton step with the exact Hessian) and
+//                  the update T <- T exp(xi); the split pose constants the
+//                  transform reads.
+//   k_transform -- every source point of an active problem moved into the
+//                  target grid's frame at the current pose (Algorithm 1,
+//                  T^-1 z): p = R^T (z - t) - o in double-float arithmetic,
+//                  stored as a float head and tail, and Sigma' = R^T Sigma R.
+// Source packing sorts each source cloud by a Morton code of its own voxels
+// and writes one float4 record triple per point in that order.
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -337,7 +341,7 @@ __device__ inline void apply_step(ProbDev *P, const double xi[6], gcvo_iter_log 
 }
 
 // The per-problem FP64 step (one thread): returns 1 when the pose changed
-// and the problem stays active, so the group anchors must be refreshed.
+// and the problem stays active, so the transform constants must be refreshed.
 __device__ int finalize_thread0(const FinalizeArgs &a, int prob, ProbDev *P, const double *tot,
                                 const long long *ctot) {
     const GridDev *G = a.grids + prob;
@@ -522,28 +526,26 @@ __device__ int finalize_thread0(const FinalizeArgs &a, int prob, ProbDev *P, con
     return P->status == 0;
 }
 
-// Per-group anchors R^T (z_g - t) - o in FP64 (stored as float), and R as
-// float, for the pair kernel's transform at the current pose.
-__device__ void refresh_anchors(const FinalizeArgs &a, int prob, ProbDev *P) {
+// The split constants of the transform at the pose P->T: R as float head
+// and tail, and c = R^T t + o (o the grid origin) likewise.
+__device__ void refresh_pose(const FinalizeArgs &a, int prob, ProbDev *P) {
     const GridDev *G = a.grids + prob;
-    double R[9], t[3], o[3];
+    double c[3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = P->T[k];
+    for (int k = 0; k < 3; ++k)
+        c[k] = P->T[k] * P->T[9] + P->T[3 + k] * P->T[10] + P->T[6 + k] * P->T[11] + G->origin[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float h = (float)P->T[k];
+        P->Rh[k] = h;
+        P->Rl[k] = (float)(P->T[k] - (double)h);
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        t[k] = P->T[9 + k];
-        o[k] = G->origin[k];
+        const float h = (float)c[k];
+        P->ch[k] = h;
+        P->cl[k] = (float)(c[k] - (double)h);
     }
-    for (int g = P->g0 + threadIdx.x; g < P->g1; g += blockDim.x) {
-        float4 z = a.spos[a.gstart[g]];
-        double d0 = (double)z.x - t[0], d1 = (double)z.y - t[1], d2 = (double)z.z - t[2];
-        a.anchor[g] = make_float4((float)(R[0] * d0 + R[3] * d1 + R[6] * d2 - o[0]),
-                                  (float)(R[1] * d0 + R[4] * d1 + R[7] * d2 - o[1]),
-                                  (float)(R[2] * d0 + R[5] * d1 + R[8] * d2 - o[2]), 0.f);
-    }
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) P->R32[k] = (float)R[k];
 }
 
 constexpr int FIN_THREADS = 512;   // 16 parts x 32 slots of the partial sums
@@ -553,8 +555,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(FinalizeArgs a) {
     if (prob >= a.n_problems) return;
     ProbDev *P = a.probs + prob;
     if (P->status != 0) return;
-    if (a.mode == FIN_ANCHORS) {
-        refresh_anchors(a, prob, P);
+    if (a.mode == FIN_POSE) {
+        if (threadIdx.x == 0) refresh_pose(a, prob, P);
         return;
     }
     __shared__ double red[FIN_THREADS];
@@ -598,10 +600,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(FinalizeArgs a) {
         }
         __syncthreads();
     }
-    __shared__ int s_upd;
-    if (threadIdx.x == 0) s_upd = finalize_thread0(a, prob, P, tot, ctot);
-    __syncthreads();
-    if (s_upd) refresh_anchors(a, prob, P);
+    if (threadIdx.x == 0 && finalize_thread0(a, prob, P, tot, ctot)) refresh_pose(a, prob, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,49 +655,96 @@ __global__ void k_src_keys(SrcArgs a) {
     if (bad) atomicOr(a.status_word, DEV_ERR_NONFINITE);
 }
 
-__global__ void k_src_segments(const unsigned long long *keys, int64_t n, int *seg) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One packed record triple per sorted source point, and its problem.
+__global__ void k_src_pack(SrcArgs a, const unsigned long long *keys, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool head = i == 0 || (keys[i] >> 9) != (keys[i - 1] >> 9);
-    seg[i] = head ? (int)i : 0;
-}
-
-__global__ void k_src_group_heads(const int *seg_start, int64_t n, int *gh) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    gh[i] = ((i - seg_start[i]) % 32 == 0) ? 1 : 0;
-}
-
-__global__ void k_src_groups(SrcArgs a, const unsigned long long *keys, const int *gid_incl, int64_t n,
-                             int *gstart, int *gcount, int *gprob, int *pg0, int *pg1) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int g = gid_incl[i] - 1;
-    int p = (int)(keys[i] >> 30);
-    bool head = i == 0 || gid_incl[i] != gid_incl[i - 1];
-    if (head) {
-        gstart[g] = (int)i;
-        gprob[g] = p;
-        atomicMin(pg0 + p, g);
-        atomicMax(pg1 + p, g + 1);
-    }
-    atomicAdd(gcount + g, 1);
-    a.pgroup[i] = g;
-    // packed source record in group order
-    int src = a.vals[i];
+    const int src = a.vals[i];
     const SrcDesc d = a.desc[a.prob_of[src]];
-    int li = a.local[src];
-    float x = d.xyz[li], y = d.xyz[d.n + li], z = d.xyz[2 * d.n + li];
-    float f0 = d.feat ? d.feat[li] : 1.f;
-    float f1 = (d.feat && a.feat_dim > 1) ? d.feat[d.n + li] : 0.f;
-    float f2 = (d.feat && a.feat_dim > 2) ? d.feat[2 * d.n + li] : 0.f;
-    float s[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t li = a.local[src];
+    const float x = d.xyz[li], y = d.xyz[d.n + li], z = d.xyz[2 * d.n + li];
+    const float f0 = d.feat ? d.feat[li] : 1.f;
+    const float f1 = (d.feat && a.feat_dim > 1) ? d.feat[d.n + li] : 0.f;
+    const float f2 = (d.feat && a.feat_dim > 2) ? d.feat[2 * d.n + li] : 0.f;
+    float s6[6] = {0, 0, 0, 0, 0, 0};
     if (!a.iso && d.cov)
-        for (int k = 0; k < 6; ++k) s[k] = d.cov[k * d.n + li];
+        for (int k = 0; k < 6; ++k) s6[k] = d.cov[k * d.n + li];
     a.spos[i] = make_float4(x, y, z, f0);
-    if (head) a.gfirst[g] = make_float4(x, y, z, 0.f);
-    a.sca[i] = make_float4(s[0], s[1], s[2], s[3]);
-    a.scb[i] = make_float4(s[4], s[5], f1, f2);
+    a.sca[i] = make_float4(s6[0], s6[1], s6[2], s6[3]);
+    a.scb[i] = make_float4(s6[4], s6[5], f1, f2);
+    a.pprob[i] = (int)(keys[i] >> 30);
+}
+
+// ---------------------------------------------------------------------------
+// The transform of Algorithm 1 (T^-1 z) for every point of an active
+// problem.  p = R^T z - c is formed in double-float arithmetic from the
+// float head / tail splits of R and c: each head product R_h z is split
+// exactly into a float and its rounding error with one FMA (the
+// error-free product of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005), the products are added with Knuth's
+// TwoSum and the rounding errors, the tail products and c's tail are
+// summed in a float alongside (their Sum2 / Dot2 scheme), and a final
+// FastTwoSum gives p = p_hi + p_lo with an error near 2^-48 |R| |z|.
+// Sigma' = R^T Sigma R is formed in float from the head of R.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__global__ void k_transform(TransformArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const ProbDev *P = a.probs + (a.pprob ? a.pprob[i] : 0);
+        if (P->status != 0) continue;   // converged or failed: left as it was
+        const float4 z = a.spos[i];
+        const float4 zb = a.scb[i];
+        const float zz[3] = {z.x, z.y, z.z};
+        float hi[3], lo[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float s = 0.f, err = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float rh = P->Rh[3 * j + k];
+                const float pr = __fmul_rn(rh, zz[j]);
+                const float pe = __fmaf_rn(rh, zz[j], -pr);
+                float e;
+                two_sum(s, pr, s, e);
+                err = __fadd_rn(err, __fadd_rn(__fadd_rn(e, pe), __fmul_rn(P->Rl[3 * j + k], zz[j])));
+            }
+            float e;
+            two_sum(s, -P->ch[k], s, e);
+            err = __fadd_rn(err, __fsub_rn(e, P->cl[k]));
+            hi[k] = __fadd_rn(s, err);
+            lo[k] = __fsub_rn(err, __fsub_rn(hi[k], s));
+        }
+        const float sg = P->sigma2;
+        a.tpos[i] = make_float4(hi[0], hi[1], hi[2], sg * z.w);
+        if (a.tlo) a.tlo[i] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!a.iso) {
+            const float4 za = a.sca[i];
+            const float sm[9] = {za.x, za.y, za.z, za.y, za.w, zb.x, za.z, zb.x, zb.y};
+            float Rf[9], T1[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Rf[k] = P->Rh[k];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    T1[3 * r + c] = sm[3 * r] * Rf[c] + sm[3 * r + 1] * Rf[3 + c] + sm[3 * r + 2] * Rf[6 + c];
+            q[0] = Rf[0] * T1[0] + Rf[3] * T1[3] + Rf[6] * T1[6];
+            q[1] = Rf[0] * T1[1] + Rf[3] * T1[4] + Rf[6] * T1[7];
+            q[2] = Rf[0] * T1[2] + Rf[3] * T1[5] + Rf[6] * T1[8];
+            q[3] = Rf[1] * T1[1] + Rf[4] * T1[4] + Rf[7] * T1[7];
+            q[4] = Rf[1] * T1[2] + Rf[4] * T1[5] + Rf[7] * T1[8];
+            q[5] = Rf[2] * T1[2] + Rf[5] * T1[5] + Rf[8] * T1[8];
+        }
+        a.tca[i] = make_float4(q[0], q[1], q[2], q[3]);
+        a.tcb[i] = make_float4(q[4], q[5], sg * zb.z, sg * zb.w);
+    }
 }
 
 }  // namespace
@@ -719,21 +765,16 @@ cudaError_t launch_src_keys(const SrcArgs &a, int n_problems, int64_t max_n, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_src_segments(const unsigned long long *keys, int64_t n, int *seg, cudaStream_t s) {
-    k_src_segments<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, seg);
+cudaError_t launch_src_pack(const SrcArgs &a, const unsigned long long *keys, int64_t n, cudaStream_t s) {
+    k_src_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, keys, n);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStream_t s) {
-    k_src_group_heads<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seg, n, gh);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
-                              int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s) {
-    k_src_groups<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, keys, gid, n, gstart, gcount, gprob, pg0, pg1);
+cudaError_t launch_transform(const TransformArgs &a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((a.n + 255) / 256, 1 << 20);
+    k_transform<<<(unsigned)blocks, 256, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }

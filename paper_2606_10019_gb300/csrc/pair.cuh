@@ -17,13 +17,15 @@ constexpr int PAIR_SLOTS_EXACT = 46;   // f, g, Q - M (21), C (9), S_B (9): G-CV
 
 enum PairMode { PAIR_EVAL = 0, PAIR_LINESEARCH = 1, PAIR_EXACT = 2 };
 // FIN_EXACT: the G-CVO-E Newton step with H_E = D(g) + Gamma;
-// FIN_EXACT_EVAL: f, g, D(g) and H_E into EvalOut (M holds D(g)).
+// FIN_EXACT_EVAL: f, g, D(g) and H_E into EvalOut (M holds D(g));
+// FIN_POSE: only the split pose constants of ProbDev (Rh, Rl, ch, cl) for
+// the initial pose.
 enum FinMode {
     FIN_EVAL = 0,
     FIN_GN = 1,
     FIN_GRAD = 2,
     FIN_LINESEARCH = 3,
-    FIN_ANCHORS = 4,
+    FIN_POSE = 4,
     FIN_EXACT = 5,
     FIN_EXACT_EVAL = 6
 };
@@ -32,11 +34,14 @@ enum FinMode {
 struct ProbDev {
     double T[12];      // current pose: R row-major (9), then t (3)
     double dir[6];     // G-CVO-1 search direction (caller frame)
-    float R32[9];      // R rounded to float (pair kernel)
+    // p = R^T (z - t) - o = R^T z - c with c = R^T t + o, every FP64 value
+    // split into a float head and a float tail (head + tail = the FP64
+    // value to about 2^-48 relative) for the double-float transform
+    float Rh[9], Rl[9];
+    float ch[3], cl[3];
     float dir32[6];    // the search direction with v' = omega x o + v (grid-origin frame)
     int status;        // 0 active, 1 converged, 2 k_max reached, < 0: -gcvo_status
     int iter;
-    int g0, g1;        // range of source groups
     int w0, w1;        // range of packed work items
     float rho2;        // Euclidean pre-test radius squared
     float c2;          // cutoff squared
@@ -49,12 +54,13 @@ struct EvalOut {
     long long n_pairs, n_kept, n_cand;
 };
 
+// Source points in the target grid's frame at the current pose, written by
+// k_transform once per iteration (sorted order, one record per point):
+//   tpos = (p_hi, sigma^2 l0), tca = (S'xx, S'xy, S'xz, S'yy),
+//   tcb = (S'yz, S'zz, sigma^2 l1, sigma^2 l2), tlo = (p_lo, 0),
+// with p = R^T (z - t) - o = p_hi + p_lo (double-float) and S' = R^T S R.
 struct PairArgs {
-    const float4 *spos, *sca, *scb;
-    const float4 *anchor;      // per group: R^T (z_g - t) - o, z_g its first point
-    const int *gstart;         // first point of each group
-    const int *pgroup;         // group of each point
-    const float4 *gfirst;      // position of each group's first point
+    const float4 *tpos, *tca, *tcb, *tlo;
     const int *items;          // per item (sub-tile): first point << 6 | points
     const int *item_prob;
     const int *n_items;
@@ -70,9 +76,6 @@ struct PairArgs {
 
 struct FinalizeArgs {
     ProbDev *probs;
-    const float4 *spos;
-    const int *gstart;
-    float4 *anchor;
     const GridDev *grids;
     const float *part;
     const float *part2;        // FIN_EXACT*: slots 32..
@@ -99,9 +102,19 @@ struct SrcArgs {
     int *lam_enc;
     unsigned *status_word;
     float4 *spos, *sca, *scb;
-    int *pgroup;
-    float4 *gfirst;
+    int *pprob;                // problem of each sorted point
     int feat_dim;
+    int iso;
+};
+
+// The per-iteration transform of every source point of the active problems
+// into the target grid's frame (k_transform).
+struct TransformArgs {
+    const float4 *spos, *sca, *scb;   // packed source records, sorted (caller frame)
+    const int *pprob;                 // problem of each point (null: all problem 0)
+    const ProbDev *probs;
+    float4 *tpos, *tca, *tcb, *tlo;   // outputs (tlo may be null)
+    int64_t n;
     int iso;
 };
 
@@ -112,10 +125,8 @@ int pair_blocks_per_sm(int mode, bool iso, int fd, int sub);
 cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
 cudaError_t launch_src_keys(const SrcArgs &a, int n_problems, int64_t max_n, cudaStream_t s);
-cudaError_t launch_src_segments(const unsigned long long *keys, int64_t n, int *seg, cudaStream_t s);
-cudaError_t launch_src_group_heads(const int *seg, int64_t n, int *gh, cudaStream_t s);
-cudaError_t launch_src_groups(const SrcArgs &a, const unsigned long long *keys, const int *gid, int64_t n,
-                              int *gstart, int *gcount, int *gprob, int *pg0, int *pg1, cudaStream_t s);
+cudaError_t launch_src_pack(const SrcArgs &a, const unsigned long long *keys, int64_t n, cudaStream_t s);
+cudaError_t launch_transform(const TransformArgs &a, cudaStream_t s);
 // Work items (sub-tiles of at most `sub` points inside one Morton voxel of
 // level `level`: edge rho / 4 * 2^level) over the n sorted source points (keys as sorted; problem p's
 // points start at point_off[p]): items[it] = first point << 6 | points,

@@ -9,10 +9,9 @@
 // on one sub-tile at a time (a work item); it takes up to PAIR_GRAB items per
 // atomic on the global counter, so the counter is touched rarely, and no warp
 // waits for another.
-//  1. Every point is moved into the target grid's frame with T^-1
-//     (Algorithm 1): p_j - o = R^T (z_j - z_g) + a_g, where a_g =
-//     R^T (z_g - t) - o is its group's anchor, computed in FP64 by the
-//     finalize; Sigma'_j = R^T Sigma_j R.
+//  1. Every point is read in the target grid's frame at the current pose
+//     (Algorithm 1: p_j = R^T (z_j - t) - o and Sigma'_j = R^T Sigma_j R),
+//     as k_transform (pair.cu) wrote it for this iteration.
 //  2. The voxel columns (cx, cy) that meet the sub-tile's bounding box grown
 //     by rho are listed, one per lane.  Points are sorted by voxel with cz
 //     fastest, so the voxels of one column over the needed cz range hold one
@@ -39,7 +38,11 @@
 // staged target meets every point: the same code visits all pairs.
 // The G-CVO-E pass (PAIR_EXACT) visits the same pairs and adds the sums of
 // the exact directional derivative of g (pair_exact); its 46 values per
-// sub-tile go to two partial rows.
+// sub-tile go to two partial rows.  The exact derivative is far more
+// sensitive to the positions than H_GN (its weight-change and Gauss-Newton
+// terms each reach several times its norm and cancel), so that pass forms
+// r from double-float positions on both sides: r = (x_hi - p_hi) +
+// (x_lo - p_lo), with the target grid's tails staged beside the points.
 #include "common.cuh"
 #include "pair.cuh"
 #include "ptx.cuh"
@@ -51,22 +54,25 @@ static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
 static_assert(PAIR_SLOTS_EXACT * 33 * 4 <= PAIR_WCAP * 48, "exact epilogue transpose fits in pos, ca, cb");
 
-// Per warp: staged target points, the list of those near the sub-tile, and
-// the mbarrier the bulk copies complete on.
+// Per warp: staged target points (with their coordinate tails when LO),
+// the list of those near the sub-tile, and the mbarrier the bulk copies
+// complete on.
+template <bool LO>
 struct __align__(16) WarpStage {
     float4 pos[PAIR_WCAP];
     float4 ca[PAIR_WCAP];
     float4 cb[PAIR_WCAP];
+    float4 lo[LO ? PAIR_WCAP : 1];
     unsigned short list[PAIR_WCAP];
     uint64_t bar;
 };
 
-// One anisotropic pair (Eq. 7) into the lane sums t[10].
+// One anisotropic pair (Eq. 7), r = x_i - p_j, into the lane sums t[10].
 template <int FD>
-__device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, const float4 cbv, float px, float py,
-                                           float pz, float l0, float l1, float l2, const float q[6], float rho2,
-                                           float c2, bool act, float *t, int &n_pairs, int &n_kept) {
-    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+__device__ __forceinline__ void pair_aniso(const float r0, const float r1, const float r2, const float4 x,
+                                           const float4 ca, const float4 cbv, float l0, float l1, float l2,
+                                           const float q[6], float rho2, float c2, bool act, float *t, int &n_pairs,
+                                           int &n_kept) {
     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
     const bool in = act && rr <= rho2;
     float cij = x.w * l0;
@@ -112,10 +118,10 @@ __device__ __forceinline__ void pair_aniso(const float4 x, const float4 ca, cons
 // Sigma'_j changes Sigma_ij^-1 r by K omega and r^T Sigma_ij^-1 r by
 // -2 u . omega (Sec. 3.4, the four terms of the derivative of Eq. 8).
 template <int FD>
-__device__ __forceinline__ void pair_exact(const float4 x, const float4 ca, const float4 cbv, float px, float py,
-                                           float pz, float l0, float l1, float l2, const float q[6], float rho2,
-                                           float c2, bool act, float *t, int &n_pairs, int &n_kept) {
-    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+__device__ __forceinline__ void pair_exact(const float r0, const float r1, const float r2, const float4 x,
+                                           const float4 ca, const float4 cbv, float l0, float l1, float l2,
+                                           const float q[6], float rho2, float c2, bool act, float *t, int &n_pairs,
+                                           int &n_kept) {
     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
     const bool in = act && rr <= rho2;
     float cij = x.w * l0;
@@ -248,12 +254,13 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
     constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : MODE == PAIR_EXACT ? 25 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? PAIR_SLOTS : MODE == PAIR_EXACT ? PAIR_SLOTS_EXACT : 5;
-    __shared__ WarpStage stage[PAIR_WARPS];
+    constexpr bool LO = MODE == PAIR_EXACT;
+    __shared__ WarpStage<LO> stage[PAIR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    WarpStage &S = stage[w];
+    WarpStage<LO> &S = stage[w];
     if (lane == 0) mbar_init(&S.bar, 1);
     __syncwarp();
     unsigned parity = 0;
@@ -294,41 +301,34 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
         const bool sval = si < cnt;
 
-        // ---- 1. the lane's source point in the grid frame
-        float Rf[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Rf[k] = P->R32[k];
+        // ---- 1. the lane's source point in the grid frame (k_transform)
         const int jj = j0 + (sval ? si : 0);
-        const int grp = a.pgroup[jj];
-        const float4 anc = a.anchor[grp];
-        const float4 zg = a.gfirst[grp];
-        const float4 z = a.spos[jj];
-        const float4 zb = a.scb[jj];
-        const float e0 = z.x - zg.x, e1 = z.y - zg.y, e2 = z.z - zg.z;
-        const float px = anc.x + (Rf[0] * e0 + Rf[3] * e1 + Rf[6] * e2);
-        const float py = anc.y + (Rf[1] * e0 + Rf[4] * e1 + Rf[7] * e2);
-        const float pz = anc.z + (Rf[2] * e0 + Rf[5] * e1 + Rf[8] * e2);
-        float qv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Sigma'_j = R^T Sigma_j R
-        if (!ISO) {
-            const float4 za = a.sca[jj];
-            const float sm[9] = {za.x, za.y, za.z, za.y, za.w, zb.x, za.z, zb.x, zb.y};
-            float T1[9];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    T1[3 * r + c] = sm[3 * r] * Rf[c] + sm[3 * r + 1] * Rf[3 + c] + sm[3 * r + 2] * Rf[6 + c];
-            qv[0] = Rf[0] * T1[0] + Rf[3] * T1[3] + Rf[6] * T1[6];
-            qv[1] = Rf[0] * T1[1] + Rf[3] * T1[4] + Rf[6] * T1[7];
-            qv[2] = Rf[0] * T1[2] + Rf[3] * T1[5] + Rf[6] * T1[8];
-            qv[3] = Rf[1] * T1[1] + Rf[4] * T1[4] + Rf[7] * T1[7];
-            qv[4] = Rf[1] * T1[2] + Rf[4] * T1[5] + Rf[7] * T1[8];
-            qv[5] = Rf[2] * T1[2] + Rf[5] * T1[5] + Rf[8] * T1[8];
+        const float4 P4 = a.tpos[jj];
+        const float px = P4.x, py = P4.y, pz = P4.z;
+        const float l0 = P4.w;   // sigma^2 l0
+        float l1 = 0.f, l2 = 0.f;
+        float qv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Sigma'_j
+        if (FD > 1 || !ISO) {
+            const float4 B4 = a.tcb[jj];
+            qv[4] = B4.x;
+            qv[5] = B4.y;
+            l1 = B4.z;
+            l2 = B4.w;
         }
-        const float sg = P->sigma2;
-        const float l0 = sg * z.w;
-        const float l1 = FD > 1 ? sg * zb.z : 0.f;
-        const float l2 = FD > 1 ? sg * zb.w : 0.f;
+        if (!ISO) {
+            const float4 A4 = a.tca[jj];
+            qv[0] = A4.x;
+            qv[1] = A4.y;
+            qv[2] = A4.z;
+            qv[3] = A4.w;
+        }
+        float plx = 0.f, ply = 0.f, plz = 0.f;   // tail of p (G-CVO-E pass)
+        if (LO) {
+            const float4 L4 = a.tlo[jj];
+            plx = L4.x;
+            ply = L4.y;
+            plz = L4.z;
+        }
         const float rho2 = P->rho2, c2 = P->c2, iso_inv = P->iso_inv;
 
         // G-CVO-1 second pass: a_k = (xi^)^k p, xi the search direction
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 // ---- stage the chunk [base, base + m) (bulk copies)
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * 48u);
+                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (LO ? 64u : 48u));
                 __syncwarp();
                 {
                     const int s0 = max(off, base), s1 = min(off + rl, base + m);
@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         bulk_g2s(S.pos + dst, G->pos + src, bytes, &S.bar);
                         bulk_g2s(S.ca + dst, G->ca + src, bytes, &S.bar);
                         bulk_g2s(S.cb + dst, G->cb + src, bytes, &S.bar);
+                        if (LO) bulk_g2s(S.lo + dst, G->plo + src, bytes, &S.bar);
                     }
                 }
                 {
@@ -474,17 +475,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     const bool act = sval && idx < L;
                     const int k = S.list[min(idx, L - 1)];
                     const float4 x = S.pos[k];
+                    float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+                    if (LO) {
+                        // r = (x_hi - p_hi) + (x_lo - p_lo)
+                        const float4 xl = S.lo[k];
+                        r0 += xl.x - plx;
+                        r1 += xl.y - ply;
+                        r2 += xl.z - plz;
+                    }
                     if (MODE == PAIR_EVAL && !ISO) {
-                        pair_aniso<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                        pair_aniso<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
                                        n_kept);
                         continue;
                     }
                     if constexpr (MODE == PAIR_EXACT && !ISO) {
-                        pair_exact<FD>(x, S.ca[k], S.cb[k], px, py, pz, l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                        pair_exact<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
                                        n_kept);
                         continue;
                     }
-                    const float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
                     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
                     const bool in = act && rr <= rho2;
                     float cij = x.w * l0;

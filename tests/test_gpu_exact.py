@@ -84,6 +84,27 @@ def test_eval_exact_every_schedule(env, corner, sub):
         G.gcvo_pair_schedule(ctx, 0)
 
 
+@pytest.mark.parametrize("frame", [0, 1, 2, 3])
+def test_eval_exact_small_corner_at_identity(env, frame):
+    """400-point corner pairs at the identity, every schedule: the input on
+    which the exact pass once missed the oracle by 1.05e-5 (frame 0).  At
+    this pose H_E's weight-change and Gauss-Newton terms are each about 8
+    times its norm, so H_E moves by up to 1e-5 of its norm when the
+    positions move by one float32 rounding (the oracle fed the kernel's
+    former float grid-frame coordinates reproduced that miss entry by
+    entry).  The pass now forms r from double-float positions on both
+    sides; the bound stays 1e-5."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=400, n_tgt=400, frame=frame)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01, eig_ratio=100.0))
+    try:
+        for sub in (4, 8, 16, 32):
+            G.gcvo_pair_schedule(ctx, sub)
+            _check_exact(O, G, ctx, f"small{frame}", case, np.eye(4))
+    finally:
+        G.gcvo_pair_schedule(ctx, 0)
+
+
 def test_eval_exact_agrees_with_gauss_newton_part(env, corner):
     """f and g of the exact pass equal those of the Gauss-Newton pass, and
     the Gauss-Newton evaluation's M is the oracle's fourth term of D(g)."""

@@ -90,6 +90,56 @@ def test_eval_dense_no_cutoff(env):
             assert r.n_pairs == 700 * 900
 
 
+def _rho_count_bounds(O, case, T, rho):
+    """The oracle's count of pairs with |r| <= rho (the pair-eval of the
+    metric), at radii widened and narrowed by the float32 rounding of the
+    kernel's grid-frame coordinates: pairs inside that band may fall on
+    either side of rho in float32, every other pair is decided alike."""
+    src = case.prob.src @ T[:3, :3] + T[:3, 3]      # any frame: only the extent matters
+    ext = max(np.abs(case.prob.tgt).max(), np.abs(src).max(), np.abs(case.prob.src).max()) + 2 * rho
+    band = 4.0 * 2.0 ** -24 * (ext + rho)
+    lo = O.evaluate(case.prob, T, O.KernelParams(**{**case.kp_o.__dict__, "rho": rho - band})).n_rho
+    hi = O.evaluate(case.prob, T, O.KernelParams(**{**case.kp_o.__dict__, "rho": rho + band})).n_rho
+    return lo, hi
+
+
+@pytest.mark.parametrize("kind", ["corner", "lidar", "isotropic"])
+def test_pair_eval_count_matches_oracle(env, kind):
+    """The unit of the pair-evals/s metric: the kernel's count of pairs with
+    |r| <= rho equals the oracle's count of the same pairs at the kernel's
+    own rho (gcvo_eval_stats.rho), exactly when no pair lies within float32
+    rounding of rho, and otherwise between the counts just inside and just
+    outside that band.  Every schedule counts the same pairs."""
+    O, G, ctx, dev = env
+    if kind == "lidar":
+        pair = D.LidarSequence(n_frames=2).pair(0)
+        pair.tgt_xyz, pair.tgt_feat = D.subsample(np.random.default_rng(3), pair.tgt_xyz, pair.tgt_feat, 5000)
+        pair.src_xyz, pair.src_feat = D.subsample(np.random.default_rng(4), pair.src_xyz, pair.src_feat, 5000)
+        case = Case(O, pair, O.KernelParams(cutoff=3.0), eig_max=0.09)
+        case.gpu(G, ctx, dev, G.kernel_params(eig_max=0.09))
+    elif kind == "corner":
+        pair = D.make_corner_pair(n_src=1500, n_tgt=1300, frame=9)
+        case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
+    else:
+        pair = D.make_corner_pair(n_src=1500, n_tgt=1300, frame=9)
+        case = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=3.0), iso=True)
+        case.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08))
+    for T in _poses(pair):
+        counts = set()
+        try:
+            for sub in (4, 8, 16, 32):
+                G.gcvo_pair_schedule(ctx, sub)
+                r = G.gcvo_eval(ctx, case.grid, *case.src, T)
+                counts.add(int(r.n_pairs))
+        finally:
+            G.gcvo_pair_schedule(ctx, 0)
+        assert len(counts) == 1, counts
+        n_gpu = counts.pop()
+        lo, hi = _rho_count_bounds(O, case, T, r.rho)
+        assert lo <= n_gpu <= hi, (n_gpu, lo, hi)
+        assert n_gpu > 0 and hi - lo <= max(8, 2e-4 * lo)   # the band holds a handful of pairs
+
+
 def test_eval_isotropic(env):
     """Remark 3: Sigma_ij = ell^2 I."""
     O, G, ctx, dev = env
