@@ -1,13 +1,18 @@
 #!/usr/bin/env python3
-"""G-CVO benchmark: pair-evals/s and registrations/s on LiDAR-like
-frame-to-frame tracking (64-beam scans of a procedural street, voxelised
-at 0.3 m, 100-frame trajectory, 1-2 m and <= 3 degrees between frames).
+"""G-CVO benchmark: pair-evals/s and registrations/s of batched
+multi-problem refinement (256 registration problems with clouds of 1k-40k
+points from the corner-scene and LiDAR-street generators, initial poses
+perturbed by up to 30 degrees and 0.5 m), against plain single-problem
+G-CVO at equal pose error.
 
-One step = the whole hot path over one batch: per-point covariances of
-every frame (Eq. 7b + eigenvalue bound), the voxel hash of every target
-frame, and Algorithm 1 (G-CVO-2) for all consecutive frame pairs from the
-identity in one batched call (transform, pair kernel, FP64 reduction,
-solve, update until ||xi||_1 < eps_tol).
+One step = the whole hot path over the batch in one library call
+(gcvo_register_clouds): per-point covariances of every target and source
+cloud (Eq. 7b + eigenvalue bound), the voxel hash of every target, and
+Algorithm 1 (G-CVO-2) for all problems in one batched registration
+(transform, pair kernel, FP64 reduction, solve, update until
+||xi||_1 < eps_tol).  Blocks beside the headline: the plain-vs-batched
+comparison, LiDAR frame-to-frame tracking (64-beam scans voxelised at
+0.3 m), G-CVO-1, G-CVO-E, the dense objective and the learned proposal.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gcvo|reference]
 
@@ -35,11 +40,11 @@ METRIC = "G-CVO kernel pair-evals/s & registrations/s at equal pose error vs pla
 UNIT = "pair-evals/s"
 FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
 FLOP_PER_PAIR_EXACT = 232   # the G-CVO-E pass: the 76 above plus y, Sigma'y, u, K and the S_yy, S_B sums
-# DRAM bytes per pair-eval of the pair kernel, from one ncu capture of the
-# kernel whose source hashes to PAIR_KERNEL_SHA (profiles/k_tile_lidar20.md);
-# the traffic is reported only while the kernel source still matches
-PAIR_DRAM_BYTES_PER_PAIR = 5.37
-PAIR_KERNEL_SHA = "7342bd38eaa7b5d7"
+# DRAM bytes per pair-eval of the pair kernel's evaluation pass on this
+# workload, measured by one ncu capture of the kernel whose source hashes to
+# PAIR_KERNEL_SHA; the traffic is reported only while the source still matches
+PAIR_DRAM_BYTES_PER_PAIR = None
+PAIR_KERNEL_SHA = None
 EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
 KNN = 10
 
@@ -51,10 +56,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcvo", choices=["gcvo", "reference"])
     ap.add_argument("--frames", type=int, default=100)
+    ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--k-max", type=int, default=200)
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem comparison")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal comparison")
+    ap.add_argument("--no-blocks", action="store_true",
+                    help="headline only: skip the tracking, G-CVO-1, G-CVO-E and dense blocks")
     return ap.parse_args()
 
 
@@ -153,8 +161,40 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def batch_problems(frames, T_true_frames, n_problems=256, n_min=1000, n_max=40000):
+    """The config-4 batch as host arrays: sizes log-uniform in [n_min, n_max];
+    even problems are corner scenes of that size (eigenvalue bound 0.01 m^2),
+    odd ones LiDAR frame pairs subsampled to it (at most a whole frame,
+    bound 0.09 m^2); every initial pose is the truth perturbed by up to 30
+    degrees and 0.5 m.  Returns a list of dicts (tx, tf, sx, sf as (n, 3) /
+    (n, 1) float32, T0, T_true, eig_max, kind)."""
+    from paper_2606_10019_gb300 import datagen as D
+    rng = np.random.default_rng(20260601 + 4000)
+    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_problems)).astype(int)
+    out = []
+    for k, n in enumerate(sizes):
+        if k % 2 == 0:
+            pair = D.make_corner_pair(frame=4000 + k, n_src=int(n), n_tgt=int(n))
+            tx, tf, sx, sf, Tt, eig, kind = pair.tgt_xyz, pair.tgt_feat, pair.src_xyz, pair.src_feat, pair.T_true, \
+                0.01, "corner"
+        else:
+            j = int(rng.integers(0, len(frames) - 1))
+            tx, tf = D.subsample(rng, frames[j][0], frames[j][1], int(n))
+            sx, sf = D.subsample(rng, frames[j + 1][0], frames[j + 1][1], int(n))
+            Tt, eig, kind = T_true_frames[j], EIG_MAX, "lidar"
+        T0 = D.perturb(rng, 30.0, 0.5) @ Tt
+        out.append(dict(tx=np.asarray(tx, np.float32), tf=np.asarray(tf, np.float32), sx=np.asarray(sx, np.float32),
+                        sf=np.asarray(sf, np.float32), T0=T0, T_true=Tt, eig_max=eig, kind=kind))
+    return out
+
+
+def _soa(a):
+    return np.ascontiguousarray(np.asarray(a, np.float32).T)
+
+
 def run_gcvo(args, rank, world):
     frames, T_true = make_frames(args.frames, rank)
+    batch = batch_problems(frames, T_true, n_problems=args.problems)
     import torch
     from paper_2606_10019_gb300 import build as B
     from paper_2606_10019_gb300 import gcvo as G
@@ -167,37 +207,26 @@ def run_gcvo(args, rank, world):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = G.gcvo_create(local, stream)
-    kp = G.kernel_params(eig_max=EIG_MAX, eig_ratio=100.0, knn=KNN)
+    kp_c = G.kernel_params(eig_max=0.01, eig_ratio=100.0, knn=KNN)
+    kp_l = G.kernel_params(eig_max=EIG_MAX, eig_ratio=100.0, knn=KNN)
     sp = G.solver_params(order=2, k_max=args.k_max, eps_tol=args.eps)
-    F = len(frames)
-    n_pts = [len(x) for x, _ in frames]
-    # inputs resident in HBM: SoA xyz (3, n) and intensity (1, n) per frame
-    xyz = [torch.from_numpy(np.ascontiguousarray(x.T)).to(dev) for x, _ in frames]
-    feat = [torch.from_numpy(np.ascontiguousarray(f.T)).to(dev) for _, f in frames]
-    cov = [torch.empty((6, n), dtype=torch.float32, device=dev) for n in n_pts]
-    grids = [None] * (F - 1)
+    n_prob = len(batch)
+    # inputs resident in HBM: SoA xyz (3, n) and intensity (1, n) per cloud
+    dclouds = [tuple(torch.from_numpy(_soa(q[key])).to(dev) for key in ("tx", "tf", "sx", "sf")) for q in batch]
+    kps = [kp_c if q["kind"] == "corner" else kp_l for q in batch]
+    dpairs = [(*c, q["T0"], kp) for c, q, kp in zip(dclouds, batch, kps)]
+    n_src_total = sum(q["sx"].shape[0] for q in batch)
+    n_tgt_total = sum(q["tx"].shape[0] for q in batch)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(xyz_in, feat_in, marks=None):
-        # marks: three CUDA events recorded after the covariances, the grids
-        # and the registration (phase times of the timed steps)
-        G.gcvo_estimate_covariances_batched(ctx, xyz_in, kp, cov)
-        if marks:
-            marks[0].record(stream)
-        grids[:] = G.gcvo_build_grids_batched(ctx, xyz_in[:-1], cov[:-1], feat_in[:-1], kp, grids)
-        if marks:
-            marks[1].record(stream)
-        probs = [(grids[k], xyz_in[k + 1], cov[k + 1], feat_in[k + 1], np.eye(4)) for k in range(F - 1)]
-        out = G.gcvo_register_batched(ctx, probs, sp, want_log=True)
-        if marks:
-            marks[2].record(stream)
-        return out
+    def step(pairs):
+        return G.gcvo_register_clouds(ctx, pairs, kp_l, sp, want_log=True)
 
     for _ in range(args.warmup):
-        out = step(xyz, feat)
+        out = step(dpairs)
     torch.cuda.synchronize(dev)
 
-    # ---- timed region: device-resident inputs
+    # ---- timed region: device-resident clouds
     G.gcvo_profile_enable(ctx, True)
     clocks = Clocks(torch.cuda.current_device())
     if world > 1:
@@ -209,11 +238,10 @@ def run_gcvo(args, rank, world):
     kept = 0
     regs = 0
     t_wall0 = time.perf_counter()
-    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     for s in range(args.steps):
         flush.zero_()                       # L2 flush, outside the events
         ev[s][0].record(stream)
-        T_est, logs, n_iter, status = step(xyz, feat, marks[s])
+        T_est, logs, n_iter, status = step(dpairs)
         ev[s][1].record(stream)
         pair_evals += sum(L["n_pairs"] for lg in logs for L in lg)
         kept += sum(L["n_kept"] for lg in logs for L in lg)
@@ -221,9 +249,6 @@ def run_gcvo(args, rank, world):
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
     schedule = G.gcvo_pair_schedule(ctx)     # the autotuner's choice for this workload
-    phases = {"covariances": float(np.mean([ev[s][0].elapsed_time(marks[s][0]) for s in range(args.steps)])),
-              "grids": float(np.mean([marks[s][0].elapsed_time(marks[s][1]) for s in range(args.steps)])),
-              "registration": float(np.mean([marks[s][1].elapsed_time(marks[s][2]) for s in range(args.steps)]))}
     clk = clocks.stop()
     prof = G.gcvo_profile_read(ctx)
     G.gcvo_profile_enable(ctx, False)
@@ -234,115 +259,103 @@ def run_gcvo(args, rank, world):
     regs_all, _ = R.combine(regs, t_dev, dev)
     t_dev = t_max
     value = pair_evals_all / t_dev
-    errs = pose_errors(list(T_est), T_true)
+    from paper_2606_10019_gb300 import proposal_data as PD
+    errs = PD.pose_errors(list(T_est), [q["T_true"] for q in batch])
+    ok = (errs[:, 0] < 2.0) & (errs[:, 1] < 0.05)
     n_conv = int(np.sum(status == 0))
     iters = n_iter.tolist()
     # the paper evaluates every pair: N_X * N_Z per problem and iteration
-    dense_pairs = float(sum(int(n_iter[k]) * n_pts[k] * n_pts[k + 1] for k in range(F - 1)))
+    dense_pairs = float(sum(int(n_iter[k]) * q["sx"].shape[0] * q["tx"].shape[0] for k, q in enumerate(batch)))
 
-    # ---- end to end: host (pinned) inputs copied in every step, poses read back
-    hx = [torch.from_numpy(np.ascontiguousarray(x.T)).pin_memory() for x, _ in frames]
-    hf = [torch.from_numpy(np.ascontiguousarray(f.T)).pin_memory() for _, f in frames]
-    h2d = sum(a.numel() * 4 for a in hx) + sum(a.numel() * 4 for a in hf)
-    d2h = (F - 1) * 16 * 8
+    # ---- end to end: the same call on pinned host clouds (copied in by the
+    # library every step), poses and iteration logs read back
+    hclouds = [tuple(torch.from_numpy(_soa(q[key])).pin_memory() for key in ("tx", "tf", "sx", "sf")) for q in batch]
+    hpairs = [(*c, q["T0"], kp) for c, q, kp in zip(hclouds, batch, kps)]
+    h2d = sum(a.numel() * 4 for c in hclouds for a in c)
+    d2h = n_prob * 16 * 8 + n_prob * args.k_max * 216 + n_prob * 8
+    step(hpairs)                             # staging buffers sized outside the timed loop
     e2e_pairs = 0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        dx = [a.to(dev, non_blocking=True) for a in hx]
-        df = [a.to(dev, non_blocking=True) for a in hf]
-        T_e, logs_e, _, _ = step(dx, df)
+        flush.zero_()
+        _, logs_e, _, _ = step(hpairs)
         e2e_pairs += sum(L["n_pairs"] for lg in logs_e for L in lg)
     torch.cuda.synchronize(dev)
     t_e2e = time.perf_counter() - t0
 
-    # ---- plain single-problem G-CVO on the same pairs (registration only)
-    plain = None
-    if not args.no_plain and rank == 0:
-        probs = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(F - 1)]
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        Tb, _, _, _ = G.gcvo_register_batched(ctx, probs, sp)
-        torch.cuda.synchronize(dev)
-        t_b = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        Ts = []
-        for p in probs:
-            T1, _, _, _ = G.gcvo_register(ctx, *p, sp, want_log=False)
-            Ts.append(T1)
-        torch.cuda.synchronize(dev)
-        t_s = time.perf_counter() - t0
-        plain = {"registrations_per_s_batched": (F - 1) / t_b, "registrations_per_s_plain": (F - 1) / t_s,
-                 "batched_over_plain": t_s / t_b,
-                 "max_pose_diff_batched_vs_plain": float(max(np.abs(np.array(Ts) - Tb).max(), 0.0))}
-
-    first = None
-    batched = None
-    exact = None
-    dense = None
-    if not args.no_plain and rank == 0:
-        fo = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(min(8, F - 1))]
-        first = first_order_block(G, ctx, dev, fo, T_true[:len(fo)])
-        batched = batched_block(G, ctx, dev, frames, T_true)
-        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_fp32 = sm_count * 128 * 2 * (clk or {}).get("sm_max_mhz", 2070.0) / 1e6
-        exact = exact_hessian_block(G, ctx, dev, probs, T_true, peak_fp32)
-        dense = dense_block(G, ctx, dev, xyz, cov, feat, T_true, peak_fp32)
-
-    # ---- roofline of the pair kernel
+    # ---- roofline of the pair kernel's evaluation pass over the batch
     n_launch = max(1, prof["n_pair_launches"])
     import hashlib
     src = os.path.join(ROOT, "paper_2606_10019_gb300", "csrc", "tile.cu")
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == PAIR_KERNEL_SHA
-    traffic = PAIR_DRAM_BYTES_PER_PAIR * pair_evals / n_launch if same_kernel else None
+    traffic = PAIR_DRAM_BYTES_PER_PAIR * pair_evals / n_launch if same_kernel and PAIR_DRAM_BYTES_PER_PAIR else None
     t_pair = prof["pair_kernel_ms"] / 1e3
     achieved = pair_evals * FLOP_PER_PAIR / t_pair / 1e12 if t_pair > 0 else 0.0
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_ghz = (clk or {}).get("sm_max_mhz", 2070.0) / 1e3
     peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_basis": "DRAM bytes per pair-eval from an ncu capture of k_tile on 20 "
-                "frames (5.37 B) x mean pair-evals per launch; null if the kernel changed since",
+                "traffic": traffic,
+                "traffic_basis": "DRAM bytes per pair-eval from an ncu capture of this pass on this workload x mean "
+                                 "pair-evals per launch; null if the kernel source changed since the capture",
                 "kernel": "k_tile (evaluation pass)", "launches": prof["n_pair_launches"],
                 "points_per_subtile": schedule,
                 "avg_launch_ms": prof["pair_kernel_ms"] / n_launch,
+                "pair_evals_per_launch": pair_evals / n_launch,
                 "pair_kernel_share_of_step": t_pair / t_dev if t_dev > 0 else None,
-                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz (max SM clock)"}
+                "frac_in_58_instruction_unit": achieved / FLOP_PER_PAIR * 58 / (peak / 2),
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {clock_ghz:.3f} GHz (max SM clock), "
+                              f"{FLOP_PER_PAIR} flops per pair-eval"}
 
+    plain = None
+    blocks = {}
+    if rank == 0 and not args.no_plain:
+        plain = plain_vs_batched(G, ctx, dev, dpairs, batch, kp_l, sp)
+    if rank == 0 and not args.no_blocks:
+        peak_fp32 = peak
+        blocks["lidar_tracking"] = lidar_tracking_block(G, ctx, dev, frames, T_true, args)
+        track = blocks["lidar_tracking"].pop("_problems")
+        fo = [p for p in track[:8]]
+        blocks["first_order"] = first_order_block(G, ctx, dev, fo, T_true[:len(fo)])
+        blocks["exact_hessian"] = exact_hessian_block(G, ctx, dev, track, T_true, peak_fp32)
+        blocks["dense_no_cutoff"] = dense_block(G, ctx, dev, *blocks["lidar_tracking"].pop("_clouds"), T_true,
+                                                peak_fp32)
+        blocks["lidar_tracking"].pop("_keep", None)
     proposal = None
     if not args.no_proposal and rank == 0:
         proposal = learned_proposal_block(G, ctx, dev)
 
     res = None
     if rank == 0:
-        cpu = cpu_baseline(frames, T_true)
+        cpu = cpu_baseline(batch)
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"lidar-64beam street tracking, {F} frames voxelised at 0.3 m "
-                                   f"(~{int(np.mean(n_pts))} points), {F - 1} frame pairs from the identity",
-                       "points_per_frame_mean": float(np.mean(n_pts)), "frame_pairs": F - 1,
-                       "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, "
-                                 f"eig clamp [{EIG_MAX / 100}, {EIG_MAX}]",
-                       "precision": "FP32 pair kernel, compensated FP32 group partials, FP64 reduction/solve/exp",
+            "config": {"workload": f"batched multi-problem refinement: {n_prob} problems, cloud sizes log-uniform in "
+                                   f"[1000, 40000] points (corner scenes and voxelised LiDAR frame pairs subsampled), "
+                                   "initial poses perturbed up to 30 deg / 0.5 m; covariances, grids and G-CVO-2 "
+                                   "in one gcvo_register_clouds call",
+                       "problems": n_prob, "source_points": n_src_total, "target_points": n_tgt_total,
+                       "lidar_points_per_frame_mean": float(np.mean([len(x) for x, _ in frames])),
+                       "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, eig clamp "
+                                 f"[eig_max/100, eig_max], eig_max 0.01 (corner) / {EIG_MAX} (LiDAR)",
+                       "precision": "FP32 pair kernel, compensated FP32 partials, FP64 reduction/solve/exp",
                        "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
                        "parallelism": f"{world} independent replica(s), no collective"},
             "registrations_per_s": regs_all / t_dev,
-            "phase_ms_per_step": phases,
             "pair_evals_per_step": pair_evals / args.steps, "kept_pairs_per_step": kept / args.steps,
             "dense_equivalent_pairs_per_s": dense_pairs * args.steps / t_dev,
             "iterations_mean": float(np.mean(iters)), "converged": f"{n_conv}/{len(iters)}",
-            "pose_error_vs_truth": errs,
+            "success": float(ok.mean()), "success_criterion": "rotation < 2 deg and translation < 5 cm vs truth",
             "roofline": roofline,
-            "e2e": {"value": e2e_pairs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_pairs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "gcvo_register_clouds with pinned host clouds"},
             "gpu_launches": prof["n_launches"],
             "clocks": clk,
             "plain_vs_batched": plain,
-            "first_order": first,
-            "batched_uneven": batched,
-            "exact_hessian": exact,
-            "dense_no_cutoff": dense,
+            **blocks,
             "learned_proposal": proposal,
             "cpu_baseline": cpu,
             "wall_s_timed": t_wall,
@@ -354,6 +367,115 @@ def run_gcvo(args, rank, world):
         dist.destroy_process_group()
     ctx.close()
     return res
+
+
+def plain_vs_batched(G, ctx, dev, dpairs, batch, kp, sp):
+    """Registrations/s of the batch's registration (after covariances and
+    grids) in one batched launch sequence against one gcvo_register call per
+    problem, same problems, same solver, and the pose errors of both."""
+    import torch
+    from paper_2606_10019_gb300 import proposal_data as PD
+    T_b, _, it_b, st_b = G.gcvo_register_clouds(ctx, dpairs, kp, sp)     # also leaves the grids and covariances
+    grids, covs = [], []
+    for k, pr in enumerate(dpairs):
+        kk = pr[5]
+        tc = torch.empty((6, pr[0].shape[1]), device=dev)
+        sc = torch.empty((6, pr[2].shape[1]), device=dev)
+        G.gcvo_estimate_covariances(ctx, pr[0], kk, tc)
+        G.gcvo_estimate_covariances(ctx, pr[2], kk, sc)
+        grids.append(G.gcvo_build_grid(ctx, pr[0], tc, pr[1], kk))
+        covs.append((tc, sc))
+    probs = [(g, pr[2], c[1], pr[3], pr[4]) for g, pr, c in zip(grids, dpairs, covs)]
+    G.gcvo_register_batched(ctx, probs[:8], sp)      # warm-up of the batched path
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Tb, _, it_b, _ = G.gcvo_register_batched(ctx, probs, sp)
+    torch.cuda.synchronize(dev)
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ts, it_s = [], []
+    for p in probs:
+        T1, _, n1, _ = G.gcvo_register(ctx, *p, sp, want_log=False)
+        Ts.append(T1)
+        it_s.append(n1)
+    torch.cuda.synchronize(dev)
+    t_s = time.perf_counter() - t0
+    truth = [q["T_true"] for q in batch]
+    e_b = PD.pose_errors(list(Tb), truth)
+    e_s = PD.pose_errors(Ts, truth)
+    ok_b = (e_b[:, 0] < 2.0) & (e_b[:, 1] < 0.05)
+    ok_s = (e_s[:, 0] < 2.0) & (e_s[:, 1] < 0.05)
+    for g in grids:
+        g.close()
+    return {"workload": "the headline batch, registration only (covariances and grids computed beforehand)",
+            "registrations_per_s_batched": len(probs) / t_b, "registrations_per_s_plain": len(probs) / t_s,
+            "batched_over_plain": t_s / t_b,
+            "iterations_mean": float(np.mean(it_b)), "iterations_mean_plain": float(np.mean(it_s)),
+            "success_batched": float(ok_b.mean()), "success_plain": float(ok_s.mean()),
+            "rot_deg_median_batched": float(np.median(e_b[:, 0])), "rot_deg_median_plain": float(np.median(e_s[:, 0])),
+            "max_pose_entry_diff_batched_vs_plain": float(np.abs(np.array(Ts) - Tb).max()),
+            "success_criterion": "rotation < 2 deg and translation < 5 cm vs ground truth"}
+
+
+def lidar_tracking_block(G, ctx, dev, frames, T_true, args, steps=3):
+    """LiDAR frame-to-frame tracking (the config-2 workload): covariances of
+    every frame, the grid of every target frame and batched G-CVO-2 over the
+    consecutive frame pairs from the identity; pair-evals/s, registrations/s,
+    phase times and pose errors."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    kp = G.kernel_params(eig_max=EIG_MAX, eig_ratio=100.0, knn=KNN)
+    sp = G.solver_params(order=2, k_max=args.k_max, eps_tol=args.eps)
+    F = len(frames)
+    n_pts = [len(x) for x, _ in frames]
+    xyz = [torch.from_numpy(_soa(x)).to(dev) for x, _ in frames]
+    feat = [torch.from_numpy(_soa(f)).to(dev) for _, f in frames]
+    cov = [torch.empty((6, n), dtype=torch.float32, device=dev) for n in n_pts]
+    grids = [None] * (F - 1)
+
+    def step(marks=None):
+        G.gcvo_estimate_covariances_batched(ctx, xyz, kp, cov)
+        if marks:
+            marks[0].record(stream)
+        grids[:] = G.gcvo_build_grids_batched(ctx, xyz[:-1], cov[:-1], feat[:-1], kp, grids)
+        if marks:
+            marks[1].record(stream)
+        probs = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(F - 1)]
+        out = G.gcvo_register_batched(ctx, probs, sp, want_log=True)
+        if marks:
+            marks[2].record(stream)
+        return out
+
+    step()
+    G.gcvo_profile_enable(ctx, True)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), [torch.cuda.Event(enable_timing=True) for _ in range(3)])
+          for _ in range(steps)]
+    pe = 0
+    for s in range(steps):
+        ev[s][0].record(stream)
+        T_est, logs, n_iter, status = step(ev[s][1])
+        pe += sum(L["n_pairs"] for lg in logs for L in lg)
+    torch.cuda.synchronize(dev)
+    prof = G.gcvo_profile_read(ctx)
+    G.gcvo_profile_enable(ctx, False)
+    t = sum(a.elapsed_time(m[2]) for a, m in ev) / 1e3
+    phases = {"covariances": float(np.mean([a.elapsed_time(m[0]) for a, m in ev])),
+              "grids": float(np.mean([m[0].elapsed_time(m[1]) for a, m in ev])),
+              "registration": float(np.mean([m[1].elapsed_time(m[2]) for a, m in ev]))}
+    probs = [(grids[k], xyz[k + 1], cov[k + 1], feat[k + 1], np.eye(4)) for k in range(F - 1)]
+    t_pair = prof["pair_kernel_ms"] / 1e3
+    return {"workload": f"{F} LiDAR frames (64 beams, 0.3 m voxels), {F - 1} consecutive pairs from the identity",
+            "points_per_frame_mean": float(np.mean(n_pts)),
+            "pair_evals_per_s": pe / t, "registrations_per_s": (F - 1) * steps / t,
+            "ms_per_step": t * 1e3 / steps, "phase_ms_per_step": phases,
+            "pair_kernel_ms_per_launch": prof["pair_kernel_ms"] / max(1, prof["n_pair_launches"]),
+            "pair_kernel_frac_of_fp32_peak": (pe * FLOP_PER_PAIR / t_pair / 1e12) / (
+                torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * 2.07 / 1e3)
+            if t_pair > 0 else None,
+            "iterations_mean": float(np.mean(n_iter)), "converged": f"{int(np.sum(status == 0))}/{F - 1}",
+            "pose_error_vs_truth": pose_errors(list(T_est), T_true),
+            "_problems": probs, "_clouds": (xyz, cov, feat), "_keep": grids}
 
 
 # ---------------------------------------------------------------------------
@@ -523,75 +645,6 @@ def dense_block(G, ctx, dev, xyz, cov, feat, T_true, peak_tflops, reps=5):
 
 
 # ---------------------------------------------------------------------------
-# Batched registration of problems of uneven size vs one call per problem
-# ---------------------------------------------------------------------------
-
-def batched_block(G, ctx, dev, frames, T_true_frames, n_problems=256, n_min=1000, n_max=40000):
-    """Config-4-style batch: sizes log-uniform in [n_min, n_max]; even
-    problems are corner scenes of that size, odd ones LiDAR frame pairs
-    subsampled to it (at most a whole frame); every initial pose is the truth
-    perturbed by up to 30 degrees and 0.5 m.  One gcvo_register_batched call
-    against one gcvo_register call per problem, same problems, same solver."""
-    import torch
-    from paper_2606_10019_gb300 import datagen as D
-    from paper_2606_10019_gb300 import proposal_data as PD
-    rng = np.random.default_rng(20260601 + 4000)
-    sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_problems)).astype(int)
-    kp_c = G.kernel_params(eig_max=0.01, eig_ratio=100.0, knn=KNN)
-    kp_l = G.kernel_params(eig_max=EIG_MAX, eig_ratio=100.0, knn=KNN)
-    probs, keep, truth = [], [], []
-    n_src_total = 0
-    for k, n in enumerate(sizes):
-        if k % 2 == 0:
-            pair = D.make_corner_pair(frame=4000 + k, n_src=int(n), n_tgt=int(n))
-            tx, tf, sx, sf, Tt, kp = pair.tgt_xyz, pair.tgt_feat, pair.src_xyz, pair.src_feat, pair.T_true, kp_c
-        else:
-            j = int(rng.integers(0, len(frames) - 1))
-            tx, tf = D.subsample(rng, frames[j][0], frames[j][1], int(n))
-            sx, sf = D.subsample(rng, frames[j + 1][0], frames[j + 1][1], int(n))
-            Tt, kp = T_true_frames[j], kp_l
-        T0 = D.perturb(rng, 30.0, 0.5) @ Tt
-        t = [torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32).T)).to(dev) for a in (tx, tf, sx, sf)]
-        tc = torch.empty((6, t[0].shape[1]), device=dev)
-        sc = torch.empty((6, t[2].shape[1]), device=dev)
-        G.gcvo_estimate_covariances(ctx, t[0], kp, tc)
-        G.gcvo_estimate_covariances(ctx, t[2], kp, sc)
-        g = G.gcvo_build_grid(ctx, t[0], tc, t[1], kp)
-        probs.append((g, t[2], sc, t[3], T0))
-        keep.append((t, tc, sc, g))
-        truth.append(Tt)
-        n_src_total += t[2].shape[1]
-    sp = G.solver_params(order=2, k_max=200, eps_tol=1e-6)
-    G.gcvo_register_batched(ctx, probs[:8], sp)      # warm-up of the batched path
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    Tb, _, it_b, _ = G.gcvo_register_batched(ctx, probs, sp)
-    torch.cuda.synchronize(dev)
-    t_b = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    Ts, it_s = [], []
-    for p in probs:
-        T1, _, n1, _ = G.gcvo_register(ctx, *p, sp, want_log=False)
-        Ts.append(T1)
-        it_s.append(n1)
-    torch.cuda.synchronize(dev)
-    t_s = time.perf_counter() - t0
-    e_b = PD.pose_errors(list(Tb), truth)
-    e_s = PD.pose_errors(Ts, truth)
-    ok_b = (e_b[:, 0] < 2.0) & (e_b[:, 1] < 0.05)
-    ok_s = (e_s[:, 0] < 2.0) & (e_s[:, 1] < 0.05)
-    return {"workload": f"{n_problems} problems, sizes log-uniform in [{n_min}, {n_max}] (corner scenes and LiDAR "
-                        f"frame pairs subsampled to at most a whole frame), {n_src_total} source points in total, "
-                        "initial poses perturbed up to 30 deg / 0.5 m",
-            "registrations_per_s_batched": n_problems / t_b, "registrations_per_s_plain": n_problems / t_s,
-            "batched_over_plain": t_s / t_b,
-            "iterations_mean": float(np.mean(it_b)), "iterations_mean_plain": float(np.mean(it_s)),
-            "success_batched": float(ok_b.mean()), "success_plain": float(ok_s.mean()),
-            "max_pose_entry_diff_batched_vs_plain": float(np.abs(np.array(Ts) - Tb).max()),
-            "success_criterion": "rotation < 2 deg and translation < 5 cm vs ground truth"}
-
-
-# ---------------------------------------------------------------------------
 # Learned proposal + batched G-CVO vs plain single-problem G-CVO
 # ---------------------------------------------------------------------------
 
@@ -653,65 +706,81 @@ def learned_proposal_block(G, ctx, dev, n_train=1024, steps=1500, n_eval=256):
 # CPU oracle: bounded sample of the same workload
 # ---------------------------------------------------------------------------
 
-def oracle_sample(frames, k=0):
-    """Covariances of one frame pair and one evaluation of f, g, H at the
-    identity, by the FP64 brute-force oracle.  Returns (pair-evals, seconds)."""
+def oracle_problem(q):
+    """One problem of the batch through the FP64 brute-force oracle: kNN
+    covariances of both clouds and one all-pairs evaluation of f, g, H at
+    the initial pose, counting the pairs within the same rho the kernel
+    uses (rho^2 = 9 (lambda_max,X + lambda_max,Z)(1 + 2e-4), from the
+    oracle's own covariances).  Returns (pair-evals, seconds)."""
     from oracle import oracle as O
-    O.build()
     t0 = time.perf_counter()
-    (xt, ft), (xs, fs) = frames[k], frames[k + 1]
-    tc = O.covariances(xt, KNN, EIG_MAX, 100.0)
-    sc = O.covariances(xs, KNN, EIG_MAX, 100.0)
-    prob = O.Problem.make(xt, tc, ft, xs, sc, fs)
-    rho = 3.0 * math.sqrt(2.0 * EIG_MAX)
-    r = O.evaluate(prob, np.eye(4), O.KernelParams(cutoff=3.0, rho=rho))
+    tc = O.covariances(q["tx"], KNN, q["eig_max"], 100.0)
+    sc = O.covariances(q["sx"], KNN, q["eig_max"], 100.0)
+    rho = 3.0 * math.sqrt((O.max_eig(tc) + O.max_eig(sc)) * (1.0 + 2e-4))
+    prob = O.Problem.make(q["tx"], tc, q["tf"], q["sx"], sc, q["sf"])
+    r = O.evaluate(prob, q["T0"], O.KernelParams(cutoff=3.0, rho=rho))
     return r.n_rho, time.perf_counter() - t0
 
 
-def cpu_baseline(frames, T_true, min_seconds=10.0):
-    """The oracle on consecutive frame pairs until at least min_seconds of
+def oracle_sample_problems(batch, n_max=8000):
+    """The bounded sample the oracle is timed on: the batch's problems with
+    at most n_max points per cloud, in batch order."""
+    return [q for q in batch if max(len(q["tx"]), len(q["sx"])) <= n_max]
+
+
+def cpu_baseline(batch, min_seconds=10.0):
+    """The oracle on problems of the batch until at least min_seconds of
     host time have been spent (a bounded sample of the workload)."""
     from oracle import oracle as O
     O.build()
     tot_n, tot_t, k = 0, 0.0, 0
-    while tot_t < min_seconds and k + 1 < len(frames):
-        n, t = oracle_sample(frames, k)
+    sample = oracle_sample_problems(batch)
+    while tot_t < min_seconds and k < len(sample):
+        n, t = oracle_problem(sample[k])
         tot_n += n
         tot_t += t
         k += 1
     return {"value": tot_n / tot_t, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{k} frame pair(s): brute-force kNN covariances of both clouds and one all-pairs FP64 "
-                      "evaluation of f, g, H at the identity each (pairs within rho counted)",
+            "sample": f"{k} problem(s) of the batch with at most 8000 points per cloud, in batch order: "
+                      "brute-force kNN covariances of both clouds and one all-pairs FP64 evaluation of f, g, H at "
+                      "the initial pose each (pairs within the kernel's rho counted)",
             "seconds": tot_t}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    frames, T_true = make_frames(3, 0)
+    frames, T_true = make_frames(min(args.frames, 100), 0)
+    batch = batch_problems(frames, T_true, n_problems=args.problems)
+    sample = oracle_sample_problems(batch)
     from oracle import oracle as O
     O.build()
+    per_step = 3
 
-    def sample():
-        n0, t0 = oracle_sample(frames, 0)
-        n1, t1 = oracle_sample(frames, 1)
-        return n0 + n1, t0 + t1
+    def one(s):
+        n, t = 0, 0.0
+        for j in range(per_step):
+            a, b = oracle_problem(sample[(s * per_step + j) % len(sample)])
+            n += a
+            t += b
+        return n, t
 
-    for _ in range(args.warmup):
-        sample()
+    for w in range(args.warmup):
+        one(w)
     tot_n, tot_t = 0.0, 0.0
-    for _ in range(args.steps):
-        n, t = sample()
+    for s in range(args.steps):
+        n, t = one(args.warmup + s)
         tot_n += n
         tot_t += t
     v = tot_n / tot_t
     res = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "lidar-64beam street tracking, voxelised at 0.3 m; two frame pairs per step"},
+           "config": {"workload": f"batched multi-problem refinement: {len(batch)} problems, cloud sizes log-uniform "
+                                  "in [1000, 40000] points; each step a bounded sample of three problems"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                            "sample": "per step: two frame pairs, kNN covariances of both clouds and one all-pairs FP64 "
-                                      "evaluation each"},
+                            "sample": f"per step: {per_step} problems of the batch with at most 8000 points per "
+                                      "cloud, kNN covariances of both clouds and one all-pairs FP64 evaluation each"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
     return res

@@ -256,6 +256,35 @@ gcvo_status gcvo_register_batched(gcvo_ctx *ctx, int n_problems, const gcvo_prob
                                   const gcvo_solver_params *params, double *T_out, gcvo_iter_log *logs,
                                   int *n_iter, int *status);
 
+/* One registration problem given as raw clouds, for gcvo_register_clouds. */
+typedef struct {
+    const float *tgt_xyz;   /* 3 x n_tgt: the target cloud X */
+    const float *tgt_feat;  /* feat_dim x n_tgt */
+    int64_t n_tgt;
+    const float *src_xyz;   /* 3 x n_src: the source cloud Z */
+    const float *src_feat;  /* feat_dim x n_src */
+    int64_t n_src;
+    double T0[16];          /* initial pose T^(0) */
+    const gcvo_kernel_params *params; /* this pair's kernel parameters, or NULL
+                                         for the call's; kernel_mode and
+                                         feat_dim must equal the call's */
+} gcvo_cloud_pair;
+
+/* The whole hot path from raw clouds: the per-point covariances of Eq.
+ * (7b) with the eigenvalue bound for every target and source cloud, the
+ * voxel grid of every target, and Algorithm 1 for all pairs in one batched
+ * registration (as gcvo_register_batched).  Clouds may be host or device
+ * arrays; host arrays are copied in, one copy per array, on the context's
+ * stream.  The covariances and grids live in buffers the context keeps
+ * and reuses on the next call.  Outputs as gcvo_register_batched: T_out
+ * n_pairs x 16 (host), logs n_pairs x k_max rows (host, may be NULL),
+ * n_iter and status n_pairs (host, may be NULL).  Covariances and grids
+ * of different clouds are computed concurrently on the context's internal
+ * streams.  Synchronises the stream. */
+gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pair *pairs,
+                                 const gcvo_kernel_params *params, const gcvo_solver_params *solver, double *T_out,
+                                 gcvo_iter_log *logs, int *n_iter, int *status);
+
 /* The evaluation of gcvo_eval (f, g and H = -M + Gamma at pose T) for
  * callers that must not allocate device memory: an application whose memory
  * pool owns every device byte (a stray cudaMalloc would fail or fragment

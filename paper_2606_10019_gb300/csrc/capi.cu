@@ -732,6 +732,10 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
+    ctx->clouds_stage.release();
+    ctx->clouds_cov.release();
+    for (gcvo_grid *g : ctx->clouds_grids)
+        if (g) gcvo_grid_destroy(g);
     for (gcvo_ctx *c : ctx->lanes) gcvo_destroy(c);
     for (cudaStream_t ls : ctx->lane_streams) cudaStreamDestroy(ls);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -988,6 +992,74 @@ gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *c
         if (grids[k]) return gcvo_rebuild_grid(c, grids[k], xyz[k], ck, feat[k], n[k], params);
         return gcvo_build_grid(c, xyz[k], ck, feat[k], n[k], params, &grids[k]);
     });
+}
+
+gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pair *pairs,
+                                 const gcvo_kernel_params *params, const gcvo_solver_params *solver, double *T_out,
+                                 gcvo_iter_log *logs, int *n_iter, int *status) {
+    if (!ctx || n_pairs < 1 || n_pairs > GCVO_MAX_PROBLEMS || !pairs || !params || !solver || !T_out)
+        return GCVO_ERR_INVALID_ARG;
+    std::vector<const gcvo_kernel_params *> kp(n_pairs);
+    for (int k = 0; k < n_pairs; ++k) {
+        const gcvo_cloud_pair &q = pairs[k];
+        kp[k] = q.params ? q.params : params;
+        if (!valid_kernel_params(kp[k]) || kp[k]->kernel_mode != params->kernel_mode ||
+            kp[k]->feat_dim != params->feat_dim)
+            return GCVO_ERR_INVALID_ARG;
+        if (!q.tgt_xyz || !q.tgt_feat || !q.src_xyz || !q.src_feat) return GCVO_ERR_INVALID_ARG;
+        if (q.n_tgt < kp[k]->knn || q.n_src < kp[k]->knn || q.n_tgt > (1 << 28) || q.n_src > (1 << 28))
+            return GCVO_ERR_INVALID_ARG;
+        if (kp[k]->knn < 2 || kp[k]->knn > GCVO_MAX_KNN) return GCVO_ERR_INVALID_ARG;
+    }
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const int fd = params->feat_dim;
+    // cloud c = 2k (target of pair k) or 2k + 1 (its source)
+    const int nc = 2 * n_pairs;
+    std::vector<const float *> hx(nc), hf(nc), dx(nc), df(nc);
+    std::vector<int64_t> n(nc);
+    std::vector<size_t> cov_off(nc);
+    size_t stage_floats = 0, cov_floats = 0;
+    for (int c = 0; c < nc; ++c) {
+        const gcvo_cloud_pair &q = pairs[c / 2];
+        hx[c] = c % 2 ? q.src_xyz : q.tgt_xyz;
+        hf[c] = c % 2 ? q.src_feat : q.tgt_feat;
+        n[c] = c % 2 ? q.n_src : q.n_tgt;
+        stage_floats += staged_floats(hx[c], 3 * (size_t)n[c]) + staged_floats(hf[c], (size_t)fd * n[c]);
+        cov_off[c] = cov_floats;
+        cov_floats += (6 * (size_t)n[c] + 63) & ~size_t(63);
+    }
+    // host clouds are copied in, one copy per array, in stream order
+    if (stage_floats) GCVO_TRY(ctx->clouds_stage.ensure(stage_floats * sizeof(float), s));
+    GCVO_TRY(ctx->clouds_cov.ensure(cov_floats * sizeof(float), s));
+    size_t off = 0;
+    for (int c = 0; c < nc; ++c) {
+        GCVO_TRY(stage(ctx, hx[c], 3 * (size_t)n[c], ctx->clouds_stage, off, &dx[c]));
+        GCVO_TRY(stage(ctx, hf[c], (size_t)fd * n[c], ctx->clouds_stage, off, &df[c]));
+    }
+    float *cov = ctx->clouds_cov.as<float>();
+    // Eq. (7b) and the eigenvalue bound for every cloud, concurrently
+    GCVO_TRY(run_lanes(ctx, nc, [&](gcvo_ctx *c, int k) {
+        return gcvo_estimate_covariances(c, dx[k], n[k], kp[k / 2], cov + cov_off[k]);
+    }));
+    // the target grids, kept by the context and rebuilt in place next call
+    if ((int)ctx->clouds_grids.size() < n_pairs) ctx->clouds_grids.resize(n_pairs, nullptr);
+    GCVO_TRY(run_lanes(ctx, n_pairs, [&](gcvo_ctx *c, int k) {
+        const float *ck = kp[k]->kernel_mode == 0 ? cov + cov_off[2 * k] : nullptr;
+        gcvo_grid *&g = ctx->clouds_grids[k];
+        if (g) return gcvo_rebuild_grid(c, g, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k]);
+        return gcvo_build_grid(c, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k], &g);
+    }));
+    std::vector<gcvo_problem> pr(n_pairs);
+    for (int k = 0; k < n_pairs; ++k) {
+        pr[k].target = ctx->clouds_grids[k];
+        pr[k].src_xyz = dx[2 * k + 1];
+        pr[k].src_cov = cov + cov_off[2 * k + 1];
+        pr[k].src_feat = df[2 * k + 1];
+        pr[k].n_src = n[2 * k + 1];
+        memcpy(pr[k].T0, pairs[k].T0, sizeof(pr[k].T0));
+    }
+    return run_register(ctx, n_pairs, pr.data(), solver, T_out, logs, n_iter, status);
 }
 
 }  // extern "C"

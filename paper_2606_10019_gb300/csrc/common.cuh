@@ -192,6 +192,9 @@ struct gcvo_ctx {
     gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, items, item_prob, pack_tmp;
     gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
+    // gcvo_register_clouds: staged host clouds, covariances and target grids
+    gcvo::DevBuf clouds_stage, clouds_cov;
+    std::vector<gcvo_grid *> clouds_grids;
     gcvo::DevBuf knn_retry;
     void *host_pinned = nullptr;
     size_t host_pinned_bytes = 0;

@@ -152,19 +152,25 @@ class Street:
 
 
 def make_street(rng, x_min: float = -120.0, x_max: float = 420.0) -> Street:
+    """A wide boulevard: two rows of box buildings on each side, set back
+    35-50 m and 55-78 m with gaps between them (walls at tens of metres
+    give the upper beams returns that fall in separate 0.3 m voxels, so a
+    frame keeps about 23k voxel centroids), parked cars along both kerbs,
+    poles along the road and a park of porous tree crowns 20-60 m out."""
     lo, hi, it = [], [], []
     for side in (-1.0, 1.0):
-        x = x_min
-        while x < x_max:
-            L = rng.uniform(5.0, 20.0)
-            D = rng.uniform(5.0, 20.0)
-            H = rng.uniform(5.0, 20.0)
-            off = rng.uniform(8.0, 15.0)
-            y0, y1 = (off, off + D) if side > 0 else (-off - D, -off)
-            lo.append([x, y0, 0.0])
-            hi.append([x + L, y1, H])
-            it.append(rng.uniform(0.2, 0.8))
-            x += L + rng.uniform(1.0, 6.0)
+        for (a, b) in ((35.0, 50.0), (55.0, 78.0)):
+            x = x_min + rng.uniform(0.0, 10.0)
+            while x < x_max:
+                L = rng.uniform(6.0, 18.0)
+                D = rng.uniform(6.0, 14.0)
+                H = rng.uniform(10.0, 30.0)
+                off = rng.uniform(a, b)
+                y0, y1 = (off, off + D) if side > 0 else (-off - D, -off)
+                lo.append([x, y0, 0.0])
+                hi.append([x + L, y1, H])
+                it.append(rng.uniform(0.2, 0.8))
+                x += L + rng.uniform(2.0, 8.0)
     # parked cars along both kerbs
     for side in (-1.0, 1.0):
         x = x_min
@@ -182,16 +188,16 @@ def make_street(rng, x_min: float = -120.0, x_max: float = 420.0) -> Street:
         while x < x_max:
             poles.append([x, side * rng.uniform(6.0, 7.5)])
             x += rng.uniform(4.0, 10.0)
-    # trees: a trunk (a pole) and a porous spherical crown
+    # park trees: a trunk (a pole) and a porous spherical crown
     crowns = []
     for side in (-1.0, 1.0):
         x = x_min + rng.uniform(0.0, 8.0)
         while x < x_max:
-            y = side * rng.uniform(5.5, 7.5)
-            r = rng.uniform(1.5, 3.0)
+            y = side * rng.uniform(20.0, 60.0)
+            r = rng.uniform(2.0, 4.0)
             crowns.append([x, y, rng.uniform(2.0, 3.5) + 0.3 * r, r])
             poles.append([x, y])
-            x += rng.uniform(3.0, 8.0)
+            x += rng.uniform(2.0, 5.0)
     return Street(np.array(lo), np.array(hi), np.array(it), np.array(poles), np.array(crowns))
 
 

@@ -58,6 +58,12 @@ class gcvo_problem(ctypes.Structure):
                 ("src_feat", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("T0", ctypes.c_double * 16)]
 
 
+class gcvo_cloud_pair(ctypes.Structure):
+    _fields_ = [("tgt_xyz", ctypes.c_void_p), ("tgt_feat", ctypes.c_void_p), ("n_tgt", ctypes.c_int64),
+                ("src_xyz", ctypes.c_void_p), ("src_feat", ctypes.c_void_p), ("n_src", ctypes.c_int64),
+                ("T0", ctypes.c_double * 16), ("params", ctypes.c_void_p)]
+
+
 class gcvo_profile(ctypes.Structure):
     _fields_ = [("n_launches", ctypes.c_int64), ("n_pair_launches", ctypes.c_int64),
                 ("pair_kernel_ms", ctypes.c_double)]
@@ -100,6 +106,7 @@ def lib() -> ctypes.CDLL:
         L.gcvo_eval_exact.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
         L.gcvo_register.argtypes = [P, P, P, P, P, I64, P, P, P, P, P]
         L.gcvo_register_batched.argtypes = [P, I, P, P, P, P, P, P]
+        L.gcvo_register_clouds.argtypes = [P, I, P, P, P, P, P, P, P]
         L.gcvo_estimate_covariances_batched.argtypes = [P, I, P, P, P, P]
         L.gcvo_build_grids_batched.argtypes = [P, I, P, P, P, P, P, P]
         L.gcvo_pair_schedule.argtypes = [P, I, P]
@@ -385,6 +392,37 @@ def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solv
     out_logs = None
     if logs is not None:
         out_logs = [_logs_to_list(logs[k * params.k_max:(k + 1) * params.k_max], int(n_iter[k])) for k in range(n)]
+    return T.reshape(n, 4, 4), out_logs, n_iter, status
+
+
+def gcvo_register_clouds(ctx: Context, pairs: list[tuple], params: gcvo_kernel_params, solver: gcvo_solver_params,
+                         want_log: bool = False):
+    """The whole hot path from raw clouds in one call.  pairs: list of
+    (tgt_xyz, tgt_feat, src_xyz, src_feat, T0) or (..., T0, kernel_params);
+    arrays on the device or on the host (host arrays are copied in by the
+    library).  Returns (T (n, 4, 4), logs or None, n_iter (n,), status (n,))."""
+    n = len(pairs)
+    arr = (gcvo_cloud_pair * n)()
+    keep = []
+    for k, pr in enumerate(pairs):
+        tx, tf, sx, sf, T0 = pr[:5]
+        arr[k].tgt_xyz, arr[k].tgt_feat, arr[k].n_tgt = _ptr(tx), _ptr(tf), _n(tx)
+        arr[k].src_xyz, arr[k].src_feat, arr[k].n_src = _ptr(sx), _ptr(sf), _n(sx)
+        arr[k].T0[:] = list(_pose(T0).ravel())
+        if len(pr) > 5 and pr[5] is not None:
+            keep.append(pr[5])
+            arr[k].params = ctypes.cast(ctypes.byref(pr[5]), ctypes.c_void_p)
+    T = np.zeros((n, 16))
+    n_iter = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    logs = (gcvo_iter_log * (n * solver.k_max))() if want_log else None
+    _check(lib().gcvo_register_clouds(ctx.handle, n, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(params),
+                                      ctypes.byref(solver), T.ctypes.data,
+                                      ctypes.cast(logs, ctypes.c_void_p) if logs is not None else None,
+                                      n_iter.ctypes.data, status.ctypes.data), "gcvo_register_clouds")
+    out_logs = None
+    if logs is not None:
+        out_logs = [_logs_to_list(logs[k * solver.k_max:(k + 1) * solver.k_max], int(n_iter[k])) for k in range(n)]
     return T.reshape(n, 4, 4), out_logs, n_iter, status
 
 

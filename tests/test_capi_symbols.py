@@ -58,6 +58,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work(libpath):
                              None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_register(None, None, None, None, None, 0, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_register_batched(None, 0, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_register_clouds(None, 1, None, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_estimate_covariances_batched(None, 1, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_build_grids_batched(None, 1, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_pair_schedule(None, 8, None) == G.GCVO_ERR_INVALID_ARG
