@@ -345,6 +345,15 @@ def run_gcvo(args, rank, world):
                        "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
                        "parallelism": f"{world} independent replica(s), no collective"},
             "registrations_per_s": regs_all / t_dev,
+            "phase_ms_per_step": {
+                "covariances": prof["clouds_covariance_ms"] / args.steps,
+                "grids": prof["clouds_grid_ms"] / args.steps,
+                "registration": t_dev * 1e3 / args.steps - (prof["clouds_covariance_ms"] + prof["clouds_grid_ms"])
+                / args.steps,
+                "of_which_pair_kernel": prof["pair_kernel_ms"] / args.steps,
+                "of_which_finalize": prof["finalize_ms"] / args.steps,
+                "of_which_transform": prof["transform_ms"] / args.steps,
+                "basis": "CUDA events on the context's stream (library profiling counters)"},
             "pair_evals_per_step": pair_evals / args.steps, "kept_pairs_per_step": kept / args.steps,
             "dense_equivalent_pairs_per_s": dense_pairs * args.steps / t_dev,
             "iterations_mean": float(np.mean(iters)), "converged": f"{n_conv}/{len(iters)}",

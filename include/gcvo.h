@@ -153,6 +153,34 @@ gcvo_status gcvo_create(gcvo_ctx **ctx, int device, void *cuda_stream);
 /* Release the context and its device memory (synchronises its stream). */
 gcvo_status gcvo_destroy(gcvo_ctx *ctx);
 
+/* Caller-owned scratch.  By default a context allocates its scratch with
+ * cudaMalloc as calls need it and keeps it until gcvo_destroy.  A caller
+ * that owns the device memory (a framework's allocator, a fixed budget)
+ * can instead hand the context one workspace: gcvo_workspace_size gives
+ * the bytes needed for calls of at most max_points points (the source
+ * points of an evaluation or a registration, all problems together, or
+ * the cloud of a covariance or grid call), max_problems problems and
+ * max_log_rows iteration-log rows (n_problems x k_max of a logged
+ * registration; 0 when no log is requested); ctx may be NULL.
+ * gcvo_set_workspace gives the context dev_ptr (device memory on the
+ * context's device, 256-byte aligned, at least that many bytes, owned by
+ * the caller and kept alive until the workspace is replaced, removed or the
+ * context destroyed) for the same limits; from then on gcvo_eval,
+ * gcvo_eval_exact, gcvo_register, gcvo_register_batched,
+ * gcvo_estimate_covariances and gcvo_build_grid / gcvo_rebuild_grid make no
+ * device allocation for their scratch (a grid still owns its own storage),
+ * and a call beyond the limits returns GCVO_ERR_WORKSPACE.  The calls that
+ * work on several clouds concurrently (the *_batched covariance and grid
+ * calls, gcvo_register_clouds) use internal child contexts that allocate
+ * their own scratch.  dev_ptr = NULL returns the context to library-owned
+ * scratch.  gcvo_set_workspace synchronises the stream and may allocate
+ * the context's small pinned host buffer.  The paper has no counterpart:
+ * this is the memory ownership of the boundary. */
+gcvo_status gcvo_workspace_size(const gcvo_ctx *ctx, int64_t max_points, int max_problems, int64_t max_log_rows,
+                                size_t *bytes);
+gcvo_status gcvo_set_workspace(gcvo_ctx *ctx, void *dev_ptr, size_t bytes, int64_t max_points, int max_problems,
+                               int64_t max_log_rows);
+
 /* Eq. (7b) plus the eigenvalue bound of the Remark after Eq. (7): for each
  * point, Sigma = 1/(n-1) sum_{y in N_n(x)} (y - x)(y - x)^T over its n = knn
  * nearest points (the point itself included, ties broken by lower index),
@@ -340,10 +368,22 @@ gcvo_status gcvo_proposal_create(gcvo_ctx *ctx, gcvo_proposal **out);
 gcvo_status gcvo_proposal_destroy(gcvo_proposal *prop);
 
 /* Copy the FP32 master parameters in (host or device pointer, n_params
- * floats) and reset the Adam state; or copy them out (checkpointing).
- * Both synchronise the stream. */
+ * floats) and reset the Adam state (a fresh start from given weights); or
+ * copy them out.  Checkpoints that resume training use the state calls
+ * below.  Both synchronise the stream. */
 gcvo_status gcvo_proposal_set_params(gcvo_ctx *ctx, gcvo_proposal *prop, const float *params);
 gcvo_status gcvo_proposal_get_params(gcvo_ctx *ctx, const gcvo_proposal *prop, float *params_out);
+
+/* The full training state, for checkpoints that resume training exactly:
+ * state (host or device, 3 x n_params floats) holds the FP32 master
+ * parameters, then Adam's first and second moment estimates, in the flat
+ * parameter order; step is the number of Adam steps taken (it sets Adam's
+ * bias corrections).  set_state also refreshes the BF16 weights.  After
+ * set_state(get_state()) further training steps give the same parameters,
+ * bit for bit, as if training had not been interrupted.  Both synchronise
+ * the stream. */
+gcvo_status gcvo_proposal_get_state(gcvo_ctx *ctx, const gcvo_proposal *prop, float *state_out, int64_t *step_out);
+gcvo_status gcvo_proposal_set_state(gcvo_ctx *ctx, gcvo_proposal *prop, const float *state, int64_t step);
 
 /* Forward pass for B pairs.  twist_out (host, B x 6, may be NULL): the
  * normalised twists; T0_out (host, B x 16, may be NULL): the proposed
@@ -372,6 +412,16 @@ typedef struct {
                                 and G-CVO-E passes (not G-CVO-1 line searches) */
     double pair_kernel_ms;   /* their summed device time, from CUDA events
                                 recorded on the context's stream around each launch */
+    int64_t n_device_allocs; /* device allocations (cudaMalloc) the library made in
+                                this process since gcvo_profile_enable */
+    int64_t n_finalize_launches; /* FP64 finalize launches of the register loops */
+    double finalize_ms;      /* their summed device time (CUDA events, as above) */
+    double transform_ms;     /* summed device time of the per-iteration source
+                                transform launches (CUDA events, as above) */
+    double clouds_covariance_ms; /* gcvo_register_clouds: time from the call's
+                                start to the end of its covariances, and */
+    double clouds_grid_ms;   /* from there to the end of its grids (CUDA events
+                                on the context's stream) */
 } gcvo_profile;
 
 /* Schedule of the pair passes (the autotuner; not in the paper): the source

@@ -432,40 +432,78 @@ gcvo_status check_status_word(gcvo_ctx *ctx) {
     return GCVO_OK;
 }
 
-// One pair pass on stream s (the work counter is reset first).  With
-// profiling on, an evaluation or G-CVO-E launch is bracketed by two events
-// from the pool; inside a stream capture they become event-record nodes of
-// the graph.
-gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode, cudaStream_t s,
-                             bool capturing = false) {
-    GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), s));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (ctx->profiling && (mode == PAIR_EVAL || mode == PAIR_EXACT)) {
-        while (ctx->ev_pool.size() < ctx->ev_used + 2) {
-            cudaEvent_t e;
-            GCVO_CUDA(cudaEventCreate(&e));
-            ctx->ev_pool.push_back(e);
-        }
-        e0 = ctx->ev_pool[ctx->ev_used];
-        e1 = ctx->ev_pool[ctx->ev_used + 1];
-        ctx->ev_used += 2;
-        GCVO_CUDA(cudaEventRecordWithFlags(e0, s, ev_flags));
+// With profiling on, a timed launch is bracketed by two events from the
+// pool (kind: 0 pair pass, 1 finalize, 2 transform); inside a stream capture
+// they become event-record nodes of the graph.  Returns the index of the
+// pair, or -1 when profiling is off.
+gcvo_status prof_begin(gcvo_ctx *ctx, cudaStream_t s, bool capturing, int kind, long long *slot) {
+    *slot = -1;
+    if (!ctx->profiling) return GCVO_OK;
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t e;
+        GCVO_CUDA(cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
     }
-    const int grid = mode == PAIR_EVAL ? b.grid : pair_grid(ctx, P, mode, b.sub);
-    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, b.sub, grid, s));
-    if (e1) GCVO_CUDA(cudaEventRecordWithFlags(e1, s, ev_flags));
+    if (ctx->ev_kind.size() < ctx->ev_pool.size() / 2) ctx->ev_kind.resize(ctx->ev_pool.size() / 2);
+    ctx->ev_kind[ctx->ev_used / 2] = kind;
+    *slot = (long long)ctx->ev_used;
+    ctx->ev_used += 2;
+    GCVO_CUDA(cudaEventRecordWithFlags(ctx->ev_pool[*slot], s,
+                                       capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     return GCVO_OK;
 }
 
-// Add the device time of the recorded pair-kernel launches (stream must be
+gcvo_status prof_end(gcvo_ctx *ctx, cudaStream_t s, bool capturing, long long slot) {
+    if (slot < 0) return GCVO_OK;
+    GCVO_CUDA(cudaEventRecordWithFlags(ctx->ev_pool[slot + 1], s,
+                                       capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+    return GCVO_OK;
+}
+
+// One pair pass on stream s (the work counter is reset first); evaluation
+// and G-CVO-E passes are timed when profiling.
+gcvo_status launch_pair_pass(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int mode, cudaStream_t s,
+                             bool capturing = false) {
+    GCVO_CUDA(cudaMemsetAsync(b.work, 0, sizeof(int), s));
+    long long slot = -1;
+    if (mode == PAIR_EVAL || mode == PAIR_EXACT) GCVO_TRY(prof_begin(ctx, s, capturing, 0, &slot));
+    const int grid = mode == PAIR_EVAL ? b.grid : pair_grid(ctx, P, mode, b.sub);
+    GCVO_CUDA(launch_pair(b.pa, mode, P.iso, P.feat_dim, b.sub, grid, s));
+    return prof_end(ctx, s, capturing, slot);
+}
+
+gcvo_status finalize_timed(gcvo_ctx *ctx, const FinalizeArgs &fa, cudaStream_t s, bool capturing) {
+    long long slot;
+    GCVO_TRY(prof_begin(ctx, s, capturing, 1, &slot));
+    GCVO_CUDA(launch_finalize(fa, s));
+    return prof_end(ctx, s, capturing, slot);
+}
+
+gcvo_status transform_timed(gcvo_ctx *ctx, const TransformArgs &ta, cudaStream_t s, bool capturing) {
+    long long slot;
+    GCVO_TRY(prof_begin(ctx, s, capturing, 2, &slot));
+    GCVO_CUDA(launch_transform(ta, s));
+    return prof_end(ctx, s, capturing, slot);
+}
+
+// Add the device time of the recorded launches (stream must be
 // synchronised) and release the events for reuse.
 gcvo_status collect_profile(gcvo_ctx *ctx, bool keep = false) {
     for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
         float ms = 0.f;
         GCVO_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[k], ctx->ev_pool[k + 1]));
-        ctx->pair_ms += ms;
-        ctx->pair_launches += 1;
+        switch (ctx->ev_kind[k / 2]) {
+            case 0:
+                ctx->pair_ms += ms;
+                ctx->pair_launches += 1;
+                break;
+            case 1:
+                ctx->fin_ms += ms;
+                ctx->fin_launches += 1;
+                break;
+            default:
+                ctx->transform_ms += ms;
+        }
     }
     if (!keep) ctx->ev_used = 0;
     return GCVO_OK;
@@ -480,22 +518,21 @@ gcvo_status enqueue_iteration(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, int
     if (order == 2) {
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
         b.fa.mode = FIN_GN;
-        GCVO_CUDA(launch_finalize(b.fa, s));
+        GCVO_TRY(finalize_timed(ctx, b.fa, s, capturing));
     } else if (order == 3) {
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EXACT, s, capturing));
         b.fa.mode = FIN_EXACT;
-        GCVO_CUDA(launch_finalize(b.fa, s));
+        GCVO_TRY(finalize_timed(ctx, b.fa, s, capturing));
     } else {
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_EVAL, s, capturing));
         b.fa.mode = FIN_GRAD;
-        GCVO_CUDA(launch_finalize(b.fa, s));
+        GCVO_TRY(finalize_timed(ctx, b.fa, s, capturing));
         GCVO_TRY(launch_pair_pass(ctx, P, b, PAIR_LINESEARCH, s, capturing));
         b.fa.mode = FIN_LINESEARCH;
-        GCVO_CUDA(launch_finalize(b.fa, s));
+        GCVO_TRY(finalize_timed(ctx, b.fa, s, capturing));
     }
     // the source at the new poses (problems that stopped keep theirs)
-    GCVO_CUDA(launch_transform(b.ta, s));
-    return GCVO_OK;
+    return transform_timed(ctx, b.ta, s, capturing);
 }
 
 // The U-iteration graph of a register call: captured on a private stream,
@@ -653,6 +690,67 @@ gcvo_status run_lanes(gcvo_ctx *ctx, int n, F fn) {
     return out;
 }
 
+// ---------------------------------------------------------------------------
+// Caller-owned workspace: every scratch buffer of the single-stream calls
+// (evaluation, registration, covariances, grid builds) as a fixed slice of
+// one caller allocation, sized for calls of at most N points (source points
+// of a registration or evaluation, or the cloud of a covariance or grid
+// call), np problems and `rows` iteration-log rows.  The slices follow the
+// buffers' own size formulas; a call that needs more fails with
+// GCVO_ERR_WORKSPACE instead of allocating.
+// ---------------------------------------------------------------------------
+std::vector<DevBuf *> ws_bufs(gcvo_ctx *c) {
+    std::vector<DevBuf *> v = {&c->stage_xyz, &c->stage_cov, &c->small,    &c->sort_keys, &c->sort_vals,
+                               &c->sort_tmp,  &c->scan_tmp,  &c->src_pos,  &c->src_ca,    &c->src_cb,
+                               &c->pprob,     &c->t_pos,     &c->t_ca,     &c->t_cb,      &c->t_lo,
+                               &c->items,     &c->item_prob, &c->pack_tmp, &c->partial,   &c->partial2,
+                               &c->probs,     &c->grids,     &c->evalout,  &c->logs,      &c->status_word,
+                               &c->knn_retry};
+    for (GridStore *g : {&c->knn_grid, &c->knn_grid2})
+        for (DevBuf *b : {&g->pos, &g->ca, &g->cb, &g->orig, &g->cell_start, &g->hkeys, &g->hval}) v.push_back(b);
+    return v;
+}
+
+std::vector<size_t> ws_sizes(int64_t N, int64_t np, int64_t rows) {
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t n = (size_t)std::max<int64_t>(N, 1);
+    const size_t n64 = (n + 63) / 64 * 64;
+    size_t H = 64;
+    while (H < 2 * n) H <<= 1;
+    const size_t small = al(np * sizeof(SrcDesc)) + al(np * sizeof(int)) * 7 + al(np * sizeof(int64_t)) +
+                         al(sizeof(int)) * 4 + 256 + 4096;
+    std::vector<size_t> v = {
+        (12 * n + 192 * (size_t)np + 192) * sizeof(float),            // stage_xyz: host xyz, cov, feat
+        6 * n * sizeof(float),                                          // stage_cov: host covariance output
+        std::max<size_t>(small, 4096),                                  // small
+        n * sizeof(unsigned long long),                                 // sort_keys
+        std::max(al(n * sizeof(int)) * 3, n * sizeof(int) * 2 + 1024),  // sort_vals
+        radix_sort_scratch_bytes((int64_t)n),                           // sort_tmp
+        scan_scratch_bytes(std::max<int64_t>((int64_t)n, ((int64_t)1 << 26) + 1)) + 1024,   // scan_tmp
+        n * sizeof(float4), n * sizeof(float4), n * sizeof(float4),     // src_pos, src_ca, src_cb
+        n * sizeof(int),                                                // pprob
+        n * sizeof(float4), n * sizeof(float4), n * sizeof(float4), n * sizeof(float4),   // t_pos, t_ca, t_cb, t_lo
+        n * sizeof(int4), n * sizeof(int),                              // items, item_prob
+        5 * n64 * sizeof(int),                                          // pack_tmp
+        n * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,        // partial
+        n * 64 * sizeof(float),                                         // partial2
+        np * sizeof(ProbDev), np * sizeof(GridDev), np * sizeof(EvalOut) + 256,
+        (size_t)std::max<int64_t>(rows, 1) * sizeof(gcvo_iter_log),     // logs
+        256,                                                            // status_word
+        n * sizeof(int) + 256};                                         // knn_retry
+    for (int g = 0; g < 2; ++g)
+        for (size_t b : {n * sizeof(float4), n * sizeof(float4), n * sizeof(float4), n * sizeof(int),
+                         (n + 1) * sizeof(int), H * sizeof(unsigned long long), H * sizeof(int)})
+            v.push_back(b);
+    return v;
+}
+
+size_t ws_total(const std::vector<size_t> &sz) {
+    size_t t = 0;
+    for (size_t b : sz) t += (std::max<size_t>(b, 256) + 255) & ~size_t(255);
+    return t;
+}
+
 }  // namespace
 
 extern "C" {
@@ -753,7 +851,13 @@ gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
     ctx->ev_used = 0;
     ctx->pair_launches = 0;
     ctx->pair_ms = 0.0;
+    ctx->fin_launches = 0;
+    ctx->fin_ms = 0.0;
+    ctx->transform_ms = 0.0;
+    ctx->clouds_cov_ms = 0.0;
+    ctx->clouds_grid_ms = 0.0;
     ctx->launch_base = launches_so_far();
+    ctx->alloc_base = device_allocs_so_far();
     return GCVO_OK;
 }
 
@@ -774,6 +878,12 @@ gcvo_status gcvo_profile_read(gcvo_ctx *ctx, gcvo_profile *out) {
     out->n_launches = launches_so_far() - ctx->launch_base;
     out->n_pair_launches = ctx->pair_launches;
     out->pair_kernel_ms = ctx->pair_ms;
+    out->n_device_allocs = device_allocs_so_far() - ctx->alloc_base;
+    out->n_finalize_launches = ctx->fin_launches;
+    out->finalize_ms = ctx->fin_ms;
+    out->transform_ms = ctx->transform_ms;
+    out->clouds_covariance_ms = ctx->clouds_cov_ms;
+    out->clouds_grid_ms = ctx->clouds_grid_ms;
     return GCVO_OK;
 }
 
@@ -1038,10 +1148,18 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
         GCVO_TRY(stage(ctx, hf[c], (size_t)fd * n[c], ctx->clouds_stage, off, &df[c]));
     }
     float *cov = ctx->clouds_cov.as<float>();
+    // phase events (profiling): start, covariances done, grids done
+    cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};
+    if (ctx->profiling)
+        for (auto &e : ph) {
+            GCVO_CUDA(cudaEventCreate(&e));
+        }
+    if (ph[0]) GCVO_CUDA(cudaEventRecord(ph[0], s));
     // Eq. (7b) and the eigenvalue bound for every cloud, concurrently
     GCVO_TRY(run_lanes(ctx, nc, [&](gcvo_ctx *c, int k) {
         return gcvo_estimate_covariances(c, dx[k], n[k], kp[k / 2], cov + cov_off[k]);
     }));
+    if (ph[1]) GCVO_CUDA(cudaEventRecord(ph[1], s));
     // the target grids, kept by the context and rebuilt in place next call
     if ((int)ctx->clouds_grids.size() < n_pairs) ctx->clouds_grids.resize(n_pairs, nullptr);
     GCVO_TRY(run_lanes(ctx, n_pairs, [&](gcvo_ctx *c, int k) {
@@ -1050,6 +1168,16 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
         if (g) return gcvo_rebuild_grid(c, g, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k]);
         return gcvo_build_grid(c, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k], &g);
     }));
+    if (ph[2]) {
+        GCVO_CUDA(cudaEventRecord(ph[2], s));
+        GCVO_CUDA(cudaEventSynchronize(ph[2]));
+        float a = 0.f, b = 0.f;
+        GCVO_CUDA(cudaEventElapsedTime(&a, ph[0], ph[1]));
+        GCVO_CUDA(cudaEventElapsedTime(&b, ph[1], ph[2]));
+        ctx->clouds_cov_ms += a;
+        ctx->clouds_grid_ms += b;
+        for (auto &e : ph) cudaEventDestroy(e);
+    }
     std::vector<gcvo_problem> pr(n_pairs);
     for (int k = 0; k < n_pairs; ++k) {
         pr[k].target = ctx->clouds_grids[k];
@@ -1060,6 +1188,57 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
         memcpy(pr[k].T0, pairs[k].T0, sizeof(pr[k].T0));
     }
     return run_register(ctx, n_pairs, pr.data(), solver, T_out, logs, n_iter, status);
+}
+
+gcvo_status gcvo_workspace_size(const gcvo_ctx *ctx, int64_t max_points, int max_problems, int64_t max_log_rows,
+                                size_t *bytes) {
+    (void)ctx;
+    if (!bytes || max_points < 1 || max_points > (1 << 26) || max_problems < 1 ||
+        max_problems > GCVO_MAX_PROBLEMS || max_log_rows < 0 || max_log_rows > ((int64_t)1 << 32))
+        return GCVO_ERR_INVALID_ARG;
+    *bytes = ws_total(ws_sizes(max_points, max_problems, max_log_rows));
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_set_workspace(gcvo_ctx *ctx, void *dev_ptr, size_t bytes, int64_t max_points, int max_problems,
+                               int64_t max_log_rows) {
+    if (!ctx) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<DevBuf *> bufs = ws_bufs(ctx);
+    if (!dev_ptr) {
+        // back to library-owned scratch, allocated on demand
+        for (DevBuf *b : bufs)
+            if (b->fixed) b->release();
+        ctx->ws_ptr = nullptr;
+        ctx->ws_bytes = 0;
+        return GCVO_OK;
+    }
+    size_t need = 0;
+    GCVO_TRY(gcvo_workspace_size(ctx, max_points, max_problems, max_log_rows, &need));
+    if (bytes < need || (reinterpret_cast<uintptr_t>(dev_ptr) & 255u)) return GCVO_ERR_INVALID_ARG;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, dev_ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return GCVO_ERR_INVALID_ARG;
+    }
+    if (at.type != cudaMemoryTypeDevice || at.device != ctx->device) return GCVO_ERR_INVALID_ARG;
+    // the host read-back buffer, sized once for the problem limit
+    void *hp;
+    GCVO_TRY(host_pinned(ctx, (size_t)(max_problems + 64) * sizeof(int), &hp));
+    const std::vector<size_t> sz = ws_sizes(max_points, max_problems, max_log_rows);
+    char *p = static_cast<char *>(dev_ptr);
+    for (size_t k = 0; k < bufs.size(); ++k) {
+        bufs[k]->release();
+        const size_t b = (std::max<size_t>(sz[k], 256) + 255) & ~size_t(255);
+        bufs[k]->ptr = p;
+        bufs[k]->bytes = b;
+        bufs[k]->fixed = true;
+        p += b;
+    }
+    ctx->ws_ptr = dev_ptr;
+    ctx->ws_bytes = bytes;
+    return GCVO_OK;
 }
 
 }  // extern "C"

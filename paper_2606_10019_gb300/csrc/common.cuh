@@ -35,9 +35,11 @@ namespace gcvo {
 void set_last_cuda_error(cudaError_t e, const char *what, int line);
 const char *last_cuda_error();
 
-// Process-wide count of kernels launched by the library (profiling).
+// Process-wide count of kernels launched by the library, and of the device
+// allocations (cudaMalloc) it made (profiling).
 void count_launches(long long n);
 long long launches_so_far();
+long long device_allocs_so_far();
 
 // Device status word bits (set by kernels with atomicOr, read by the host).
 enum : unsigned {
@@ -47,11 +49,14 @@ enum : unsigned {
 };
 
 // ---------------------------------------------------------------------------
-// A device buffer that only grows (released by the owner's destroy call).
+// A device buffer that only grows (released by the owner's destroy call), or,
+// when `fixed`, a slice of a caller-owned workspace that never grows: a need
+// beyond it is GCVO_ERR_WORKSPACE and release() forgets it without freeing.
 // ---------------------------------------------------------------------------
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
+    bool fixed = false;
     gcvo_status ensure(size_t need, cudaStream_t s);
     void release();
     template <class T> T *as() const { return static_cast<T *>(ptr); }
@@ -202,14 +207,23 @@ struct gcvo_ctx {
     // profiling: CUDA events around pair-kernel launches
     int profiling = 0;
     std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;   // per event pair: 0 pair pass, 1 finalize, 2 transform
     size_t ev_used = 0;
     long long launch_base = 0;
+    long long alloc_base = 0;
     long long pair_launches = 0;
     double pair_ms = 0.0;
+    long long fin_launches = 0;
+    double fin_ms = 0.0, transform_ms = 0.0;
+    double clouds_cov_ms = 0.0, clouds_grid_ms = 0.0;   // gcvo_register_clouds phases
     // child contexts with their own streams for the *_batched calls
     std::vector<gcvo_ctx *> lanes;
     std::vector<cudaStream_t> lane_streams;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // caller-owned workspace (gcvo_set_workspace): null when the library
+    // allocates its own scratch
+    void *ws_ptr = nullptr;
+    size_t ws_bytes = 0;
     // pair-kernel schedule (points per sub-tile): forced (0 = autotune), the
     // autotuner's choices per problem shape, and the last one used
     int forced_sub = 0;

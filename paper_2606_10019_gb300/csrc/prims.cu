@@ -11,9 +11,11 @@ namespace gcvo {
 
 static thread_local char g_last_err[256];
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_allocs{0};
 
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+long long device_allocs_so_far() { return g_allocs.load(std::memory_order_relaxed); }
 
 const char *last_cuda_error() { return g_last_err; }
 
@@ -23,6 +25,7 @@ void set_last_cuda_error(cudaError_t e, const char *what, int line) {
 
 gcvo_status DevBuf::ensure(size_t need, cudaStream_t s) {
     if (need <= bytes && ptr) return GCVO_OK;
+    if (fixed) return GCVO_ERR_WORKSPACE;   // a workspace slice never grows
     if (ptr) {
         GCVO_CUDA(cudaStreamSynchronize(s));
         GCVO_CUDA(cudaFree(ptr));
@@ -31,6 +34,7 @@ gcvo_status DevBuf::ensure(size_t need, cudaStream_t s) {
     }
     size_t b = need < 256 ? 256 : need;
     b = (b + 255) & ~size_t(255);
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     if (cudaMalloc(&ptr, b) != cudaSuccess) {
         cudaGetLastError();
         ptr = nullptr;
@@ -41,9 +45,10 @@ gcvo_status DevBuf::ensure(size_t need, cudaStream_t s) {
 }
 
 void DevBuf::release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr && !fixed) cudaFree(ptr);
     ptr = nullptr;
     bytes = 0;
+    fixed = false;
 }
 
 // ---------------------------------------------------------------------------

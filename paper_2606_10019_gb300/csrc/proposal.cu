@@ -706,6 +706,35 @@ gcvo_status gcvo_proposal_get_params(gcvo_ctx *ctx, const gcvo_proposal *P, floa
     return GCVO_OK;
 }
 
+gcvo_status gcvo_proposal_get_state(gcvo_ctx *ctx, const gcvo_proposal *P, float *state_out, int64_t *step_out) {
+    if (!ctx || !P || !state_out || !step_out) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)P->L.n();
+    const DevBuf *parts[3] = {&P->p, &P->m, &P->v};
+    for (int k = 0; k < 3; ++k)
+        GCVO_CUDA(cudaMemcpyAsync(state_out + k * n, parts[k]->ptr, n * sizeof(float), cudaMemcpyDefault,
+                                  ctx->stream));
+    GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
+    *step_out = P->step;
+    return GCVO_OK;
+}
+
+gcvo_status gcvo_proposal_set_state(gcvo_ctx *ctx, gcvo_proposal *P, const float *state, int64_t step) {
+    if (!ctx || !P || !state || step < 0 || step > (int64_t)1 << 30) return GCVO_ERR_INVALID_ARG;
+    GCVO_CUDA(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)P->L.n();
+    cudaStream_t s = ctx->stream;
+    DevBuf *parts[3] = {&P->p, &P->m, &P->v};
+    for (int k = 0; k < 3; ++k)
+        GCVO_CUDA(cudaMemcpyAsync(parts[k]->ptr, state + k * n, n * sizeof(float), cudaMemcpyDefault, s));
+    prop::k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int)n, P->p.as<float>(), P->w.as<__nv_bfloat16>());
+    count_launches(1);
+    GCVO_CUDA(cudaGetLastError());
+    GCVO_CUDA(cudaStreamSynchronize(s));
+    P->step = (int)step;
+    return GCVO_OK;
+}
+
 gcvo_status gcvo_proposal_infer(gcvo_ctx *ctx, gcvo_proposal *P, int B, int n, const float *src_xyz,
                                 const float *src_feat, int src_feat_stride, const float *tgt_xyz,
                                 const float *tgt_feat, int tgt_feat_stride, float *twist_out, double *T0_out) {

@@ -66,7 +66,10 @@ class gcvo_cloud_pair(ctypes.Structure):
 
 class gcvo_profile(ctypes.Structure):
     _fields_ = [("n_launches", ctypes.c_int64), ("n_pair_launches", ctypes.c_int64),
-                ("pair_kernel_ms", ctypes.c_double)]
+                ("pair_kernel_ms", ctypes.c_double), ("n_device_allocs", ctypes.c_int64),
+                ("n_finalize_launches", ctypes.c_int64),
+                ("finalize_ms", ctypes.c_double), ("transform_ms", ctypes.c_double),
+                ("clouds_covariance_ms", ctypes.c_double), ("clouds_grid_ms", ctypes.c_double)]
 
 
 class GcvoError(RuntimeError):
@@ -107,6 +110,8 @@ def lib() -> ctypes.CDLL:
         L.gcvo_register.argtypes = [P, P, P, P, P, I64, P, P, P, P, P]
         L.gcvo_register_batched.argtypes = [P, I, P, P, P, P, P, P]
         L.gcvo_register_clouds.argtypes = [P, I, P, P, P, P, P, P, P]
+        L.gcvo_workspace_size.argtypes = [P, I64, I, I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.gcvo_set_workspace.argtypes = [P, P, ctypes.c_size_t, I64, I, I64]
         L.gcvo_estimate_covariances_batched.argtypes = [P, I, P, P, P, P]
         L.gcvo_build_grids_batched.argtypes = [P, I, P, P, P, P, P, P]
         L.gcvo_pair_schedule.argtypes = [P, I, P]
@@ -426,6 +431,28 @@ def gcvo_register_clouds(ctx: Context, pairs: list[tuple], params: gcvo_kernel_p
     return T.reshape(n, 4, 4), out_logs, n_iter, status
 
 
+def gcvo_workspace_size(max_points: int, max_problems: int = 1, max_log_rows: int = 0) -> int:
+    """Bytes of a caller-owned workspace for calls of at most max_points
+    points, max_problems problems and max_log_rows iteration-log rows."""
+    b = ctypes.c_size_t()
+    _check(lib().gcvo_workspace_size(None, int(max_points), int(max_problems), int(max_log_rows), ctypes.byref(b)),
+           "gcvo_workspace_size")
+    return int(b.value)
+
+
+def gcvo_set_workspace(ctx: Context, buf, max_points: int = 1, max_problems: int = 1, max_log_rows: int = 0) -> None:
+    """Hand the context a caller-owned device buffer (a CUDA uint8 tensor of
+    at least gcvo_workspace_size bytes) as its scratch, or None to return to
+    library-owned scratch.  The buffer must outlive its use by the context."""
+    if buf is None:
+        _check(lib().gcvo_set_workspace(ctx.handle, None, 0, 1, 1, 0), "gcvo_set_workspace")
+        ctx._workspace = None
+        return
+    _check(lib().gcvo_set_workspace(ctx.handle, buf.data_ptr(), buf.numel() * buf.element_size(), int(max_points),
+                                    int(max_problems), int(max_log_rows)), "gcvo_set_workspace")
+    ctx._workspace = buf
+
+
 def gcvo_pair_schedule(ctx: Context, set: int = -1) -> int:
     """Force the pair-pass schedule (4, 8, 16, 32 points per sub-tile), hand it
     back to the autotuner (0) or leave it (-1); returns the last one used."""
@@ -441,7 +468,10 @@ def gcvo_profile_enable(ctx: Context, enable: bool = True) -> None:
 def gcvo_profile_read(ctx: Context) -> dict:
     p = gcvo_profile()
     _check(lib().gcvo_profile_read(ctx.handle, ctypes.byref(p)), "gcvo_profile_read")
-    return dict(n_launches=p.n_launches, n_pair_launches=p.n_pair_launches, pair_kernel_ms=p.pair_kernel_ms)
+    return dict(n_launches=p.n_launches, n_pair_launches=p.n_pair_launches, pair_kernel_ms=p.pair_kernel_ms,
+                n_device_allocs=p.n_device_allocs,
+                n_finalize_launches=p.n_finalize_launches, finalize_ms=p.finalize_ms, transform_ms=p.transform_ms,
+                clouds_covariance_ms=p.clouds_covariance_ms, clouds_grid_ms=p.clouds_grid_ms)
 
 
 # ---------------------------------------------------------------------------
@@ -458,6 +488,8 @@ def _prop_lib():
         L.gcvo_proposal_destroy.argtypes = [P]
         L.gcvo_proposal_set_params.argtypes = [P, P, P]
         L.gcvo_proposal_get_params.argtypes = [P, P, P]
+        L.gcvo_proposal_get_state.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int64)]
+        L.gcvo_proposal_set_state.argtypes = [P, P, P, ctypes.c_int64]
         L.gcvo_proposal_infer.argtypes = [P, P, I, I, P, P, I, P, P, I, P, P]
         L.gcvo_proposal_train_step.argtypes = [P, P, I, I, P, P, I, P, P, I, P, ctypes.c_float, P, P]
         L._prop_ready = True
@@ -495,6 +527,20 @@ class Proposal:
         p = np.zeros(self.n_params, dtype=np.float32)
         _check(_prop_lib().gcvo_proposal_get_params(self.ctx.handle, self.handle, p.ctypes.data), "get_params")
         return p
+
+    def get_state(self):
+        """(state (3, n_params) float32: parameters, Adam m, Adam v; Adam step)."""
+        st = np.zeros((3, self.n_params), dtype=np.float32)
+        step = ctypes.c_int64()
+        _check(_prop_lib().gcvo_proposal_get_state(self.ctx.handle, self.handle, st.ctypes.data, ctypes.byref(step)),
+               "get_state")
+        return st, int(step.value)
+
+    def set_state(self, state: np.ndarray, step: int) -> None:
+        st = np.ascontiguousarray(state, dtype=np.float32)
+        assert st.size == 3 * self.n_params
+        _check(_prop_lib().gcvo_proposal_set_state(self.ctx.handle, self.handle, st.ctypes.data, int(step)),
+               "set_state")
 
     def infer(self, src_xyz, src_feat, tgt_xyz, tgt_feat):
         """Batched clouds: xyz (B, 3, n), feat (B, n) device tensors.

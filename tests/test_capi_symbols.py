@@ -63,6 +63,11 @@ def test_invalid_arguments_are_rejected_before_any_device_work(libpath):
     assert L.gcvo_build_grids_batched(None, 1, None, None, None, None, None, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_pair_schedule(None, 8, None) == G.GCVO_ERR_INVALID_ARG
     assert L.gcvo_profile_enable(None, 1) == G.GCVO_ERR_INVALID_ARG
+    P = ctypes.c_void_p
+    L.gcvo_proposal_get_state.argtypes = [P, P, P, P]
+    L.gcvo_proposal_set_state.argtypes = [P, P, P, ctypes.c_int64]
+    assert L.gcvo_proposal_get_state(None, None, None, None) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_proposal_set_state(None, None, None, 0) == G.GCVO_ERR_INVALID_ARG
 
 
 def test_eval_static_rejects_bad_arguments_without_touching_a_device(libpath):
@@ -79,3 +84,22 @@ def test_eval_static_rejects_bad_arguments_without_touching_a_device(libpath):
     T = (ctypes.c_double * 16)(*[1.0 if k % 5 == 0 else 0.0 for k in range(16)])
     assert L.gcvo_eval_static(None, None, None, None, 10, T, None, ctypes.byref(f), g, H) == G.GCVO_ERR_INVALID_ARG
 
+
+
+def test_workspace_size_follows_the_limits(libpath):
+    """gcvo_workspace_size needs no device: it grows with every limit and
+    refuses limits outside the documented ranges."""
+    from paper_2606_10019_gb300 import gcvo as G
+    a = G.gcvo_workspace_size(10_000, 1, 0)
+    b = G.gcvo_workspace_size(20_000, 1, 0)
+    c = G.gcvo_workspace_size(20_000, 64, 0)
+    d = G.gcvo_workspace_size(20_000, 64, 64 * 200)
+    assert 0 < a < b < c < d
+    # per point: source records, transformed records and partials dominate
+    assert 400 < (b - a) / 10_000 < 2000
+    L = G.lib()
+    s = ctypes.c_size_t()
+    assert L.gcvo_workspace_size(None, 0, 1, 0, ctypes.byref(s)) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_workspace_size(None, 10, 0, 0, ctypes.byref(s)) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_workspace_size(None, 10, 1, -1, ctypes.byref(s)) == G.GCVO_ERR_INVALID_ARG
+    assert L.gcvo_set_workspace(None, None, 0, 1, 1, 0) == G.GCVO_ERR_INVALID_ARG
