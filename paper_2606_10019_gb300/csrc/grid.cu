@@ -305,6 +305,16 @@ gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gc
     GridStore &fine = ctx->knn_grid;
     GridStore &coarse = ctx->knn_grid2;
     GCVO_TRY(build_grid_store(ctx, xyz, nullptr, nullptr, n, q, true, cell, fine));
+    // A voxel from the kernel range can hold hundreds of points of a dense
+    // cloud, and every query would sort all of them.  The search is exact
+    // at any voxel size, so shrink it towards about knn / 2 points per
+    // occupied voxel (points on surfaces: the count scales with the square
+    // of the edge), at most 16-fold.
+    const double occ = (double)n / std::max(1, fine.d.n_cells);
+    if (occ > 2.0 * kp.knn) {
+        cell *= std::max(1.0 / 16.0, std::sqrt(0.5 * kp.knn / occ));
+        GCVO_TRY(build_grid_store(ctx, xyz, nullptr, nullptr, n, q, true, cell, fine));
+    }
     GCVO_TRY(build_grid_store(ctx, xyz, nullptr, nullptr, n, q, true, cell * 8.0, coarse));
     GCVO_TRY(ctx->status_word.ensure(256, s));
     GCVO_TRY(ctx->knn_retry.ensure(n * sizeof(int) + 256, s));

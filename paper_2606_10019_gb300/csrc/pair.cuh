@@ -7,14 +7,10 @@ namespace gcvo {
 
 // Pair-kernel tiling (tile.cu): blocks of PAIR_WARPS independent warps; a
 // warp takes one work item, a sub-tile of at most SUB = 4, 8, 16 or 32 source
-// points (the schedule: 8, 4, 2 or 1 lanes per point), lists the runs of
-// target points of the voxel columns near it (up to PAIR_MAXRUN at a time)
-// and stages them PAIR_WCAP at a time into one of two buffers in its own
-// shared memory, the next chunk's copies in flight while it works on the
-// current one.
+// points (the schedule: 8, 4, 2 or 1 lanes per point), and stages target
+// points PAIR_WCAP at a time in its own shared memory.
 constexpr int PAIR_WARPS = 4;
-constexpr int PAIR_WCAP = 128;
-constexpr int PAIR_MAXRUN = 128;
+constexpr int PAIR_WCAP = 160;
 constexpr int PAIR_GRAB = 16;   // work items a warp takes per atomic
 constexpr int PAIR_SLOTS = 28;         // f, g (6), M (21) per sub-tile
 constexpr int PAIR_SLOTS_EXACT = 46;   // f, g, Q - M (21), C (9), S_B (9): G-CVO-E

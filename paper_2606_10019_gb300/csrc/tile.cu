@@ -16,12 +16,9 @@
 //     by rho are listed, one per lane.  Points are sorted by voxel with cz
 //     fastest, so the voxels of one column over the needed cz range hold one
 //     run of points, read from the grid's dense per-voxel prefix table with
-//     two loads.  The non-empty runs go into the warp's run table, which
-//     lays them end to end; that candidate space is staged into the warp's
-//     shared memory PAIR_WCAP points at a time by cp.async.bulk copies into
-//     two buffers, each completing on its own mbarrier: the copies of chunk
-//     k + 1 are issued before the warp waits for chunk k, so the transfer of
-//     one chunk overlaps the pair work on the previous one.
+//     two loads.  The runs are staged into the warp's shared memory
+//     PAIR_WCAP points at a time by cp.async.bulk copies completing on the
+//     warp's mbarrier.
 //  3. SUB = 4, 8, 16 or 32 (8, 4, 2 or 1 lanes per point) is the schedule the
 //     autotuner picks.  The warp holds its sub-tile's points one per lane of
 //     each group of SUB lanes, keeps the staged targets that lie within rho
@@ -54,30 +51,20 @@ namespace gcvo {
 namespace {
 
 static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
-static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a buffer's staged pos, ca");
+static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
 static_assert(PAIR_SLOTS_EXACT * 33 * 4 <= PAIR_WCAP * 48, "exact epilogue transpose fits in pos, ca, cb");
-static_assert(PAIR_MAXRUN % 32 == 0, "the run table is filled 32 columns at a time");
 
-// One staging buffer: a chunk of target points (with their coordinate tails
-// when LO).
+// Per warp: staged target points (with their coordinate tails when LO),
+// the list of those near the sub-tile, and the mbarrier the bulk copies
+// complete on.
 template <bool LO>
-struct __align__(16) StageBuf {
+struct __align__(16) WarpStage {
     float4 pos[PAIR_WCAP];
     float4 ca[PAIR_WCAP];
     float4 cb[PAIR_WCAP];
     float4 lo[LO ? PAIR_WCAP : 1];
-};
-
-// Per warp: two staging buffers and their mbarriers, the run table (first
-// target of each run and its offset in the candidate space, with the total
-// after the last), and the list of staged targets near the sub-tile.
-template <bool LO>
-struct __align__(16) WarpStage {
-    StageBuf<LO> buf[2];
-    int run_start[PAIR_MAXRUN];
-    int run_off[PAIR_MAXRUN + 1];
     unsigned short list[PAIR_WCAP];
-    uint64_t bar[2];
+    uint64_t bar;
 };
 
 // One anisotropic pair (Eq. 7), r = x_i - p_j, into the lane sums t[10].
@@ -262,27 +249,21 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
 }
 
 template <int MODE, bool ISO, int FD, int SUB>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) k_tile(PairArgs a) {
+__global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
     static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
     constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : MODE == PAIR_EXACT ? 25 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? PAIR_SLOTS : MODE == PAIR_EXACT ? PAIR_SLOTS_EXACT : 5;
     constexpr bool LO = MODE == PAIR_EXACT;
-    constexpr unsigned TBYTES = LO ? 64u : 48u;   // staged bytes per target
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpStage<LO> *stage = reinterpret_cast<WarpStage<LO> *>(smem_raw);
+    __shared__ WarpStage<LO> stage[PAIR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     WarpStage<LO> &S = stage[w];
-    if (lane == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-    }
+    if (lane == 0) mbar_init(&S.bar, 1);
     __syncwarp();
-    unsigned parity = 0;   // bit b: the phase parity of buffer b's mbarrier
-    int cur = 0;           // the buffer of the next chunk to stage
+    unsigned parity = 0;
     const int n_items = *a.n_items;
     // items per grab: up to PAIR_GRAB, fewer when there are few items per
     // warp, so that small problems still spread over the whole GPU
@@ -403,227 +384,196 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) k_tile(PairArgs a) {
         int n_pairs = 0, n_kept = 0, n_cand = 0;
         const int dy = G->dims[1], dzs = G->dims[2];
 
-        int col = 0;   // next voxel column to list
-        while (col < n_cols) {
-            // ---- 2. runs of the next columns into the run table, 32 at a
-            // time, until it is full.  A column is kept when its xy
-            // rectangle lies within rho of the box; its cz range shrinks
-            // with that distance.
-            int n_runs = 0, total = 0;
-            while (col < n_cols && n_runs + 32 <= PAIR_MAXRUN) {
-                const int c = col + lane;
-                int rs = 0, rl = 0;
-                if (c < n_cols) {
-                    const int cx = lo[0] + c / ncy, cy = lo[1] + c % ncy;
-                    const float x0 = G->corner[0] + (float)cx * h, y0 = G->corner[1] + (float)cy * h;
-                    const float ddx = fmaxf(0.0f, fmaxf(x0 - bmax[0], bmin[0] - (x0 + h)));
-                    const float ddy = fmaxf(0.0f, fmaxf(y0 - bmax[1], bmin[1] - (y0 + h)));
-                    const float d2xy = ddx * ddx + ddy * ddy;
-                    if (d2xy <= rc2) {
-                        const float ez = sqrtf(rc2 - d2xy);
-                        const int czl = max(lo[2], (int)floorf(fmaxf((bmin[2] - ez - G->corner[2]) * ih, -1.0f)));
-                        const int czh = min(hi[2], (int)floorf(fminf((bmax[2] + ez - G->corner[2]) * ih, (float)dzs)));
-                        if (czl <= czh) {
-                            const size_t base = ((size_t)cx * dy + cy) * dzs;
-                            rs = __ldg(G->vox_first + base + czl);
-                            rl = __ldg(G->vox_first + base + czh + 1) - rs;
-                        }
+        for (int cb0 = 0; cb0 < n_cols; cb0 += 32) {
+            // ---- 2. one column per lane: its run of target points.  A
+            // column is kept when its xy rectangle lies within rho of the
+            // box; its cz range shrinks with that distance.
+            const int c = cb0 + lane;
+            int rs = 0, rl = 0;
+            if (c < n_cols) {
+                const int cx = lo[0] + c / ncy, cy = lo[1] + c % ncy;
+                const float x0 = G->corner[0] + (float)cx * h, y0 = G->corner[1] + (float)cy * h;
+                const float ddx = fmaxf(0.0f, fmaxf(x0 - bmax[0], bmin[0] - (x0 + h)));
+                const float ddy = fmaxf(0.0f, fmaxf(y0 - bmax[1], bmin[1] - (y0 + h)));
+                const float d2xy = ddx * ddx + ddy * ddy;
+                if (d2xy <= rc2) {
+                    const float ez = sqrtf(rc2 - d2xy);
+                    const int czl = max(lo[2], (int)floorf(fmaxf((bmin[2] - ez - G->corner[2]) * ih, -1.0f)));
+                    const int czh = min(hi[2], (int)floorf(fminf((bmax[2] + ez - G->corner[2]) * ih, (float)dzs)));
+                    if (czl <= czh) {
+                        const size_t base = ((size_t)cx * dy + cy) * dzs;
+                        rs = __ldg(G->vox_first + base + czl);
+                        rl = __ldg(G->vox_first + base + czh + 1) - rs;
                     }
                 }
-                // exclusive offsets of the non-empty runs
-                int incl = rl;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const unsigned has = __ballot_sync(FULL, rl > 0);
-                if (rl > 0) {
-                    const int r = n_runs + __popc(has & lt_mask);
-                    S.run_start[r] = rs;
-                    S.run_off[r] = total + incl - rl;
-                }
-                n_runs += __popc(has);
-                total += __shfl_sync(FULL, incl, 31);
-                col += 32;
             }
-            if (lane == 0) S.run_off[n_runs] = total;
-            __syncwarp();
+            // exclusive warp offsets of the runs
+            int incl = rl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int off = incl - rl;
 
-            // ---- stage [base, base + m) of the candidate space into buffer b
-            auto issue = [&](int base, int b) {
-                const int m = min(PAIR_WCAP, total - base);
-                StageBuf<LO> &D = S.buf[b];
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_expect_tx(&S.bar[b], (unsigned)m * TBYTES);
-                __syncwarp();
-                for (int r = lane; r < n_runs; r += 32) {
-                    const int o0 = S.run_off[r], o1 = S.run_off[r + 1];
-                    const int s0 = max(o0, base), s1 = min(o1, base + m);
-                    if (s1 > s0) {
-                        const int src = S.run_start[r] + (s0 - o0), dst = s0 - base;
-                        const unsigned bytes = (unsigned)(s1 - s0) * 16u;
-                        bulk_g2s(D.pos + dst, G->pos + src, bytes, &S.bar[b]);
-                        bulk_g2s(D.ca + dst, G->ca + src, bytes, &S.bar[b]);
-                        bulk_g2s(D.cb + dst, G->cb + src, bytes, &S.bar[b]);
-                        if (LO) bulk_g2s(D.lo + dst, G->plo + src, bytes, &S.bar[b]);
-                    }
-                }
-            };
-            if (total > 0) issue(0, cur);
             for (int base = 0; base < total; base += PAIR_WCAP) {
                 const int m = min(PAIR_WCAP, total - base);
-                const int b = cur;
-                cur ^= 1;
-                if (base + PAIR_WCAP < total) issue(base + PAIR_WCAP, cur);   // the next chunk, in flight
+                // ---- stage the chunk [base, base + m) (bulk copies)
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (LO ? 64u : 48u));
+                __syncwarp();
                 {
-                    // bounded wait for chunk base; the exit decision is warp-uniform
+                    const int s0 = max(off, base), s1 = min(off + rl, base + m);
+                    if (s1 > s0) {
+                        const int src = rs + (s0 - off), dst = s0 - base;
+                        const unsigned bytes = (unsigned)(s1 - s0) * 16u;
+                        bulk_g2s(S.pos + dst, G->pos + src, bytes, &S.bar);
+                        bulk_g2s(S.ca + dst, G->ca + src, bytes, &S.bar);
+                        bulk_g2s(S.cb + dst, G->cb + src, bytes, &S.bar);
+                        if (LO) bulk_g2s(S.lo + dst, G->plo + src, bytes, &S.bar);
+                    }
+                }
+                {
+                    // bounded wait; the exit decision is warp-uniform
                     int spin = 0;
                     bool all_done;
                     for (;;) {
-                        all_done = __all_sync(FULL, mbar_try_wait(&S.bar[b], (parity >> b) & 1u));
+                        all_done = __all_sync(FULL, mbar_try_wait(&S.bar, parity));
                         if (all_done || ++spin > (1 << 22)) break;
                     }
                     if (!all_done) {
-                        // give up: record it, then let the copies still in
-                        // flight land (bounded as well) before leaving
                         if (lane == 0) atomicOr(a.status_word, DEV_ERR_TIMEOUT);
-                        if (base + PAIR_WCAP < total) {
-                            for (int k = 0; k < (1 << 22); ++k)
-                                if (__all_sync(FULL, mbar_try_wait(&S.bar[cur], (parity >> cur) & 1u))) break;
-                        }
                         return;
                     }
-                    parity ^= 1u << b;
+                    parity ^= 1u;
                 }
-                const StageBuf<LO> &B = S.buf[b];
 
-                    // ---- 3. the staged targets within rho of the sub-tile box
-                    int L = 0;
-                    for (int t0 = 0; t0 < m; t0 += 32) {
-                        const int tt = t0 + lane;
-                        bool hit = false;
-                        if (tt < m) {
-                            const float4 x = B.pos[tt];
-                            const float dx = fmaxf(0.f, fmaxf(bmin[0] - x.x, x.x - bmax[0]));
-                            const float dyy = fmaxf(0.f, fmaxf(bmin[1] - x.y, x.y - bmax[1]));
-                            const float dz = fmaxf(0.f, fmaxf(bmin[2] - x.z, x.z - bmax[2]));
-                            hit = dx * dx + dyy * dyy + dz * dz <= rc2;
-                        }
-                        const unsigned bal = __ballot_sync(FULL, hit);
-                        if (hit) S.list[L + __popc(bal & lt_mask)] = (unsigned short)tt;
-                        L += __popc(bal);
+                // ---- 3. the staged targets within rho of the sub-tile box
+                int L = 0;
+                for (int t0 = 0; t0 < m; t0 += 32) {
+                    const int tt = t0 + lane;
+                    bool hit = false;
+                    if (tt < m) {
+                        const float4 x = S.pos[tt];
+                        const float dx = fmaxf(0.f, fmaxf(bmin[0] - x.x, x.x - bmax[0]));
+                        const float dyy = fmaxf(0.f, fmaxf(bmin[1] - x.y, x.y - bmax[1]));
+                        const float dz = fmaxf(0.f, fmaxf(bmin[2] - x.z, x.z - bmax[2]));
+                        hit = dx * dx + dyy * dyy + dz * dz <= rc2;
                     }
-                    __syncwarp();
-                    if (qi == 0 && sval) n_cand += L;
+                    const unsigned bal = __ballot_sync(FULL, hit);
+                    if (hit) S.list[L + __popc(bal & lt_mask)] = (unsigned short)tt;
+                    L += __popc(bal);
+                }
+                __syncwarp();
+                if (qi == 0 && sval) n_cand += L;
 
-                    // ---- 4. TQ targets per step, one per group of lanes
-                    for (int j = 0; j < L; j += TQ) {
-                        const int idx = j + qi;
-                        const bool act = sval && idx < L;
-                        const int k = S.list[min(idx, L - 1)];
-                        const float4 x = B.pos[k];
-                        float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
-                        if (LO) {
-                            // r = (x_hi - p_hi) + (x_lo - p_lo)
-                            const float4 xl = B.lo[k];
-                            r0 += xl.x - plx;
-                            r1 += xl.y - ply;
-                            r2 += xl.z - plz;
-                        }
-                        if (MODE == PAIR_EVAL && !ISO) {
-                            pair_aniso<FD>(r0, r1, r2, x, B.ca[k], B.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
-                                           n_kept);
-                            continue;
-                        }
-                        if constexpr (MODE == PAIR_EXACT && !ISO) {
-                            pair_exact<FD>(r0, r1, r2, x, B.ca[k], B.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
-                                           n_kept);
-                            continue;
-                        }
-                        const float rr = r0 * r0 + r1 * r1 + r2 * r2;
-                        const bool in = act && rr <= rho2;
-                        float cij = x.w * l0;
-                        if (FD > 1) {
-                            const float4 cbv = B.cb[k];
-                            cij += cbv.z * l1 + cbv.w * l2;
-                        }
-                        if (ISO) {
-                            const float d2 = rr * iso_inv;
-                            const bool keep = in && d2 <= c2;
-                            const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                            n_pairs += in;
-                            n_kept += keep;
-                            if constexpr (MODE == PAIR_EVAL || MODE == PAIR_EXACT) {
-                                t[0] += wgt;
-                                t[1] += wgt * r0;
-                                t[2] += wgt * r1;
-                                t[3] += wgt * r2;
-                                if constexpr (MODE == PAIR_EXACT) {
-                                    // Sigma'_j = 0: y = r / ell^2, u = 0, K = 0
-                                    t[10] += wgt * r0 * r0;
-                                    t[11] += wgt * r0 * r1;
-                                    t[12] += wgt * r0 * r2;
-                                    t[13] += wgt * r1 * r1;
-                                    t[14] += wgt * r1 * r2;
-                                    t[15] += wgt * r2 * r2;
-                                }
-                            } else {
-                                // A = I / ell^2
-                                const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
-                                const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
-                                const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
-                                const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
-                                const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
-                                const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
-                                const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
-                                const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
-                                ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
+                // ---- 4. TQ targets per step, one per group of lanes
+                for (int j = 0; j < L; j += TQ) {
+                    const int idx = j + qi;
+                    const bool act = sval && idx < L;
+                    const int k = S.list[min(idx, L - 1)];
+                    const float4 x = S.pos[k];
+                    float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+                    if (LO) {
+                        // r = (x_hi - p_hi) + (x_lo - p_lo)
+                        const float4 xl = S.lo[k];
+                        r0 += xl.x - plx;
+                        r1 += xl.y - ply;
+                        r2 += xl.z - plz;
+                    }
+                    if (MODE == PAIR_EVAL && !ISO) {
+                        pair_aniso<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                                       n_kept);
+                        continue;
+                    }
+                    if constexpr (MODE == PAIR_EXACT && !ISO) {
+                        pair_exact<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
+                                       n_kept);
+                        continue;
+                    }
+                    const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+                    const bool in = act && rr <= rho2;
+                    float cij = x.w * l0;
+                    if (FD > 1) {
+                        const float4 cbv = S.cb[k];
+                        cij += cbv.z * l1 + cbv.w * l2;
+                    }
+                    if (ISO) {
+                        const float d2 = rr * iso_inv;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        if constexpr (MODE == PAIR_EVAL || MODE == PAIR_EXACT) {
+                            t[0] += wgt;
+                            t[1] += wgt * r0;
+                            t[2] += wgt * r1;
+                            t[3] += wgt * r2;
+                            if constexpr (MODE == PAIR_EXACT) {
+                                // Sigma'_j = 0: y = r / ell^2, u = 0, K = 0
+                                t[10] += wgt * r0 * r0;
+                                t[11] += wgt * r0 * r1;
+                                t[12] += wgt * r0 * r2;
+                                t[13] += wgt * r1 * r1;
+                                t[14] += wgt * r1 * r2;
+                                t[15] += wgt * r2 * r2;
                             }
                         } else {
-                            // anisotropic line search (MODE == PAIR_LINESEARCH)
-                            const float4 ca = B.ca[k];
-                            const float4 cbv = B.cb[k];
-                            const float s00 = ca.x + qv[0], s01 = ca.y + qv[1], s02 = ca.z + qv[2];
-                            const float s11 = ca.w + qv[3], s12 = cbv.x + qv[4], s22 = cbv.y + qv[5];
-                            const float c00 = s11 * s22 - s12 * s12;
-                            const float c01 = s02 * s12 - s01 * s22;
-                            const float c02 = s01 * s12 - s02 * s11;
-                            const float c11 = s00 * s22 - s02 * s02;
-                            const float c12 = s01 * s02 - s00 * s12;
-                            const float c22 = s00 * s11 - s01 * s01;
-                            const float det = s00 * c00 + s01 * c01 + s02 * c02;
-                            const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
-                            const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
-                            const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
-                            const float qf = r0 * y0 + r1 * y1 + r2 * y2;
-                            const float rdet = rcp_approx(det);
-                            const float d2 = qf * rdet;
-                            const bool keep = in && d2 <= c2;
-                            const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                            n_pairs += in;
-                            n_kept += keep;
-                            // bilinear forms of A = adj / det with r and a_k
-                            const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
-                            const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
-                            const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
-                            const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
-                            const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
-                            const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
-                            const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
-                            const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
-                            const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
-                            const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
-                            const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
-                            const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
-                            const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
-                            const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
+                            // A = I / ell^2
+                            const float kr1 = (b1[0] * r0 + b1[1] * r1 + b1[2] * r2) * iso_inv;
+                            const float kr2 = (b2[0] * r0 + b2[1] * r1 + b2[2] * r2) * iso_inv;
+                            const float kr3 = (b3[0] * r0 + b3[1] * r1 + b3[2] * r2) * iso_inv;
+                            const float kr4 = (b4[0] * r0 + b4[1] * r1 + b4[2] * r2) * iso_inv;
+                            const float a11 = (b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]) * iso_inv;
+                            const float a12 = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) * iso_inv;
+                            const float a13 = (b1[0] * b3[0] + b1[1] * b3[1] + b1[2] * b3[2]) * iso_inv;
+                            const float a22 = (b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]) * iso_inv;
                             ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
                         }
+                    } else {
+                        // anisotropic line search (MODE == PAIR_LINESEARCH)
+                        const float4 ca = S.ca[k];
+                        const float4 cbv = S.cb[k];
+                        const float s00 = ca.x + qv[0], s01 = ca.y + qv[1], s02 = ca.z + qv[2];
+                        const float s11 = ca.w + qv[3], s12 = cbv.x + qv[4], s22 = cbv.y + qv[5];
+                        const float c00 = s11 * s22 - s12 * s12;
+                        const float c01 = s02 * s12 - s01 * s22;
+                        const float c02 = s01 * s12 - s02 * s11;
+                        const float c11 = s00 * s22 - s02 * s02;
+                        const float c12 = s01 * s02 - s00 * s12;
+                        const float c22 = s00 * s11 - s01 * s01;
+                        const float det = s00 * c00 + s01 * c01 + s02 * c02;
+                        const float y0 = c00 * r0 + c01 * r1 + c02 * r2;
+                        const float y1 = c01 * r0 + c11 * r1 + c12 * r2;
+                        const float y2 = c02 * r0 + c12 * r1 + c22 * r2;
+                        const float qf = r0 * y0 + r1 * y1 + r2 * y2;
+                        const float rdet = rcp_approx(det);
+                        const float d2 = qf * rdet;
+                        const bool keep = in && d2 <= c2;
+                        const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+                        n_pairs += in;
+                        n_kept += keep;
+                        // bilinear forms of A = adj / det with r and a_k
+                        const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
+                        const float kr2 = (b2[0] * y0 + b2[1] * y1 + b2[2] * y2) * rdet;
+                        const float kr3 = (b3[0] * y0 + b3[1] * y1 + b3[2] * y2) * rdet;
+                        const float kr4 = (b4[0] * y0 + b4[1] * y1 + b4[2] * y2) * rdet;
+                        const float w0 = c00 * b1[0] + c01 * b1[1] + c02 * b1[2];
+                        const float w1 = c01 * b1[0] + c11 * b1[1] + c12 * b1[2];
+                        const float w2 = c02 * b1[0] + c12 * b1[1] + c22 * b1[2];
+                        const float a11 = (b1[0] * w0 + b1[1] * w1 + b1[2] * w2) * rdet;
+                        const float a12 = (b2[0] * w0 + b2[1] * w1 + b2[2] * w2) * rdet;
+                        const float a13 = (b3[0] * w0 + b3[1] * w1 + b3[2] * w2) * rdet;
+                        const float v0 = c00 * b2[0] + c01 * b2[1] + c02 * b2[2];
+                        const float v1 = c01 * b2[0] + c11 * b2[1] + c12 * b2[2];
+                        const float v2 = c02 * b2[0] + c12 * b2[1] + c22 * b2[2];
+                        const float a22 = (b2[0] * v0 + b2[1] * v1 + b2[2] * v2) * rdet;
+                        ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
                     }
-
-                __syncwarp();   // the list and buffer b are reused by later chunks
+                }
+                __syncwarp();   // the list and staged points are reused by the next chunk
             }
         }
 
@@ -708,8 +658,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) k_tile(PairArgs a) {
             }
         }
         // compensated sums over the sub-tile's points: transpose through the
-        // warp's staging buffer 0 (no copy is in flight now), lane k adds slot k
-        float *tr = reinterpret_cast<float *>(S.buf[0].pos);
+        // warp's staging area (free now), lane k adds slot k
+        float *tr = reinterpret_cast<float *>(S.pos);
         __syncwarp();
         if (qi == 0)
 #pragma unroll
@@ -795,26 +745,9 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-// Dynamic shared memory of one pair-kernel block (its warps' stages), and
-// the opt-in above the 48 KB default, once per kernel instance.
-template <int MODE>
-constexpr size_t tile_smem_bytes() {
-    return PAIR_WARPS * sizeof(WarpStage<MODE == PAIR_EXACT>);
-}
-
-template <int MODE, bool ISO, int FD, int SUB>
-static cudaError_t tile_smem_optin() {
-    static cudaError_t once = cudaFuncSetAttribute(k_tile<MODE, ISO, FD, SUB>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)tile_smem_bytes<MODE>());
-    return once;
-}
-
 template <int MODE, bool ISO, int FD, int SUB>
 static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
-    cudaError_t e = tile_smem_optin<MODE, ISO, FD, SUB>();
-    if (e != cudaSuccess) return e;
-    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, tile_smem_bytes<MODE>(), s>>>(a);
+    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -822,9 +755,7 @@ static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
 template <int MODE, bool ISO, int FD, int SUB>
 static int occupancy_t() {
     int nb = 0;
-    if (tile_smem_optin<MODE, ISO, FD, SUB>() != cudaSuccess) return 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32,
-                                                  tile_smem_bytes<MODE>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32, 0);
     return nb;
 }
 

@@ -351,13 +351,19 @@ def gcvo_eval_exact(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T) -> 
                            st.rho)
 
 
-def _logs_to_list(logs, n):
-    out = []
-    for k in range(n):
-        L = logs[k]
-        out.append(dict(f=L.f, g=np.array(L.g[:]), xi=np.array(L.xi[:]), xi_l1=L.xi_l1,
-                        T=np.array(L.T[:]).reshape(4, 4), n_pairs=L.n_pairs, n_kept=L.n_kept))
-    return out
+# The iteration log as a NumPy record type with the layout of gcvo_iter_log:
+# rows index like dicts (row["f"], row["T"] as a 4 x 4 pose, ...) and whole
+# columns are vectors (log["n_pairs"]), without copying the C buffer.
+LOG_DTYPE = np.dtype([("f", "<f8"), ("g", "<f8", (6,)), ("xi", "<f8", (6,)), ("xi_l1", "<f8"),
+                      ("T", "<f8", (4, 4)), ("n_pairs", "<i8"), ("n_kept", "<i8")])
+assert LOG_DTYPE.itemsize == ctypes.sizeof(gcvo_iter_log)
+
+
+def _logs_view(logs, k_max: int, n_iter) -> list:
+    """Per problem, the first n_iter[k] rows of its k_max log rows, as
+    record arrays sharing the memory of the ctypes buffer."""
+    rec = np.frombuffer(logs, dtype=LOG_DTYPE)
+    return [rec[k * k_max:k * k_max + int(n)] for k, n in enumerate(n_iter)]
 
 
 def gcvo_register(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T0, params: gcvo_solver_params,
@@ -372,7 +378,8 @@ def gcvo_register(ctx: Context, grid: Grid, src_xyz, src_cov, src_feat, T0, para
                             T0.ctypes.data, ctypes.byref(params), T.ctypes.data,
                             ctypes.cast(logs, ctypes.c_void_p) if logs is not None else None, ctypes.byref(n_iter))
     _check(s, "gcvo_register", ok=(GCVO_OK, GCVO_ERR_NOT_CONVERGED))
-    return T.reshape(4, 4), (_logs_to_list(logs, n_iter.value) if logs is not None else None), n_iter.value, s
+    return T.reshape(4, 4), (_logs_view(logs, params.k_max, [n_iter.value])[0] if logs is not None else None), \
+        n_iter.value, s
 
 
 def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solver_params, want_log: bool = False):
@@ -396,7 +403,7 @@ def gcvo_register_batched(ctx: Context, problems: list[tuple], params: gcvo_solv
                                        n_iter.ctypes.data, status.ctypes.data), "gcvo_register_batched")
     out_logs = None
     if logs is not None:
-        out_logs = [_logs_to_list(logs[k * params.k_max:(k + 1) * params.k_max], int(n_iter[k])) for k in range(n)]
+        out_logs = _logs_view(logs, params.k_max, n_iter)
     return T.reshape(n, 4, 4), out_logs, n_iter, status
 
 
@@ -427,7 +434,7 @@ def gcvo_register_clouds(ctx: Context, pairs: list[tuple], params: gcvo_kernel_p
                                       n_iter.ctypes.data, status.ctypes.data), "gcvo_register_clouds")
     out_logs = None
     if logs is not None:
-        out_logs = [_logs_to_list(logs[k * solver.k_max:(k + 1) * solver.k_max], int(n_iter[k])) for k in range(n)]
+        out_logs = _logs_view(logs, solver.k_max, n_iter)
     return T.reshape(n, 4, 4), out_logs, n_iter, status
 
 

@@ -82,3 +82,100 @@ def pose_errors(Ts, T_true):
         e.append((np.degrees(np.linalg.norm(Rotation.from_matrix(Dm[:3, :3]).as_rotvec())),
                   float(np.linalg.norm(Dm[:3, 3]))))
     return np.array(e)
+
+
+def _corner_job(args):
+    seed, b0, b1, n, max_deg, max_t = args
+    rng = np.random.default_rng([seed, b0])
+    out = []
+    for b in range(b0, b1):
+        pair = D.make_corner_pair(frame=100000 * seed + b, n_src=n, n_tgt=n)
+        G = D.perturb(rng, max_deg, max_t)
+        src = D.apply(G, pair.src_xyz.astype(np.float64)).astype(np.float32)
+        out.append((pair.tgt_xyz, pair.tgt_feat[:, 0].copy(), src, pair.src_feat[:, 0].copy(), G @ pair.T_true))
+    return out
+
+
+_FRAMES = None
+
+
+def set_frames(frames, T_true_frames):
+    """Pool initialiser: the LiDAR frames the LiDAR jobs draw from."""
+    global _FRAMES
+    _FRAMES = (frames, T_true_frames)
+
+
+def _lidar_job(args):
+    seed, b0, b1, n, max_deg, max_t = args
+    frames, T_true_frames = _FRAMES
+    rng = np.random.default_rng([seed, b0, 1])
+    out = []
+    while len(out) < b1 - b0:
+        j = int(rng.integers(0, len(frames) - 1))
+        tx, tf = D.subsample(rng, frames[j][0], frames[j][1], n)
+        sx, sf = D.subsample(rng, frames[j + 1][0], frames[j + 1][1], n)
+        if len(tx) < n or len(sx) < n:
+            continue
+        G = D.perturb(rng, max_deg, max_t)
+        sx = D.apply(G, sx.astype(np.float64)).astype(np.float32)
+        out.append((tx, tf[:, 0].copy(), sx, sf[:, 0].copy(), G @ T_true_frames[j]))
+    return out
+
+
+def mixed_pairs(frames, T_true_frames, n_pairs: int, seed: int, n: int = 4096, max_deg: float = 30.0,
+                max_t: float = 0.5, pool=None):
+    """The config-5 data: n_pairs pairs of n points, alternately a corner
+    scene and a consecutive LiDAR frame pair (frames: list of (xyz, l) with
+    the true relative poses T_true_frames) subsampled to n points, each
+    misaligned by a random motion up to max_deg / max_t.  Returns (pairs,
+    kinds) with pairs as in corner_pairs and kinds 0 (corner) / 1 (LiDAR).
+    The work runs in chunks on `pool` when given (a process pool whose
+    initialiser is set_frames(frames, T_true_frames))."""
+    n_c = (n_pairs + 1) // 2
+    n_l = n_pairs - n_c
+    cj = [(seed, b, min(b + 512, n_c), n, max_deg, max_t) for b in range(0, n_c, 512)]
+    lj = [(seed, b, min(b + 512, n_l), n, max_deg, max_t) for b in range(0, n_l, 512)]
+    if pool is not None:
+        corner = [p for c in pool.map(_corner_job, cj) for p in c]
+        lidar = [p for c in pool.map(_lidar_job, lj) for p in c]
+    else:
+        set_frames(frames, T_true_frames)
+        corner = [p for j in cj for p in _corner_job(j)]
+        lidar = [p for j in lj for p in _lidar_job(j)]
+    pairs = [None] * n_pairs
+    kinds = np.zeros(n_pairs, dtype=np.int32)
+    pairs[0::2] = corner
+    pairs[1::2] = lidar
+    kinds[1::2] = 1
+    return pairs, kinds
+
+
+def mixed_pair_chunks(n_pairs: int, seed: int, n: int = 4096, chunk: int = 512, max_deg: float = 30.0,
+                      max_t: float = 0.5, pool=None):
+    """mixed_pairs in chunks, in order: yields (pairs, kinds) of up to
+    `chunk` pairs, alternately corner and LiDAR pairs, drawn on `pool` (a
+    process pool initialised with set_frames) so that no more than a few
+    chunks are ever held on the host."""
+    jobs = []
+    for c0 in range(0, n_pairs, chunk):
+        m = min(chunk, n_pairs - c0)
+        nc = (m + 1) // 2
+        # corner and LiDAR draws numbered by their position in the whole set
+        jobs.append((("c", (seed, c0 // 2, c0 // 2 + nc, n, max_deg, max_t)),
+                     ("l", (seed, c0 // 2, c0 // 2 + m - nc, n, max_deg, max_t))))
+    flat = [j for pair in jobs for j in pair]
+    run = lambda j: _corner_job(j[1]) if j[0] == "c" else _lidar_job(j[1])
+    it = pool.imap(_run_job, flat) if pool is not None else map(run, flat)
+    for _ in jobs:
+        corner, lidar = next(it), next(it)
+        m = len(corner) + len(lidar)
+        pairs = [None] * m
+        pairs[0::2] = corner
+        pairs[1::2] = lidar
+        kinds = np.zeros(m, dtype=np.int32)
+        kinds[1::2] = 1
+        yield pairs, kinds
+
+
+def _run_job(j):
+    return _corner_job(j[1]) if j[0] == "c" else _lidar_job(j[1])

@@ -243,6 +243,38 @@ def test_register_corner_matches_oracle(env):
     assert ang_t < math.radians(0.5) and dt_t < 0.02
 
 
+def test_register_first_order_lidar_long_run_steps_match_oracle(env):
+    """G-CVO-1 for 400 iterations on a LiDAR frame pair (3000 points each),
+    checked step by step against the oracle at the GPU's own iterates (a
+    backward-error check: trajectories of a first-order method drift apart
+    by float rounding, the steps must not): f and g within 1e-5, and the
+    step length mu within 5 % of the oracle's smallest positive root of the
+    line-search cubic (Eq. 9).  Its coefficients are sums of terms up to
+    beta^4 / 24 that cancel by many orders of magnitude, so the root moves
+    by up to 2-3 % in FP32 (measured over 3000 iterations)."""
+    O, G, ctx, dev = env
+    pair = D.LidarSequence(n_frames=2).pair(0)
+    rng = np.random.default_rng(7)
+    pair.tgt_xyz, pair.tgt_feat = D.subsample(rng, pair.tgt_xyz, pair.tgt_feat, 3000)
+    pair.src_xyz, pair.src_feat = D.subsample(rng, pair.src_xyz, pair.src_feat, 3000)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0), eig_max=0.09).gpu(G, ctx, dev, G.kernel_params(eig_max=0.09))
+    K = 400
+    T, log, n_iter, st = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4),
+                                         G.solver_params(order=1, k_max=K, eps_tol=0.0, mu0=1e-10))
+    assert n_iter == K
+    for k in (0, 1, 2, 5, 10, 25, 50, 100, 200, 300, K - 1):
+        Tk = log[k]["T"]
+        o = O.evaluate(case.prob, Tk, case.kp_o)
+        assert rel_f(log[k]["f"], o.f) <= TOL, k
+        assert rel_g(log[k]["g"], o.g, o.gabs) <= TOL, k
+        c = O.linesearch_poly(case.prob, Tk, o.g, case.kp_o)
+        mu_o = O.linesearch_step(c, 1e-10)
+        mu_g = np.linalg.norm(log[k]["xi"]) / np.linalg.norm(log[k]["g"])
+        assert abs(mu_g / mu_o - 1.0) <= 5e-2, (k, mu_g, mu_o)
+    # f rises along the run (the method creeps along the street here)
+    assert log[K - 1]["f"] > 1.3 * log[0]["f"]
+
+
 def test_register_first_order_matches_oracle(env):
     """G-CVO-1: gradient step with the line search of Eq. (9).  At every GPU
     iterate the oracle's f and g agree within 1e-5 and its step within 1e-3
