@@ -77,8 +77,10 @@ typedef struct {
     double eig_max;     /* eigenvalue bound of the Remark after Eq. (7): every
                            eigenvalue of a per-point covariance is clamped to */
     double eig_ratio;   /* [eig_max / eig_ratio, eig_max]; eig_max <= 0 disables */
-    int feat_dim;       /* l: channels of the pose-invariant features, 1..3;
-                           c_ij = <l_i, l_j> (Eq. 5) */
+    int feat_dim;       /* l: channels of the pose-invariant features, 1..7
+                           (an intensity, RGB, or a label distribution over up
+                           to 7 classes as in SemanticCVO); c_ij = <l_i, l_j>
+                           (Eq. 5) */
     double cell_size;   /* target voxel edge; <= 0 picks the kernel range */
 } gcvo_kernel_params;
 
@@ -126,7 +128,7 @@ typedef struct {
 } gcvo_problem;
 
 /* Library-wide limits of this build. */
-#define GCVO_MAX_FEAT 3
+#define GCVO_MAX_FEAT 7
 #define GCVO_MAX_KNN 16
 #define GCVO_MAX_KMAX 100000
 #define GCVO_MAX_PROBLEMS 4096
@@ -325,7 +327,8 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
  * device array of 5.3 MiB in the library, reserved on every device that
  * loads the library until the process exits.  The caller passes device
  * pointers on the grid's device for every input (host pointers and
- * pointers to another device are rejected with GCVO_ERR_INVALID_ARG), the
+ * pointers to another device are rejected with GCVO_ERR_INVALID_ARG, as are
+ * grids with more than 3 feature channels), the
  * target grid (built earlier with gcvo_build_grid), the stream, and host
  * outputs.  Source points are processed in the caller's order, 8 per work
  * item.

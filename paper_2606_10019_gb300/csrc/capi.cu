@@ -168,6 +168,10 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     GCVO_TRY(ctx->src_ca.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->src_cb.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->pprob.ensure(N * sizeof(int), s));
+    if (P.feat_dim > 3) {
+        GCVO_TRY(ctx->src_fx.ensure(N * sizeof(float4), s));
+        GCVO_TRY(ctx->t_fx.ensure(N * sizeof(float4), s));
+    }
     GCVO_TRY(ctx->t_pos.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->t_ca.ensure(N * sizeof(float4), s));
     GCVO_TRY(ctx->t_cb.ensure(N * sizeof(float4), s));
@@ -196,6 +200,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sa.sca = ctx->src_ca.as<float4>();
     sa.scb = ctx->src_cb.as<float4>();
     sa.pprob = ctx->pprob.as<int>();
+    sa.sfx = P.feat_dim > 3 ? ctx->src_fx.as<float4>() : nullptr;
     sa.feat_dim = P.feat_dim;
     sa.iso = P.iso;
     GCVO_CUDA(launch_src_keys(sa, np, max_n, s));
@@ -383,6 +388,8 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     t.tca = ctx->t_ca.as<float4>();
     t.tcb = ctx->t_cb.as<float4>();
     t.tlo = exact ? ctx->t_lo.as<float4>() : nullptr;
+    t.sfx = P.feat_dim > 3 ? ctx->src_fx.as<float4>() : nullptr;
+    t.tfx = P.feat_dim > 3 ? ctx->t_fx.as<float4>() : nullptr;
     t.n = P.n_points;
     t.iso = P.iso;
     PairArgs &a = b.pa;
@@ -390,6 +397,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     a.tca = t.tca;
     a.tcb = t.tcb;
     a.tlo = t.tlo;
+    a.tfx = t.tfx;
     a.items = ctx->items.as<int>();
     a.item_prob = ctx->item_prob.as<int>();
     a.n_items = P.d_nitems;
@@ -703,6 +711,7 @@ std::vector<DevBuf *> ws_bufs(gcvo_ctx *c) {
     std::vector<DevBuf *> v = {&c->stage_xyz, &c->stage_cov, &c->small,    &c->sort_keys, &c->sort_vals,
                                &c->sort_tmp,  &c->scan_tmp,  &c->src_pos,  &c->src_ca,    &c->src_cb,
                                &c->pprob,     &c->t_pos,     &c->t_ca,     &c->t_cb,      &c->t_lo,
+                               &c->src_fx,    &c->t_fx,
                                &c->items,     &c->item_prob, &c->pack_tmp, &c->partial,   &c->partial2,
                                &c->probs,     &c->grids,     &c->evalout,  &c->logs,      &c->status_word,
                                &c->knn_retry};
@@ -730,6 +739,7 @@ std::vector<size_t> ws_sizes(int64_t N, int64_t np, int64_t rows) {
         n * sizeof(float4), n * sizeof(float4), n * sizeof(float4),     // src_pos, src_ca, src_cb
         n * sizeof(int),                                                // pprob
         n * sizeof(float4), n * sizeof(float4), n * sizeof(float4), n * sizeof(float4),   // t_pos, t_ca, t_cb, t_lo
+        n * sizeof(float4), n * sizeof(float4),                         // src_fx, t_fx
         n * sizeof(int4), n * sizeof(int),                              // items, item_prob
         5 * n64 * sizeof(int),                                          // pack_tmp
         n * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,        // partial
@@ -821,6 +831,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->sort_keys, &ctx->sort_vals, &ctx->sort_tmp, &ctx->scan_tmp, &ctx->small,
                       &ctx->stage_xyz, &ctx->stage_cov, &ctx->stage_feat, &ctx->src_pos, &ctx->src_ca,
                       &ctx->src_cb, &ctx->pprob, &ctx->t_pos, &ctx->t_ca, &ctx->t_cb, &ctx->t_lo,
+                      &ctx->src_fx, &ctx->t_fx,
                       &ctx->partial, &ctx->probs, &ctx->grids, &ctx->logs, &ctx->evalout, &ctx->status_word,
                       &ctx->items, &ctx->item_prob, &ctx->pack_tmp, &ctx->partial2};
     for (DevBuf *b : bufs) b->release();
@@ -968,6 +979,7 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid) {
     s.ca.release();
     s.cb.release();
     s.plo.release();
+    s.fx.release();
     s.orig.release();
     s.cell_start.release();
     s.hkeys.release();

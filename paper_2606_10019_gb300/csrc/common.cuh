@@ -81,6 +81,7 @@ struct GridDev {
     const float4 *ca;
     const float4 *cb;
     const float4 *plo;        // target grids: coordinate tails (x, y, z, 0)
+    const float4 *fx;         // feature channels 3..6 (when feat_dim > 3)
     const int *orig;          // original index of each sorted point
     const int *cell_start;    // n_cells + 1 offsets into the sorted points
     const unsigned long long *hkeys;  // open-addressing table of voxel keys
@@ -163,7 +164,7 @@ __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, f
 // ---------------------------------------------------------------------------
 struct GridStore {
     GridDev d{};
-    DevBuf pos, ca, cb, plo, orig, cell_start, hkeys, hval, vox_first;
+    DevBuf pos, ca, cb, plo, fx, orig, cell_start, hkeys, hval, vox_first;
 };
 
 // Build a grid from SoA inputs.  absolute: keep absolute coordinates and no
@@ -193,7 +194,8 @@ struct gcvo_ctx {
     gcvo::DevBuf sort_keys, sort_vals, sort_tmp, scan_tmp, small;
     gcvo::DevBuf stage_xyz, stage_cov, stage_feat;   // host-input staging
     gcvo::DevBuf src_pos, src_ca, src_cb, pprob;     // packed sources (sorted) and their problems
-    gcvo::DevBuf t_pos, t_ca, t_cb, t_lo;            // the same at the current pose (k_transform)
+    gcvo::DevBuf src_fx;                             // their feature channels 3..6 (feat_dim > 3)
+    gcvo::DevBuf t_pos, t_ca, t_cb, t_lo, t_fx;      // the same at the current pose (k_transform)
     gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, items, item_prob, pack_tmp;
     gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances

@@ -66,7 +66,7 @@ __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long 
 
 __global__ void k_reorder(const float *xyz, const float *cov, const float *feat, int feat_dim, int64_t n,
                           const int *vals, GridDev g, bool absolute, float4 *pos, float4 *ca, float4 *cb,
-                          float4 *plo, int *orig) {
+                          float4 *plo, float4 *fx, int *orig) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int j = vals[i];
@@ -78,8 +78,9 @@ __global__ void k_reorder(const float *xyz, const float *cov, const float *feat,
         if (!absolute) t[a] = (float)(d - (double)p[a]);
     }
     if (plo) plo[i] = make_float4(t[0], t[1], t[2], 0.f);
-    float l[3] = {0.f, 0.f, 0.f};
-    for (int q = 0; q < feat_dim && feat; ++q) l[q] = feat[q * n + j];
+    float l[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < feat_dim && q < 7 && feat; ++q) l[q] = feat[q * n + j];
+    if (fx) fx[i] = make_float4(l[3], l[4], l[5], l[6]);
     float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (cov)
         for (int q = 0; q < 6; ++q) c[q] = cov[q * n + j];
@@ -195,6 +196,8 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(out.ca.ensure(n * sizeof(float4), s));
     GCVO_TRY(out.cb.ensure(n * sizeof(float4), s));
     if (!absolute) GCVO_TRY(out.plo.ensure(n * sizeof(float4), s));
+    const bool with_fx = !absolute && kp.feat_dim > 3;
+    if (with_fx) GCVO_TRY(out.fx.ensure(n * sizeof(float4), s));
     GCVO_TRY(out.orig.ensure(n * sizeof(int), s));
     GCVO_TRY(out.cell_start.ensure((n_cells + 1) * sizeof(int), s));
     GCVO_TRY(out.hkeys.ensure(H * sizeof(unsigned long long), s));
@@ -205,7 +208,8 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
                                    out.hval.as<int>(), H - 1);
     k_reorder<<<blocks, 256, 0, s>>>(xyz, kp.kernel_mode == 0 ? cov : nullptr, feat, kp.feat_dim, n, vals, g,
                                      absolute, out.pos.as<float4>(), out.ca.as<float4>(), out.cb.as<float4>(),
-                                     absolute ? nullptr : out.plo.as<float4>(), out.orig.as<int>());
+                                     absolute ? nullptr : out.plo.as<float4>(), with_fx ? out.fx.as<float4>() : nullptr,
+                                     out.orig.as<int>());
     count_launches(3);
     GCVO_CUDA(cudaGetLastError());
     if (!absolute) {
@@ -221,6 +225,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.ca = out.ca.as<float4>();
     g.cb = out.cb.as<float4>();
     g.plo = absolute ? nullptr : out.plo.as<float4>();
+    g.fx = with_fx ? out.fx.as<float4>() : nullptr;
     g.orig = out.orig.as<int>();
     g.cell_start = out.cell_start.as<int>();
     g.hkeys = out.hkeys.as<unsigned long long>();

@@ -138,6 +138,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
                                         double *f, double g[6], double H[36]) {
     if (!target || !src_xyz || !src_feat || !T || !f || !g || !H) return GCVO_ERR_INVALID_ARG;
     if (target->kp.kernel_mode == 0 && !src_cov) return GCVO_ERR_INVALID_ARG;
+    if (target->kp.feat_dim > 3) return GCVO_ERR_INVALID_ARG;   // the scratch holds 3 feature channels
     if (n_src < 1) return GCVO_ERR_INVALID_ARG;
     if (n_src > NA_MAX_SRC) return GCVO_ERR_CAPACITY;   // beyond the static scratch
     for (int k = 0; k < 16; ++k)
@@ -209,6 +210,8 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     ta.sca = ta.tca = reinterpret_cast<float4 *>(base + NA_SCA);
     ta.scb = ta.tcb = reinterpret_cast<float4 *>(base + NA_SCB);
     ta.tlo = nullptr;
+    ta.sfx = nullptr;
+    ta.tfx = nullptr;
     ta.pprob = nullptr;
     ta.probs = fa.probs;
     ta.n = n;
@@ -219,6 +222,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.tca = ta.tca;
     pa.tcb = ta.tcb;
     pa.tlo = nullptr;
+    pa.tfx = nullptr;
     pa.items = reinterpret_cast<const int *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
     pa.n_items = words + 1;

@@ -672,6 +672,11 @@ __global__ void k_src_pack(SrcArgs a, const unsigned long long *keys, int64_t n)
     a.spos[i] = make_float4(x, y, z, f0);
     a.sca[i] = make_float4(s6[0], s6[1], s6[2], s6[3]);
     a.scb[i] = make_float4(s6[4], s6[5], f1, f2);
+    if (a.sfx) {
+        float fx[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 3; q < a.feat_dim && q < 7; ++q) fx[q - 3] = d.feat[q * d.n + li];
+        a.sfx[i] = make_float4(fx[0], fx[1], fx[2], fx[3]);
+    }
     a.pprob[i] = (int)(keys[i] >> 30);
 }
 
@@ -744,6 +749,10 @@ __global__ void k_transform(TransformArgs a) {
         }
         a.tca[i] = make_float4(q[0], q[1], q[2], q[3]);
         a.tcb[i] = make_float4(q[4], q[5], sg * zb.z, sg * zb.w);
+        if (a.tfx) {
+            const float4 f = a.sfx[i];
+            a.tfx[i] = make_float4(sg * f.x, sg * f.y, sg * f.z, sg * f.w);
+        }
     }
 }
 

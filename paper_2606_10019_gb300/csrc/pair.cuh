@@ -11,7 +11,7 @@ namespace gcvo {
 // points PAIR_WCAP at a time in its own shared memory.
 constexpr int PAIR_WARPS = 4;
 constexpr int PAIR_WCAP = 160;
-constexpr int PAIR_GRAB = 16;   // work items a warp takes per atomic
+constexpr int PAIR_GRAB = 2;    // work items a warp takes per atomic (larger grabs of heavy items left long tails)
 constexpr int PAIR_SLOTS = 28;         // f, g (6), M (21) per sub-tile
 constexpr int PAIR_SLOTS_EXACT = 46;   // f, g, Q - M (21), C (9), S_B (9): G-CVO-E
 
@@ -58,9 +58,10 @@ struct EvalOut {
 // k_transform once per iteration (sorted order, one record per point):
 //   tpos = (p_hi, sigma^2 l0), tca = (S'xx, S'xy, S'xz, S'yy),
 //   tcb = (S'yz, S'zz, sigma^2 l1, sigma^2 l2), tlo = (p_lo, 0),
+//   tfx = sigma^2 (l3, l4, l5, l6) when there are more than 3 feature channels,
 // with p = R^T (z - t) - o = p_hi + p_lo (double-float) and S' = R^T S R.
 struct PairArgs {
-    const float4 *tpos, *tca, *tcb, *tlo;
+    const float4 *tpos, *tca, *tcb, *tlo, *tfx;
     const int *items;          // per item (sub-tile): first point << 6 | points
     const int *item_prob;
     const int *n_items;
@@ -102,6 +103,7 @@ struct SrcArgs {
     int *lam_enc;
     unsigned *status_word;
     float4 *spos, *sca, *scb;
+    float4 *sfx;               // feature channels 3..6 (null when feat_dim <= 3)
     int *pprob;                // problem of each sorted point
     int feat_dim;
     int iso;
@@ -111,9 +113,11 @@ struct SrcArgs {
 // into the target grid's frame (k_transform).
 struct TransformArgs {
     const float4 *spos, *sca, *scb;   // packed source records, sorted (caller frame)
+    const float4 *sfx;                // feature channels 3..6 (may be null)
     const int *pprob;                 // problem of each point (null: all problem 0)
     const ProbDev *probs;
     float4 *tpos, *tca, *tcb, *tlo;   // outputs (tlo may be null)
+    float4 *tfx;                      // sigma^2 sfx (null when sfx is)
     int64_t n;
     int iso;
 };

@@ -7,8 +7,8 @@
 // sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho
 // (or 2 rho, the coarser cut the autotuner may pick).  Every warp works alone
 // on one sub-tile at a time (a work item); it takes up to PAIR_GRAB items per
-// atomic on the global counter, so the counter is touched rarely, and no warp
-// waits for another.
+// atomic on the global counter (two: a larger grab of heavy items leaves a
+// few warps working long after the rest), and no warp waits for another.
 //  1. Every point is read in the target grid's frame at the current pose
 //     (Algorithm 1: p_j = R^T (z_j - t) - o and Sigma'_j = R^T Sigma_j R),
 //     as k_transform (pair.cu) wrote it for this iteration.
@@ -36,6 +36,9 @@
 //     one (hi, lo) partial per sub-tile for the FP64 finalize.
 // With no cutoff (dense mode) rho and the cutoff are infinite and every
 // staged target meets every point: the same code visits all pairs.
+// Features (c_ij = <l_i, l_j>, Eq. 5): channels 0..2 ride in pos.w, cb.z and
+// cb.w; channels 3..6 (FD = 7: label distributions over up to 7 classes,
+// SemanticCVO) in one more float4 stream staged beside the others.
 // The G-CVO-E pass (PAIR_EXACT) visits the same pairs and adds the sums of
 // the exact directional derivative of g (pair_exact); its 46 values per
 // sub-tile go to two partial rows.  The exact derivative is far more
@@ -52,17 +55,19 @@ namespace {
 
 static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
+static_assert(PAIR_WARPS * (PAIR_WCAP * 80 + PAIR_WCAP * 2 + 64) <= 227 * 1024, "the largest block stage fits");
 static_assert(PAIR_SLOTS_EXACT * 33 * 4 <= PAIR_WCAP * 48, "exact epilogue transpose fits in pos, ca, cb");
 
-// Per warp: staged target points (with their coordinate tails when LO),
-// the list of those near the sub-tile, and the mbarrier the bulk copies
-// complete on.
-template <bool LO>
+// Per warp: staged target points (with their coordinate tails when LO and
+// their feature channels 3..6 when FX), the list of those near the
+// sub-tile, and the mbarrier the bulk copies complete on.
+template <bool LO, bool FX>
 struct __align__(16) WarpStage {
     float4 pos[PAIR_WCAP];
     float4 ca[PAIR_WCAP];
     float4 cb[PAIR_WCAP];
     float4 lo[LO ? PAIR_WCAP : 1];
+    float4 fx[FX ? PAIR_WCAP : 1];   // feature channels 3..6
     unsigned short list[PAIR_WCAP];
     uint64_t bar;
 };
@@ -70,13 +75,15 @@ struct __align__(16) WarpStage {
 // One anisotropic pair (Eq. 7), r = x_i - p_j, into the lane sums t[10].
 template <int FD>
 __device__ __forceinline__ void pair_aniso(const float r0, const float r1, const float r2, const float4 x,
-                                           const float4 ca, const float4 cbv, float l0, float l1, float l2,
+                                           const float4 ca, const float4 cbv, const float4 xf, const float4 lf,
+                                           float l0, float l1, float l2,
                                            const float q[6], float rho2, float c2, bool act, float *t, int &n_pairs,
                                            int &n_kept) {
     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
     const bool in = act && rr <= rho2;
     float cij = x.w * l0;
     if (FD > 1) cij += cbv.z * l1 + cbv.w * l2;
+    if (FD > 3) cij += xf.x * lf.x + xf.y * lf.y + xf.z * lf.z + xf.w * lf.w;
     const float s00 = ca.x + q[0], s01 = ca.y + q[1], s02 = ca.z + q[2];
     const float s11 = ca.w + q[3], s12 = cbv.x + q[4], s22 = cbv.y + q[5];
     const float c00 = s11 * s22 - s12 * s12;
@@ -93,11 +100,11 @@ __device__ __forceinline__ void pair_aniso(const float r0, const float r1, const
     const float rdet = rcp_approx(det);
     const float d2 = qf * rdet;
     const bool keep = in && d2 <= c2;
-    const float wgt = cij * ex2_approx(d2 * NEG_HALF_LOG2E);
-    const float wd = keep ? wgt * rdet : 0.f;
+    const float wk = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
+    const float wd = wk * rdet;
     n_pairs += in;
     n_kept += keep;
-    t[0] += keep ? wgt : 0.f;
+    t[0] += wk;
     t[1] += wd * y0;
     t[2] += wd * y1;
     t[3] += wd * y2;
@@ -119,13 +126,15 @@ __device__ __forceinline__ void pair_aniso(const float r0, const float r1, const
 // -2 u . omega (Sec. 3.4, the four terms of the derivative of Eq. 8).
 template <int FD>
 __device__ __forceinline__ void pair_exact(const float r0, const float r1, const float r2, const float4 x,
-                                           const float4 ca, const float4 cbv, float l0, float l1, float l2,
+                                           const float4 ca, const float4 cbv, const float4 xf, const float4 lf,
+                                           float l0, float l1, float l2,
                                            const float q[6], float rho2, float c2, bool act, float *t, int &n_pairs,
                                            int &n_kept) {
     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
     const bool in = act && rr <= rho2;
     float cij = x.w * l0;
     if (FD > 1) cij += cbv.z * l1 + cbv.w * l2;
+    if (FD > 3) cij += xf.x * lf.x + xf.y * lf.y + xf.z * lf.z + xf.w * lf.w;
     const float s00 = ca.x + q[0], s01 = ca.y + q[1], s02 = ca.z + q[2];
     const float s11 = ca.w + q[3], s12 = cbv.x + q[4], s22 = cbv.y + q[5];
     const float c00 = s11 * s22 - s12 * s12;
@@ -251,16 +260,19 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
 template <int MODE, bool ISO, int FD, int SUB>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
     static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
+    static_assert(FD == 1 || FD == 3 || FD == 7, "1, up to 3 or up to 7 feature channels");
     constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : MODE == PAIR_EXACT ? 25 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? PAIR_SLOTS : MODE == PAIR_EXACT ? PAIR_SLOTS_EXACT : 5;
     constexpr bool LO = MODE == PAIR_EXACT;
-    __shared__ WarpStage<LO> stage[PAIR_WARPS];
+    constexpr bool FX = FD > 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];   // PAIR_WARPS stages
+    WarpStage<LO, FX> *stage = reinterpret_cast<WarpStage<LO, FX> *>(smem_raw);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    WarpStage<LO> &S = stage[w];
+    WarpStage<LO, FX> &S = stage[w];
     if (lane == 0) mbar_init(&S.bar, 1);
     __syncwarp();
     unsigned parity = 0;
@@ -322,6 +334,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
             qv[2] = A4.z;
             qv[3] = A4.w;
         }
+        float4 lf = make_float4(0.f, 0.f, 0.f, 0.f);   // sigma^2 l3..l6
+        if (FX) lf = a.tfx[jj];
         float plx = 0.f, ply = 0.f, plz = 0.f;   // tail of p (G-CVO-E pass)
         if (LO) {
             const float4 L4 = a.tlo[jj];
@@ -422,7 +436,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 // ---- stage the chunk [base, base + m) (bulk copies)
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (LO ? 64u : 48u));
+                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (48u + (LO ? 16u : 0u) + (FX ? 16u : 0u)));
                 __syncwarp();
                 {
                     const int s0 = max(off, base), s1 = min(off + rl, base + m);
@@ -433,6 +447,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         bulk_g2s(S.ca + dst, G->ca + src, bytes, &S.bar);
                         bulk_g2s(S.cb + dst, G->cb + src, bytes, &S.bar);
                         if (LO) bulk_g2s(S.lo + dst, G->plo + src, bytes, &S.bar);
+                        if (FX) bulk_g2s(S.fx + dst, G->fx + src, bytes, &S.bar);
                     }
                 }
                 {
@@ -483,14 +498,15 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         r1 += xl.y - ply;
                         r2 += xl.z - plz;
                     }
+                    const float4 xf = FX ? S.fx[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE == PAIR_EVAL && !ISO) {
-                        pair_aniso<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
-                                       n_kept);
+                        pair_aniso<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], xf, lf, l0, l1, l2, qv, rho2, c2, act, t,
+                                       n_pairs, n_kept);
                         continue;
                     }
                     if constexpr (MODE == PAIR_EXACT && !ISO) {
-                        pair_exact<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], l0, l1, l2, qv, rho2, c2, act, t, n_pairs,
-                                       n_kept);
+                        pair_exact<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], xf, lf, l0, l1, l2, qv, rho2, c2, act, t,
+                                       n_pairs, n_kept);
                         continue;
                     }
                     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
@@ -500,6 +516,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         const float4 cbv = S.cb[k];
                         cij += cbv.z * l1 + cbv.w * l2;
                     }
+                    if (FX) cij += xf.x * lf.x + xf.y * lf.y + xf.z * lf.z + xf.w * lf.w;
                     if (ISO) {
                         const float d2 = rr * iso_inv;
                         const bool keep = in && d2 <= c2;
@@ -745,9 +762,25 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of one block (its warps' stages), with the opt-in
+// above the 48 KB default made once per kernel instance.
+template <int MODE, int FD>
+constexpr size_t tile_smem_bytes() {
+    return PAIR_WARPS * sizeof(WarpStage<MODE == PAIR_EXACT, (FD > 3)>);
+}
+
+template <int MODE, bool ISO, int FD, int SUB>
+static cudaError_t tile_smem_optin() {
+    static const cudaError_t once = cudaFuncSetAttribute(
+        k_tile<MODE, ISO, FD, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes<MODE, FD>());
+    return once;
+}
+
 template <int MODE, bool ISO, int FD, int SUB>
 static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
-    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, 0, s>>>(a);
+    const cudaError_t e = tile_smem_optin<MODE, ISO, FD, SUB>();
+    if (e != cudaSuccess) return e;
+    k_tile<MODE, ISO, FD, SUB><<<grid, PAIR_WARPS * 32, tile_smem_bytes<MODE, FD>(), s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -755,25 +788,30 @@ static cudaError_t launch_tile_t(const PairArgs &a, int grid, cudaStream_t s) {
 template <int MODE, bool ISO, int FD, int SUB>
 static int occupancy_t() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32, 0);
+    if (tile_smem_optin<MODE, ISO, FD, SUB>() != cudaSuccess) return 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<MODE, ISO, FD, SUB>, PAIR_WARPS * 32,
+                                                  tile_smem_bytes<MODE, FD>());
     return nb;
 }
 
 // All three passes in all four schedules (the line-search pass of G-CVO-1
 // and the G-CVO-E pass run over the same items as the evaluation pass).
-#define PAIR_VARIANTS_M(X, M)                                                                 \
-    X(M, false, 1, 4) X(M, false, 3, 4) X(M, true, 1, 4) X(M, true, 3, 4) X(M, false, 1, 8)    \
-    X(M, false, 3, 8) X(M, true, 1, 8) X(M, true, 3, 8) X(M, false, 1, 16) X(M, false, 3, 16) \
-    X(M, true, 1, 16) X(M, true, 3, 16) X(M, false, 1, 32) X(M, false, 3, 32) X(M, true, 1, 32) X(M, true, 3, 32)
+#define PAIR_VARIANTS_U(X, M, U) \
+    X(M, false, 1, U) X(M, false, 3, U) X(M, false, 7, U) X(M, true, 1, U) X(M, true, 3, U) X(M, true, 7, U)
+#define PAIR_VARIANTS_M(X, M) \
+    PAIR_VARIANTS_U(X, M, 4) PAIR_VARIANTS_U(X, M, 8) PAIR_VARIANTS_U(X, M, 16) PAIR_VARIANTS_U(X, M, 32)
 #define PAIR_VARIANTS(X) \
     PAIR_VARIANTS_M(X, PAIR_EVAL) PAIR_VARIANTS_M(X, PAIR_LINESEARCH) PAIR_VARIANTS_M(X, PAIR_EXACT)
 
 int pair_sub_for(int, int sub) { return sub == 4 || sub == 16 || sub == 32 ? sub : 8; }
 
+// The kernel instance of a feature count: 1, up to 3, or up to 7 channels.
+static int fd_class(int fd) { return fd <= 1 ? 1 : fd <= 3 ? 3 : 7; }
+
 int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
     sub = pair_sub_for(mode, sub);
 #define OCC(M, I, F, U) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return occupancy_t<M, I, F, U>();
+    if (mode == M && iso == I && fd_class(fd) == F && sub == U) return occupancy_t<M, I, F, U>();
     PAIR_VARIANTS(OCC)
 #undef OCC
     return 1;
@@ -782,7 +820,7 @@ int pair_blocks_per_sm(int mode, bool iso, int fd, int sub) {
 cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, int grid, cudaStream_t s) {
     sub = pair_sub_for(mode, sub);
 #define L(M, I, F, U) \
-    if (mode == M && iso == I && (fd > 1) == (F > 1) && sub == U) return launch_tile_t<M, I, F, U>(a, grid, s);
+    if (mode == M && iso == I && fd_class(fd) == F && sub == U) return launch_tile_t<M, I, F, U>(a, grid, s);
     PAIR_VARIANTS(L)
 #undef L
     return cudaErrorInvalidValue;

@@ -163,6 +163,34 @@ def test_eval_rgb_features_and_sigma2(env):
         _check_eval(O, G, ctx, case, T)
 
 
+@pytest.mark.parametrize("fd", [5, 7])
+def test_eval_label_features(env, fd):
+    """Label distributions over fd classes (SemanticCVO, Remark 3): c_ij =
+    <l_i, l_j> over fd channels, carried by the kernel in the point records
+    (channels 0..2) and one more staged stream (3..6); anisotropic and
+    isotropic, two schedules, and registration to the oracle's pose."""
+    O, G, ctx, dev = env
+    pair = D.make_corner_pair(n_src=900, n_tgt=1000, frame=6)
+    rng = np.random.default_rng(fd)
+    pair.tgt_feat = rng.dirichlet(np.ones(fd), size=1000).astype(np.float32)
+    pair.src_feat = rng.dirichlet(np.ones(fd), size=900).astype(np.float32)
+    case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01, feat_dim=fd))
+    iso = Case(O, pair, O.KernelParams(kernel_mode=1, iso_ell=0.08, cutoff=3.0), iso=True)
+    iso.gpu(G, ctx, dev, G.kernel_params(kernel_mode=1, iso_ell=0.08, feat_dim=fd))
+    try:
+        for sub in (8, 32):
+            G.gcvo_pair_schedule(ctx, sub)
+            for c in (case, iso):
+                for T in _poses(pair):
+                    _check_eval(O, G, ctx, c, T)
+    finally:
+        G.gcvo_pair_schedule(ctx, 0)
+    T, log, n_iter, st = G.gcvo_register(ctx, case.grid, *case.src, np.eye(4), G.solver_params(k_max=60, eps_tol=1e-7))
+    ref = O.register(case.prob, np.eye(4), case.kp_o, order=2, k_max=60, eps_tol=1e-7)
+    ang, dt = O.pose_error(T, ref.T)
+    assert ang <= POSE_TOL and dt <= POSE_TOL, (ang, dt)
+
+
 def test_eval_far_from_origin(env):
     """The whole scene 300 m from the origin: the grid-origin shift and its
     exact FP64 change of frame keep g and H in the caller's frame."""

@@ -603,3 +603,47 @@ def test_exact_hessian_c_loops_equal_numpy(oracle_mod, mode):
         a = O.grad_derivative(prob, T, kp)
         b = O.grad_derivative_c(prob, T, kp)
         assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_label_features_are_a_sum_over_classes(oracle_mod):
+    """Eq. (5) with label features (SemanticCVO, Remark 3): c_ij = <l_i, l_j>
+    over l channels.  With one-hot labels over 6 classes, c_ij is 1 for
+    pairs of the same class and 0 otherwise, so f, g and M equal the sums of
+    the one-channel problems restricted to each class's points (a plausible
+    slip -- reading one channel, or the channels of the wrong point --
+    breaks this)."""
+    O = oracle_mod
+    rng = np.random.default_rng(11)
+    base = _small_problem(O, n_t=90, n_s=80, seed=5)
+    L = 6
+    lt = rng.integers(0, L, size=90)
+    ls = rng.integers(0, L, size=80)
+    onehot = lambda lab: np.eye(L)[lab]
+    prob = O.Problem.make(base.tgt, base.tgt_cov, onehot(lt), base.src, base.src_cov, onehot(ls))
+    T = D.rigid(_rand_rot(rng, 4.0), rng.normal(size=3) * 0.02)
+    kp = O.KernelParams(cutoff=3.0)
+    full = O.evaluate(prob, T, kp)
+    f = 0.0
+    g = np.zeros(6)
+    M = np.zeros((6, 6))
+    for c in range(L):
+        it, js = lt == c, ls == c
+        if not it.any() or not js.any():
+            continue
+        sub = O.Problem.make(base.tgt[it], base.tgt_cov[it], np.ones((it.sum(), 1)), base.src[js], base.src_cov[js],
+                             np.ones((js.sum(), 1)))
+        r = O.evaluate(sub, T, kp)
+        f += r.f
+        g += r.g
+        M += r.M
+    assert full.f == pytest.approx(f, rel=1e-12)
+    assert np.allclose(full.g, g, rtol=1e-11, atol=1e-12 * np.abs(g).max())
+    assert np.allclose(full.M, M, rtol=1e-11, atol=1e-12 * np.abs(M).max())
+    # soft labels: the channels add, c_ij of the sum is the sum of the c_ij
+    pt = rng.dirichlet(np.ones(L), size=90)
+    ps = rng.dirichlet(np.ones(L), size=80)
+    soft = O.evaluate(O.Problem.make(base.tgt, base.tgt_cov, pt, base.src, base.src_cov, ps), T, kp)
+    parts = [O.evaluate(O.Problem.make(base.tgt, base.tgt_cov, pt[:, [c]], base.src, base.src_cov, ps[:, [c]]), T, kp)
+             for c in range(L)]
+    assert soft.f == pytest.approx(sum(p.f for p in parts), rel=1e-12)
+    assert np.allclose(soft.g, sum(p.g for p in parts), rtol=1e-11, atol=1e-12 * np.abs(soft.g).max())
