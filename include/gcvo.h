@@ -169,12 +169,14 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx);
  * the caller and kept alive until the workspace is replaced, removed or the
  * context destroyed) for the same limits; from then on gcvo_eval,
  * gcvo_eval_exact, gcvo_register, gcvo_register_batched,
- * gcvo_estimate_covariances and gcvo_build_grid / gcvo_rebuild_grid make no
+ * gcvo_estimate_covariances, gcvo_estimate_covariances_batched (all its
+ * clouds together count as its points, and it takes at most
+ * 2 x max_problems clouds) and gcvo_build_grid / gcvo_rebuild_grid make no
  * device allocation for their scratch (a grid still owns its own storage),
  * and a call beyond the limits returns GCVO_ERR_WORKSPACE.  The calls that
- * work on several clouds concurrently (the *_batched covariance and grid
- * calls, gcvo_register_clouds) use internal child contexts that allocate
- * their own scratch.  dev_ptr = NULL returns the context to library-owned
+ * build several grids concurrently (gcvo_build_grids_batched,
+ * gcvo_register_clouds) use internal child contexts that allocate their own
+ * scratch.  dev_ptr = NULL returns the context to library-owned
  * scratch.  gcvo_set_workspace synchronises the stream and may allocate
  * the context's small pinned host buffer.  The paper has no counterpart:
  * this is the memory ownership of the boundary. */
@@ -188,7 +190,8 @@ gcvo_status gcvo_set_workspace(gcvo_ctx *ctx, void *dev_ptr, size_t bytes, int64
  * nearest points (the point itself included, ties broken by lower index),
  * then each eigenvalue is clamped to [eig_max/eig_ratio, eig_max].
  * xyz: 3 x n input; cov_out: 6 x n output, device memory, caller-owned.
- * Requires n >= knn.  Stream-ordered; does not synchronise. */
+ * Requires n >= knn.  Synchronises the stream (the search reads back how
+ * many points need the coarse second pass, and its status). */
 gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n,
                                       const gcvo_kernel_params *params, float *cov_out);
 
@@ -217,10 +220,14 @@ gcvo_status gcvo_grid_destroy(gcvo_grid *grid);
 
 /* gcvo_estimate_covariances for n_clouds clouds in one call: cloud k has
  * n[k] points at xyz[k] (3 x n[k]) and its covariances go to cov_out[k]
- * (6 x n[k]); all device memory.  The clouds are processed concurrently on
- * the context's internal streams (one host thread each), after the work
- * already queued on the context's stream, which then waits for them.  The
- * results equal those of one call per cloud.  Returns the first failure. */
+ * (6 x n[k]); all device memory.  All clouds share one set of launches on
+ * the context's stream: their points are gathered into one array, every
+ * cloud gets its own voxel box and size, and one sort and one hash table
+ * (voxel keys offset per cloud) serve the batch, so the cost no longer
+ * grows with the number of clouds beyond their points.  The results equal
+ * those of one call per cloud, bit for bit (the neighbour lists do not
+ * depend on the voxel grid).  Synchronises the stream; a failure (a
+ * non-finite coordinate in any cloud) fails the whole call. */
 gcvo_status gcvo_estimate_covariances_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
                                               const int64_t *n, const gcvo_kernel_params *params,
                                               float *const *cov_out);

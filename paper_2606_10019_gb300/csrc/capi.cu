@@ -714,9 +714,9 @@ std::vector<DevBuf *> ws_bufs(gcvo_ctx *c) {
                                &c->src_fx,    &c->t_fx,
                                &c->items,     &c->item_prob, &c->pack_tmp, &c->partial,   &c->partial2,
                                &c->probs,     &c->grids,     &c->evalout,  &c->logs,      &c->status_word,
-                               &c->knn_retry};
+                               &c->knn_retry,  &c->knn_meta,  &c->knn_grid.ca};
     for (GridStore *g : {&c->knn_grid, &c->knn_grid2})
-        for (DevBuf *b : {&g->pos, &g->ca, &g->cb, &g->orig, &g->cell_start, &g->hkeys, &g->hval}) v.push_back(b);
+        for (DevBuf *b : {&g->pos, &g->orig, &g->cell_start, &g->hkeys, &g->hval}) v.push_back(b);
     return v;
 }
 
@@ -747,10 +747,12 @@ std::vector<size_t> ws_sizes(int64_t N, int64_t np, int64_t rows) {
         np * sizeof(ProbDev), np * sizeof(GridDev), np * sizeof(EvalOut) + 256,
         (size_t)std::max<int64_t>(rows, 1) * sizeof(gcvo_iter_log),     // logs
         256,                                                            // status_word
-        n * sizeof(int) + 256};                                         // knn_retry
+        2 * n * sizeof(int) + 256,                                      // knn_retry: two point lists
+        knn_meta_bytes((int64_t)n, (int)std::min<int64_t>(2 * np, (int64_t)n)),   // knn_meta
+        n * sizeof(float4)};                                            // knn_grid.ca: gathered points
     for (int g = 0; g < 2; ++g)
-        for (size_t b : {n * sizeof(float4), n * sizeof(float4), n * sizeof(float4), n * sizeof(int),
-                         (n + 1) * sizeof(int), H * sizeof(unsigned long long), H * sizeof(int)})
+        for (size_t b : {n * sizeof(float4), n * sizeof(int), (n + 1) * sizeof(int), H * sizeof(unsigned long long),
+                         H * sizeof(int)})
             v.push_back(b);
     return v;
 }
@@ -841,6 +843,7 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
         for (DevBuf *b : kb) b->release();
     }
     ctx->knn_retry.release();
+    ctx->knn_meta.release();
     ctx->clouds_stage.release();
     ctx->clouds_cov.release();
     for (gcvo_grid *g : ctx->clouds_grids)
@@ -917,7 +920,8 @@ gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n
         GCVO_TRY(ctx->stage_cov.ensure(6 * (size_t)n * sizeof(float), ctx->stream));
         dcov = ctx->stage_cov.as<float>();
     }
-    GCVO_TRY(knn_covariances(ctx, dx, n, *params, dcov));
+    const KnnJob job{dx, dcov, n, params};
+    GCVO_TRY(knn_covariances(ctx, 1, &job));
     if (host_out) {
         GCVO_CUDA(cudaMemcpyAsync(cov_out, dcov, 6 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
         GCVO_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1092,10 +1096,16 @@ gcvo_status gcvo_estimate_covariances_batched(gcvo_ctx *ctx, int n_clouds, const
     for (int k = 0; k < n_clouds; ++k)
         if (!xyz[k] || !cov_out[k] || !is_device_ptr(xyz[k]) || !is_device_ptr(cov_out[k]))
             return GCVO_ERR_INVALID_ARG;
+    if (params->knn < 2 || params->knn > GCVO_MAX_KNN) return GCVO_ERR_INVALID_ARG;
+    if (params->eig_max > 0 && !(params->eig_ratio >= 1.0)) return GCVO_ERR_INVALID_ARG;
+    if (!(params->cutoff >= 0)) return GCVO_ERR_INVALID_ARG;
+    std::vector<KnnJob> jobs(n_clouds);
+    for (int k = 0; k < n_clouds; ++k) {
+        if (n[k] < params->knn || n[k] > (1 << 28)) return GCVO_ERR_INVALID_ARG;
+        jobs[k] = KnnJob{xyz[k], cov_out[k], n[k], params};
+    }
     GCVO_CUDA(cudaSetDevice(ctx->device));
-    return run_lanes(ctx, n_clouds, [&](gcvo_ctx *c, int k) {
-        return gcvo_estimate_covariances(c, xyz[k], n[k], params, cov_out[k]);
-    });
+    return knn_covariances(ctx, n_clouds, jobs.data());
 }
 
 gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
@@ -1167,10 +1177,16 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
             GCVO_CUDA(cudaEventCreate(&e));
         }
     if (ph[0]) GCVO_CUDA(cudaEventRecord(ph[0], s));
-    // Eq. (7b) and the eigenvalue bound for every cloud, concurrently
-    GCVO_TRY(run_lanes(ctx, nc, [&](gcvo_ctx *c, int k) {
-        return gcvo_estimate_covariances(c, dx[k], n[k], kp[k / 2], cov + cov_off[k]);
-    }));
+    // Eq. (7b) and the eigenvalue bound for every cloud, in one batch
+    {
+        std::vector<KnnJob> jobs(nc);
+        for (int c = 0; c < nc; ++c) {
+            const gcvo_kernel_params *p = kp[c / 2];
+            if (p->eig_max > 0 && !(p->eig_ratio >= 1.0)) return GCVO_ERR_INVALID_ARG;
+            jobs[c] = KnnJob{dx[c], cov + cov_off[c], n[c], p};
+        }
+        GCVO_TRY(knn_covariances(ctx, nc, jobs.data()));
+    }
     if (ph[1]) GCVO_CUDA(cudaEventRecord(ph[1], s));
     // the target grids, kept by the context and rebuilt in place next call
     if ((int)ctx->clouds_grids.size() < n_pairs) ctx->clouds_grids.resize(n_pairs, nullptr);

@@ -88,6 +88,7 @@ struct GridDev {
     const int *hval;          // voxel index of each table slot
     const int *vox_first;     // target grids: first sorted point of every voxel, dense (+1 entry)
     unsigned long long hmask; // table size - 1 (power of two)
+    unsigned long long key_base;   // batched kNN grids: offset of this cloud's voxel keys (0 otherwise)
     double origin[3];         // o (target grid) or 0 (kNN grid), double
     float corner[3];          // lowest voxel corner, in the coordinates of pos
     float h, inv_h;
@@ -173,8 +174,17 @@ struct GridStore {
 gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
                              const gcvo_kernel_params &kp, bool absolute, double cell, GridStore &out);
 
-gcvo_status knn_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n, const gcvo_kernel_params &kp,
-                            float *cov_out);
+// kNN covariances of a batch of clouds in one set of launches: cloud k has
+// n[k] points at xyz[k] (3 x n SoA, device) and its own parameters kp[k];
+// Sigma goes to cov[k] (6 x n SoA, device).
+struct KnnJob {
+    const float *xyz;
+    float *cov;
+    int64_t n;
+    const gcvo_kernel_params *kp;
+};
+gcvo_status knn_covariances(gcvo_ctx *ctx, int n_clouds, const KnnJob *jobs);
+size_t knn_meta_bytes(int64_t n_points, int n_clouds);
 
 }  // namespace gcvo
 
@@ -199,6 +209,7 @@ struct gcvo_ctx {
     gcvo::DevBuf partial, probs, grids, logs, evalout, status_word, items, item_prob, pack_tmp;
     gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
+    gcvo::DevBuf knn_meta;                           // its per-cloud descriptors and grids
     // gcvo_register_clouds: staged host clouds, covariances and target grids
     gcvo::DevBuf clouds_stage, clouds_cov;
     std::vector<gcvo_grid *> clouds_grids;

@@ -48,11 +48,68 @@ __device__ inline void jacobi3(double a[3][3], double w[3], double V[3][3]) {
     for (int k = 0; k < 3; ++k) w[k] = a[k][k];
 }
 
+// One cloud of a batched covariance call (device copy).
+struct KnnCloud {
+    const float *xyz;     // 3 x n SoA
+    float *cov;           // 6 x n SoA output
+    int64_t n, off;       // points; index of the first one in the gathered array
+    double eig_max, eig_ratio;
+    double cell0;         // search voxel from the kernel range; 0: from the box
+    int knn;
+    int pad;
+};
+
+// Cloud of a gathered or sorted point: its index is carried in w.
+__device__ __forceinline__ int cloud_of(float4 p) { return __float_as_int(p.w); }
+
+// The nearest points found so far, in DESCENDING order of (squared
+// distance, original index): slot 0 holds the knn-th nearest, the pruning
+// bound, and slots knn .. KNN_MAX-1 are unused.  Every access is to a slot
+// fixed at compile time (the loops over slots are unrolled, with knn as a
+// predicate), so the list stays in registers.
 struct KnnList {
     float d[KNN_MAX];
     int i[KNN_MAX];   // original index (tie-break)
     int k[KNN_MAX];   // sorted index in the grid searched
 };
+
+__device__ __forceinline__ void knn_list_init(KnnList &L) {
+#pragma unroll
+    for (int m = 0; m < KNN_MAX; ++m) {
+        L.d[m] = INFINITY;
+        L.i[m] = 0x7fffffff;
+        L.k[m] = -1;
+    }
+}
+
+// Insert a candidate that precedes slot 0: slot 0 drops out, the entries
+// still farther than the candidate move up one slot, and the candidate takes
+// the slot after them.
+__device__ __forceinline__ void knn_list_insert(KnnList &L, int knn, float cd, int ci, int ck) {
+    bool placing = true;
+#pragma unroll
+    for (int m = 0; m < KNN_MAX; ++m) {
+        if (m < knn && placing) {
+            float nd = -INFINITY;
+            int ni = -1, nk = -1;
+            if (m + 1 < KNN_MAX && m + 1 < knn) {
+                nd = L.d[m + 1 < KNN_MAX ? m + 1 : m];
+                ni = L.i[m + 1 < KNN_MAX ? m + 1 : m];
+                nk = L.k[m + 1 < KNN_MAX ? m + 1 : m];
+            }
+            if (nd > cd || (nd == cd && ni > ci)) {
+                L.d[m] = nd;
+                L.i[m] = ni;
+                L.k[m] = nk;
+            } else {
+                L.d[m] = cd;
+                L.i[m] = ci;
+                L.k[m] = ck;
+                placing = false;
+            }
+        }
+    }
+}
 
 // The knn nearest points of q in grid g, searching shells R = 1..R_max of
 // voxels around q's voxel.  After shell R every point closer than R * h has
@@ -65,14 +122,7 @@ __device__ __forceinline__ bool knn_search(const GridDev &g, float4 q, int knn, 
         int c = (int)floorf((qc[a] - g.corner[a]) * g.inv_h);
         cq[a] = min(max(c, 0), g.dims[a] - 1);
     }
-#pragma unroll
-    for (int m = 0; m < KNN_MAX; ++m) {
-        L.d[m] = INFINITY;
-        L.i[m] = 0x7fffffff;
-        L.k[m] = -1;
-    }
-    float wd = INFINITY;   // knn-th distance so far
-    int wi = 0x7fffffff;   // its original index (INT_MAX while the list is short)
+    knn_list_init(L);
     #pragma unroll 1
     for (int R = 1; R <= R_max; ++R) {
         #pragma unroll 1
@@ -91,7 +141,7 @@ __device__ __forceinline__ bool knn_search(const GridDev &g, float4 q, int knn, 
                 for (int dz = -R; dz <= R; dz += step) {
                     int cz = cq[2] + dz;
                     if (cz < 0 || cz >= g.dims[2]) continue;
-                    unsigned long long key = ((unsigned long long)cx * g.dims[1] + cy) * g.dims[2] + cz;
+                    unsigned long long key = g.key_base + ((unsigned long long)cx * g.dims[1] + cy) * g.dims[2] + cz;
                     int c = grid_lookup(g, key);
                     if (c < 0) continue;
                     int s0 = g.cell_start[c], s1 = g.cell_start[c + 1];
@@ -99,50 +149,32 @@ __device__ __forceinline__ bool knn_search(const GridDev &g, float4 q, int knn, 
                         float4 y = g.pos[k];
                         float ex = y.x - q.x, ey = y.y - q.y, ez = y.z - q.z;
                         float d2 = ex * ex + ey * ey + ez * ez;
-                        if (d2 > wd) continue;
+                        if (d2 > L.d[0]) continue;
                         int oi = g.orig[k];
-                        if (d2 == wd && oi >= wi) continue;
-                        float cd = d2;
-                        int ci = oi, ck = k;
-#pragma unroll
-                        for (int m = 0; m < KNN_MAX; ++m) {
-                            if (m < knn) {
-                                bool less = cd < L.d[m] || (cd == L.d[m] && ci < L.i[m]);
-                                if (less) {
-                                    float td = L.d[m];
-                                    int ti = L.i[m], tk = L.k[m];
-                                    L.d[m] = cd;
-                                    L.i[m] = ci;
-                                    L.k[m] = ck;
-                                    cd = td;
-                                    ci = ti;
-                                    ck = tk;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int m = 0; m < KNN_MAX; ++m)
-                            if (m == knn - 1) {
-                                wd = L.d[m];
-                                wi = L.i[m];
-                            }
+                        if (d2 == L.d[0] && oi >= L.i[0]) continue;
+                        knn_list_insert(L, knn, d2, oi, k);
                     }
                 }
             }
         }
         float reach = (float)R * g.h;
-        if (wi != 0x7fffffff && wd <= reach * reach * 0.999f) return true;
+        if (L.i[0] != 0x7fffffff && L.d[0] <= reach * reach * 0.999f) return true;
     }
     return false;
 }
 
 // Eq. (7b) over the list, then the eigenvalue bound; writes column o of cov_out.
+// DESC: the list is a KnnList from knn_search (descending); otherwise it is
+// ascending (the merged list of the warp search).  The sum runs in ascending
+// order either way.
+template <bool DESC>
 __device__ __forceinline__ void knn_write_cov(const GridDev &g, float4 q, const KnnList &L, int knn, double eig_max,
                               double eig_ratio, int64_t n, int o, float *cov_out) {
     // Sigma = 1/(n-1) sum (y - x)(y - x)^T, centred at the query point
     float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int m = 0; m < KNN_MAX; ++m) {
+    for (int mm = 0; mm < KNN_MAX; ++mm) {
+        const int m = DESC ? KNN_MAX - 1 - mm : mm;
         if (m < knn) {
             float4 y = g.pos[L.k[m]];
             float d0 = y.x - q.x, d1 = y.y - q.y, d2 = y.z - q.z;

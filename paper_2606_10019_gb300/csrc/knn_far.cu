@@ -1,6 +1,6 @@
-// Pass 2 of the kNN covariances: the points whose neighbours lie beyond the
-// fine grid's two shells (a separate translation unit so that it compiles in
-// parallel with grid.cu).
+// Pass 3 of the kNN covariances: the points whose neighbours lie beyond the
+// fine and middle grids' two shells (a separate translation unit so that it
+// compiles in parallel with grid.cu).
 #include "common.cuh"
 #include "knn.cuh"
 
@@ -9,21 +9,25 @@ namespace {
 
 using namespace knn;
 
-// Pass 2: one warp per queued point, searching the coarse grid shell by
-// shell without a limit.  The lanes split each shell's voxels and keep
+// Pass 3: one warp per queued point, searching its cloud's coarse grid shell
+// by shell without a limit.  The lanes split each shell's voxels and keep
 // private sorted lists; after every shell the warp merges them (repeated
 // warp-wide minimum over each lane's next entry) into the knn nearest so
 // far, and stops once the knn-th distance is within the shells' reach.
-__global__ void k_knn_cov_far(GridDev fine, GridDev coarse, int knn, double eig_max, double eig_ratio, int64_t n,
-                              float *cov_out, const int *retry, const int *n_retry, unsigned *status) {
+__global__ void k_knn_cov_far(const GridDev *gcs, const KnnCloud *cl, const float4 *P, const int *list,
+                              const int *n_list, unsigned *status) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    const int m = *n_retry;
-    const int maxR = max(coarse.dims[0], max(coarse.dims[1], coarse.dims[2]));
+    const int m = *n_list;
     for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < m; t += gridDim.x * wpb) {
-        const int i = retry[t];
-        const float4 q = fine.pos[i];
+        const int j = list[t];
+        const float4 q = P[j];
+        const int cloud = cloud_of(q);
+        const GridDev &coarse = gcs[cloud];
+        const KnnCloud &kc = cl[cloud];
+        const int knn = kc.knn;
+        const int maxR = max(coarse.dims[0], max(coarse.dims[1], coarse.dims[2]));
         int cq[3];
         {
             float qc[3] = {q.x, q.y, q.z};
@@ -53,7 +57,8 @@ __global__ void k_knn_cov_far(GridDev fine, GridDev coarse, int knn, double eig_
                 if (cx < 0 || cy < 0 || cz < 0 || cx >= coarse.dims[0] || cy >= coarse.dims[1] ||
                     cz >= coarse.dims[2])
                     continue;
-                unsigned long long key = ((unsigned long long)cx * coarse.dims[1] + cy) * coarse.dims[2] + cz;
+                unsigned long long key =
+                    coarse.key_base + ((unsigned long long)cx * coarse.dims[1] + cy) * coarse.dims[2] + cz;
                 int c = grid_lookup(coarse, key);
                 if (c < 0) continue;
                 for (int k = coarse.cell_start[c], k1 = coarse.cell_start[c + 1]; k < k1; ++k) {
@@ -150,16 +155,15 @@ __global__ void k_knn_cov_far(GridDev fine, GridDev coarse, int knn, double eig_
             if (lane == 0) atomicOr(status, DEV_ERR_CAPACITY);
             continue;
         }
-        if (lane == 0) knn_write_cov(coarse, q, M, knn, eig_max, eig_ratio, n, fine.orig[i], cov_out);
+        if (lane == 0) knn_write_cov<false>(coarse, q, M, knn, kc.eig_max, kc.eig_ratio, kc.n, (int)(j - kc.off), kc.cov);
     }
 }
 
 }  // namespace
 
-void launch_knn_far(const GridDev &fine, const GridDev &coarse, int knn, double eig_max, double eig_ratio, int64_t n,
-                    float *cov_out, const int *retry, const int *n_retry, unsigned *status, int blocks,
-                    cudaStream_t s) {
-    k_knn_cov_far<<<blocks, 128, 0, s>>>(fine, coarse, knn, eig_max, eig_ratio, n, cov_out, retry, n_retry, status);
+void launch_knn_far(const GridDev *gc, const KnnCloud *cl, const float4 *P, const int *list, const int *n_list,
+                    unsigned *status, int blocks, cudaStream_t s) {
+    k_knn_cov_far<<<blocks, 128, 0, s>>>(gc, cl, P, list, n_list, status);
 }
 
 }  // namespace gcvo
