@@ -331,7 +331,7 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
  * deployment variant of one evaluation.)
  *
  * It needs no gcvo_ctx and allocates nothing: its scratch is one static
- * device array of 5.3 MiB in the library, reserved on every device that
+ * device array of 6.3 MiB in the library, reserved on every device that
  * loads the library until the process exits.  The caller passes device
  * pointers on the grid's device for every input (host pointers and
  * pointers to another device are rejected with GCVO_ERR_INVALID_ARG, as are
@@ -437,8 +437,8 @@ typedef struct {
 /* Schedule of the pair passes (the autotuner; not in the paper): the source
  * points are cut into sub-tiles of at most `sub` = 4, 8, 16 or 32 points
  * (8, 4, 2 or 1 threads per point) that never cross a Morton voxel of edge
- * rho (level 2) or 2 rho (level 3); a schedule is sub | level << 8, and a
- * bare sub means level 2.  set = 0 lets the autotuner pick per problem shape
+ * rho / 2 (level 1), rho (level 2) or 2 rho (level 3); a schedule is
+ * sub | level << 8, and a bare sub means level 2.  set = 0 lets the autotuner pick per problem shape
  * (the default: on the first call for a shape it times one pass with each
  * candidate and keeps the fastest for the context); any other valid value
  * forces that schedule; set = -1 changes nothing.  *last_used (may be NULL)

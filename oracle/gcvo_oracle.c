@@ -205,11 +205,17 @@ typedef struct {
     double n_pairs_kept;   /* pairs passing the cutoff */
     double n_pairs_rho;    /* pairs with |r_ij| <= rho */
     double n_near_cut;     /* pairs with |d^2 - cutoff^2| < 1e-4 * cutoff^2 */
+    /* The terms those near-cutoff pairs have at their own d^2, kept or not:
+     * the cutoff test d^2 <= c^2 of Eq. (7) decides them, and a computation
+     * in lower precision may decide them the other way; f_near and
+     * g_near[a] (sum of |g^(ij)_a|) bound the difference that makes. */
+    double f_near;
+    double g_near[6];
 } orc_eval_out;
 
 /* Per-source-point contribution (summed over all targets i). */
 typedef struct {
-    double f, g[6], M[36], gabs[6], kept, nrho, near;
+    double f, g[6], M[36], gabs[6], kept, nrho, near, fnear, gnear[6];
 } orc_partial;
 
 static void pair_terms(const double *x, const double *covx, const double *lx, const double *p,
@@ -233,19 +239,27 @@ static void pair_terms(const double *x, const double *covx, const double *lx, co
     double u[3];
     for (int a = 0; a < 3; ++a) u[a] = Ainv[3 * a + 0] * r[0] + Ainv[3 * a + 1] * r[1] + Ainv[3 * a + 2] * r[2];
     double d2 = r[0] * u[0] + r[1] * u[1] + r[2] * u[2];
-    if (P->cutoff > 0) {
-        double c2 = P->cutoff * P->cutoff;
-        if (fabs(d2 - c2) < 1e-4 * c2) acc->near += 1;
-        if (d2 > c2) return;
-    }
-    acc->kept += 1;
+    const double c2 = P->cutoff * P->cutoff;
+    const int near = P->cutoff > 0 && fabs(d2 - c2) < 1e-4 * c2;
+    const int cut = P->cutoff > 0 && d2 > c2;
+    if (cut && !near) return;
     /* Eq. (5), (7a): f_ij = c_ij k(x_i, p_j), c_ij = <l_i^X, l_j^Z> */
     double cij = 0;
     for (int q = 0; q < P->feat_dim; ++q) cij += lx[q] * lz[q];
     double fij = cij * P->sigma2 * exp(-0.5 * d2);
-    acc->f += fij;
     /* Lemma 1: g_v = -sum f_ij Sigma^-1 r, g_omega = -sum f_ij p^ Sigma^-1 r */
     double pxu[3] = {p[1] * u[2] - p[2] * u[1], p[2] * u[0] - p[0] * u[2], p[0] * u[1] - p[1] * u[0]};
+    if (near) {
+        acc->near += 1;
+        acc->fnear += fabs(fij);
+        for (int a = 0; a < 3; ++a) {
+            acc->gnear[a] += fabs(fij * pxu[a]);
+            acc->gnear[3 + a] += fabs(fij * u[a]);
+        }
+    }
+    if (cut) return;
+    acc->kept += 1;
+    acc->f += fij;
     for (int a = 0; a < 3; ++a) {
         acc->g[a] -= fij * pxu[a];
         acc->g[3 + a] -= fij * u[a];
@@ -324,6 +338,8 @@ int orc_eval(const double *tgt, const double *tgt_cov, const double *tgt_feat, i
         out->n_pairs_kept += part[j].kept;
         out->n_pairs_rho += part[j].nrho;
         out->n_near_cut += part[j].near;
+        out->f_near += part[j].fnear;
+        for (int a = 0; a < 6; ++a) out->g_near[a] += part[j].gnear[a];
         if (per_src) {
             per_src[7 * j] = part[j].f;
             for (int a = 0; a < 6; ++a) per_src[7 * j + 1 + a] = part[j].g[a];

@@ -64,7 +64,8 @@ class _Params(ctypes.Structure):
 class _EvalOut(ctypes.Structure):
     _fields_ = [("f", ctypes.c_double), ("g", ctypes.c_double * 6), ("M", ctypes.c_double * 36),
                 ("gabs", ctypes.c_double * 6), ("n_pairs_kept", ctypes.c_double),
-                ("n_pairs_rho", ctypes.c_double), ("n_near_cut", ctypes.c_double)]
+                ("n_pairs_rho", ctypes.c_double), ("n_near_cut", ctypes.c_double),
+                ("f_near", ctypes.c_double), ("g_near", ctypes.c_double * 6)]
 
 
 _lib = None
@@ -277,6 +278,9 @@ class EvalResult:
     n_rho: float
     n_near_cut: float
     per_src: np.ndarray | None = None
+    f_near: float = 0.0                  # |f| and |g| terms of the pairs within 1e-4 c^2 of the
+    g_near: np.ndarray | None = None     # cutoff (Eq. 7), kept or not: a lower-precision cutoff
+                                         # test may decide those pairs the other way
 
 
 def _params(kp: KernelParams, feat_dim: int) -> _Params:
@@ -301,7 +305,7 @@ def evaluate(prob: Problem, T, kp: KernelParams, per_src: bool = False) -> EvalR
     M = np.array(out.M[:]).reshape(6, 6)
     G = gamma_matrix(g)
     return EvalResult(out.f, g, M, G, -M + G, np.array(out.gabs[:]), out.n_pairs_kept,
-                      out.n_pairs_rho, out.n_near_cut, ps)
+                      out.n_pairs_rho, out.n_near_cut, ps, out.f_near, np.array(out.g_near[:]))
 
 
 def gn_step(res: EvalResult) -> np.ndarray:

@@ -91,6 +91,31 @@ struct Prepared {
     std::vector<ProbDev> probs;
 };
 
+// Whether the pair passes of a problem must form r = x - p from
+// double-float positions.  Positions are relative to the target box centre,
+// so FP32 rounds both x and p by up to 2^-24 R, R the box half-diagonal
+// plus rho; with |Sigma_ij^-1 r| <= c / sigma_min (sigma_min^2 the smallest
+// eigenvalue of Sigma_ij, at least the sum of the two clouds' smallest), each
+// d^2 moves by up to 4 c R 2^-24 / sigma_min.  Above 3e-4 (a LiDAR frame,
+// R about 100 m with sigma_min about 4 cm, reaches 1.7e-3) the sums of a few
+// thousand pairs drift towards the 1e-5 relative tolerance of f and g, and
+// the tails are worth their 7 instructions per pair; a small scene (2 m,
+// sigma_min 1.4 cm: 1e-4) is accurate in FP32.  Dense mode (no cutoff) and
+// degenerate covariances always take the tails.
+bool pair_needs_lo(const GridDev &g, const gcvo_kernel_params &kp, double rho2, float lmin_src) {
+    if (kp.cutoff <= 0 || !std::isfinite(rho2)) return true;
+    double half = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = 0.5 * (double)g.dims[a] * (double)g.h;
+        half += e * e;
+    }
+    const double R = std::sqrt(half) + std::sqrt(rho2);
+    const double s2 = kp.kernel_mode == 1 ? kp.iso_ell * kp.iso_ell
+                                          : (double)g.lam_min + (double)std::max(0.0f, lmin_src);
+    if (!(s2 > 0.0)) return true;
+    return 4.0 * kp.cutoff * R * std::ldexp(1.0, -24) / std::sqrt(s2) > 3e-4;
+}
+
 gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) {
     cudaStream_t s = ctx->stream;
     if (np < 1 || np > GCVO_MAX_PROBLEMS || !pr) return GCVO_ERR_INVALID_ARG;
@@ -153,6 +178,8 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sp += al(np * sizeof(SrcDesc));
     int *d_lam = reinterpret_cast<int *>(sp);
     sp += al(np * sizeof(int));
+    int *d_lmin = reinterpret_cast<int *>(sp);
+    sp += al(np * sizeof(int));
     int *d_nitems = reinterpret_cast<int *>(sp);
     sp += 256;
     int *d_pcnt = reinterpret_cast<int *>(sp);
@@ -186,6 +213,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
 
     GCVO_CUDA(cudaMemcpyAsync(d_desc, desc.data(), np * sizeof(SrcDesc), cudaMemcpyHostToDevice, s));
     GCVO_CUDA(cudaMemsetAsync(d_lam, 0, np * sizeof(int), s));
+    GCVO_CUDA(cudaMemsetAsync(d_lmin, 0x7f, np * sizeof(int), s));   // a huge positive float
     GCVO_CUDA(cudaMemsetAsync(ctx->status_word.ptr, 0, 256, s));
 
     SrcArgs sa{};
@@ -195,6 +223,7 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
     sa.prob_of = prob_of;
     sa.local = local;
     sa.lam_enc = d_lam;
+    sa.lam_min_enc = d_lmin;
     sa.status_word = ctx->status_word.as<unsigned>();
     sa.spos = ctx->src_pos.as<float4>();
     sa.sca = ctx->src_ca.as<float4>();
@@ -224,10 +253,11 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
 
     // read back the status word and the source eigenvalue bounds
     void *hp;
-    GCVO_TRY(host_pinned(ctx, (size_t)(np + 8) * sizeof(int), &hp));
+    GCVO_TRY(host_pinned(ctx, (size_t)(2 * np + 8) * sizeof(int), &hp));
     int *h = static_cast<int *>(hp);
     GCVO_CUDA(cudaMemcpyAsync(h + 1, ctx->status_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaMemcpyAsync(h + 8, d_lam, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GCVO_CUDA(cudaMemcpyAsync(h + 8 + np, d_lmin, np * sizeof(int), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaStreamSynchronize(s));
     if (h[1] & DEV_ERR_NONFINITE) return GCVO_ERR_NONFINITE;
     P.probs.assign(np, ProbDev{});
@@ -243,10 +273,14 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
         d.iter = 0;
         d.w0 = 0;   // set with the work items
         d.w1 = 0;
-        int le = h[8 + p];
-        int li = le >= 0 ? le : le ^ 0x7fffffff;
-        float lam_src;
-        memcpy(&lam_src, &li, 4);
+        auto dec = [](int e) {
+            const int i = e >= 0 ? e : e ^ 0x7fffffff;
+            float f;
+            memcpy(&f, &i, 4);
+            return f;
+        };
+        const float lam_src = dec(h[8 + p]);
+        const float lmin_src = dec(h[8 + np + p]);
         const gcvo_kernel_params &kp = G->kp;
         double c2 = kp.cutoff * kp.cutoff;
         double rho2;
@@ -258,11 +292,13 @@ gcvo_status prepare(gcvo_ctx *ctx, int np, const gcvo_problem *pr, Prepared &P) 
             rho2 = c2 * ((double)G->store.d.lam_max + (double)lam_src) * (1.0 + 2e-4) + 1e-12;
         d.rho2 = (float)rho2;
         d.c2 = (float)c2;
+        d.lo = pair_needs_lo(G->store.d, kp, rho2, lmin_src) ? 1 : 0;
         d.sigma2 = (float)kp.sigma2;
         d.iso_inv = kp.kernel_mode == 1 ? (float)(1.0 / (kp.iso_ell * kp.iso_ell)) : 0.f;
     }
     // per-iteration buffers
-    GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_items, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,
+    GCVO_TRY(ctx->partial.ensure((size_t)std::max(P.n_items, 1) * (64 * sizeof(float) + 4 * sizeof(long long)) +
+                                     fin_chunk_bytes(P.n_items, P.n_problems) + 4096,
                                  s));
     GCVO_TRY(ctx->probs.ensure(np * sizeof(ProbDev), s));
     GCVO_TRY(ctx->grids.ensure(np * sizeof(GridDev), s));
@@ -294,12 +330,17 @@ int pair_grid(const gcvo_ctx *ctx, const Prepared &P, int mode, int sub) {
 
 // A schedule of the pair passes: sub (points per sub-tile: 4, 8, 16 or 32,
 // i.e. 8, 4, 2 or 1 lanes per point) | level << 8 (the Morton voxel level
-// that sub-tiles never cross: 2 = edge rho, 3 = edge 2 rho).  The work items
+// that sub-tiles never cross: 1 = edge rho / 2, 2 = edge rho, 3 = edge 2 rho;
+// a finer cut gives smaller sub-tile boxes and so fewer targets per box that
+// lie out of range of the box's points, at the price of more, emptier
+// sub-tiles in sparse parts).  The work items
 // are packed for it.
 gcvo_status pack(gcvo_ctx *ctx, const Prepared &P, int sched) {
     return pack_items(P.n_problems, ctx->sort_keys.as<unsigned long long>(), P.n_points, sched & 0xff, sched >> 8,
                       P.d_poff, P.d_npts, ctx->pack_tmp.as<int>(), ctx->items.as<int>(), ctx->item_prob.as<int>(),
-                      P.d_nitems, ctx->probs.as<ProbDev>(), ctx->scan_tmp.ptr, ctx->stream);
+                      P.d_nitems, ctx->probs.as<ProbDev>(),
+                      reinterpret_cast<int *>(ctx->status_word.as<char>() + 64) + 2,   // chunk count
+                      ctx->scan_tmp.ptr, ctx->stream);
 }
 
 // The autotuner: the schedule for this shape of problem set -- a forced
@@ -318,8 +359,9 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
         for (auto &kv : ctx->tuned)
             if (kv.first == key) sched = kv.second;
         if (!sched) {
-            constexpr int NC = 7;
-            const int cands[NC] = {4 | 2 << 8, 8 | 2 << 8, 16 | 2 << 8, 32 | 2 << 8, 8 | 3 << 8, 16 | 3 << 8, 32 | 3 << 8};
+            constexpr int NC = 9;
+            const int cands[NC] = {4 | 2 << 8,  8 | 2 << 8,  16 | 2 << 8, 32 | 2 << 8, 8 | 3 << 8,
+                                   16 | 3 << 8, 32 | 3 << 8, 4 | 1 << 8,  8 | 1 << 8};
             cudaEvent_t ev[2 * NC];
             for (auto &e : ev) GCVO_CUDA(cudaEventCreate(&e));
             float best = 0.f;
@@ -364,7 +406,7 @@ gcvo_status choose_schedule(gcvo_ctx *ctx, const Prepared &P, IterBufs &b) {
 
 // The buffers of the per-iteration launches, the split pose constants and
 // the transformed source at the initial pose, and the pair schedule.  exact:
-// the G-CVO-E pass will run (second partial row, coordinate tails of p).
+// the G-CVO-E pass will run (second partial row).
 gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_log *dlogs, int k_max,
                       bool exact) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -372,12 +414,15 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     size_t ng = (size_t)std::max(P.n_items, 1);
     float *pf = reinterpret_cast<float *>(part);
     long long *pc = reinterpret_cast<long long *>(part + al(ng * 64 * sizeof(float)));
+    const size_t n_chunk_rows = (size_t)(P.n_items / FIN_CHUNK) + (size_t)P.n_problems + 1;
+    double *chunk = reinterpret_cast<double *>(part + al(ng * 64 * sizeof(float)) + al(ng * 4 * sizeof(long long)));
+    long long *chunk_cnt = reinterpret_cast<long long *>(reinterpret_cast<char *>(chunk) +
+                                                         al(n_chunk_rows * 64 * sizeof(double)));
     int *work = reinterpret_cast<int *>(ctx->status_word.as<char>() + 64);
     int *n_active = work + 1;
-    if (exact) {
-        GCVO_TRY(ctx->partial2.ensure(ng * 64 * sizeof(float), ctx->stream));
-        GCVO_TRY(ctx->t_lo.ensure((size_t)std::max<int64_t>(P.n_points, 1) * sizeof(float4), ctx->stream));
-    }
+    if (exact) GCVO_TRY(ctx->partial2.ensure(ng * 64 * sizeof(float), ctx->stream));
+    // the tails of p: every pair pass forms r in double-float
+    GCVO_TRY(ctx->t_lo.ensure((size_t)std::max<int64_t>(P.n_points, 1) * sizeof(float4), ctx->stream));
     TransformArgs &t = b.ta;
     t.spos = ctx->src_pos.as<float4>();
     t.sca = ctx->src_ca.as<float4>();
@@ -387,7 +432,7 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     t.tpos = ctx->t_pos.as<float4>();
     t.tca = ctx->t_ca.as<float4>();
     t.tcb = ctx->t_cb.as<float4>();
-    t.tlo = exact ? ctx->t_lo.as<float4>() : nullptr;
+    t.tlo = ctx->t_lo.as<float4>();
     t.sfx = P.feat_dim > 3 ? ctx->src_fx.as<float4>() : nullptr;
     t.tfx = P.feat_dim > 3 ? ctx->t_fx.as<float4>() : nullptr;
     t.n = P.n_points;
@@ -415,6 +460,10 @@ gcvo_status iter_bufs(gcvo_ctx *ctx, const Prepared &P, IterBufs &b, gcvo_iter_l
     f.part = pf;
     f.part2 = a.part2;
     f.counts = pc;
+    f.chunk = chunk;
+    f.chunk_cnt = chunk_cnt;
+    f.n_chunks = work + 2;   // written by pack_items
+    f.reduce_blocks = std::max(1, ctx->sm_count) * 8;
     f.evalout = ctx->evalout.as<EvalOut>();
     f.logs = dlogs;
     f.n_active = n_active;
@@ -742,7 +791,7 @@ std::vector<size_t> ws_sizes(int64_t N, int64_t np, int64_t rows) {
         n * sizeof(float4), n * sizeof(float4),                         // src_fx, t_fx
         n * sizeof(int4), n * sizeof(int),                              // items, item_prob
         5 * n64 * sizeof(int),                                          // pack_tmp
-        n * (64 * sizeof(float) + 4 * sizeof(long long)) + 4096,        // partial
+        n * (64 * sizeof(float) + 4 * sizeof(long long)) + fin_chunk_bytes((int64_t)n, (int)np) + 4096,   // partial
         n * 64 * sizeof(float),                                         // partial2
         np * sizeof(ProbDev), np * sizeof(GridDev), np * sizeof(EvalOut) + 256,
         (size_t)std::max<int64_t>(rows, 1) * sizeof(gcvo_iter_log),     // logs
@@ -877,7 +926,7 @@ gcvo_status gcvo_profile_enable(gcvo_ctx *ctx, int enable) {
 
 gcvo_status gcvo_pair_schedule(gcvo_ctx *ctx, int set, int *last_used) {
     const int sub = set & 0xff, level = set >> 8;
-    const bool ok_sub = sub == 4 || sub == 8 || sub == 16 || sub == 32, ok_level = level == 0 || level == 2 || level == 3;
+    const bool ok_sub = sub == 4 || sub == 8 || sub == 16 || sub == 32, ok_level = level == 0 || (level >= 1 && level <= 3);
     if (!ctx || (set != -1 && set != 0 && !(ok_sub && ok_level))) return GCVO_ERR_INVALID_ARG;
     if (set >= 0) ctx->forced_sub = set;
     if (last_used) *last_used = ctx->last_sub;
@@ -1253,7 +1302,7 @@ gcvo_status gcvo_set_workspace(gcvo_ctx *ctx, void *dev_ptr, size_t bytes, int64
     if (at.type != cudaMemoryTypeDevice || at.device != ctx->device) return GCVO_ERR_INVALID_ARG;
     // the host read-back buffer, sized once for the problem limit
     void *hp;
-    GCVO_TRY(host_pinned(ctx, (size_t)(max_problems + 64) * sizeof(int), &hp));
+    GCVO_TRY(host_pinned(ctx, (size_t)(2 * max_problems + 64) * sizeof(int), &hp));
     const std::vector<size_t> sz = ws_sizes(max_points, max_problems, max_log_rows);
     char *p = static_cast<char *>(dev_ptr);
     for (size_t k = 0; k < bufs.size(); ++k) {

@@ -95,6 +95,7 @@ struct GridDev {
     int dims[3];
     int n, n_cells;
     float lam_max;            // largest eigenvalue over the stored covariances
+    float lam_min;            // smallest (target grids with covariances; else 0)
     int feat_dim;
     int kernel_mode;
 };
@@ -138,9 +139,9 @@ size_t scan_scratch_bytes(int64_t n);
 gcvo_status scan_inclusive_sum(int *data, int64_t n, void *scratch, cudaStream_t s);
 gcvo_status scan_inclusive_max(int *data, int64_t n, void *scratch, cudaStream_t s);
 
-// Bounding box of a 3 x n SoA cloud and the largest eigenvalue of a 6 x n
-// SoA covariance array (cov may be null).  out: 8 floats
-// (min xyz, max xyz, lam_max, nonfinite flag).
+// Bounding box of a 3 x n SoA cloud and the largest and smallest
+// eigenvalues of a 6 x n SoA covariance array (cov may be null).  out: 9
+// floats (min xyz, max xyz, lam_max, flags, lam_min).
 gcvo_status bbox_lammax(const float *xyz, const float *cov, int64_t n, float *out_dev, cudaStream_t s);
 
 // Largest eigenvalue of a symmetric 3x3 (closed form, float).
@@ -158,6 +159,23 @@ __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, f
     float r = fminf(fmaxf(0.5f * detb, -1.0f), 1.0f);
     float phi = acosf(r) * (1.0f / 3.0f);
     return q + 2.0f * p * cosf(phi);
+}
+
+// Smallest eigenvalue of a symmetric 3x3 (the same closed form, third root).
+__host__ __device__ inline float sym3_min_eig(float a00, float a01, float a02, float a11, float a12, float a22) {
+    float p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * p1;
+    if (p2 <= 0.0f) return q;
+    float p = sqrtf(p2 * (1.0f / 6.0f));
+    float ip = 1.0f / p;
+    b00 *= ip; b11 *= ip; b22 *= ip;
+    float c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    float detb = b00 * (b11 * b22 - c12 * c12) - c01 * (c01 * b22 - c12 * c02) + c02 * (c01 * c12 - b11 * c02);
+    float r = fminf(fmaxf(0.5f * detb, -1.0f), 1.0f);
+    float phi = acosf(r) * (1.0f / 3.0f);
+    return q + 2.0f * p * cosf(phi + 2.0943951023931953f);   // the third root, phi + 2 pi / 3
 }
 
 // ---------------------------------------------------------------------------

@@ -105,7 +105,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     GCVO_TRY(ctx->small.ensure(4096, s));
     float *bb = ctx->small.as<float>();
     GCVO_TRY(bbox_lammax(xyz, kp.kernel_mode == 0 ? cov : nullptr, n, bb, s));
-    int hb[8];
+    int hb[9];
     GCVO_CUDA(cudaMemcpyAsync(hb, bb, sizeof(hb), cudaMemcpyDeviceToHost, s));
     GCVO_CUDA(cudaStreamSynchronize(s));
     auto dec = [](int k) {
@@ -144,6 +144,7 @@ gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, 
     g.feat_dim = kp.feat_dim;
     g.kernel_mode = kp.kernel_mode;
     g.lam_max = lam;
+    g.lam_min = kp.kernel_mode == 0 && cov ? std::max(0.0f, dec(hb[8])) : 0.0f;
     double prod = 1.0;
     for (int a = 0; a < 3; ++a) {
         g.origin[a] = absolute ? 0.0 : 0.5 * ((double)mn[a] + (double)mx[a]);

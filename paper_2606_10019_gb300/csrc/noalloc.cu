@@ -33,19 +33,24 @@ constexpr size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t NA_SPOS = 0;
 constexpr size_t NA_SCA = NA_SPOS + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_SCB = NA_SCA + al256(NA_MAX_SRC * 16);
-constexpr size_t NA_ITEMS = NA_SCB + al256(NA_MAX_SRC * 16);
+constexpr size_t NA_TLO = NA_SCB + al256(NA_MAX_SRC * 16);      // tails of the transformed positions
+constexpr size_t NA_ITEMS = NA_TLO + al256(NA_MAX_SRC * 16);
 constexpr size_t NA_IPROB = NA_ITEMS + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_PART = NA_IPROB + al256(NA_MAX_ITEMS * 4);
 constexpr size_t NA_COUNTS = NA_PART + al256((size_t)NA_MAX_ITEMS * 64 * 4);
-constexpr size_t NA_PROB = NA_COUNTS + al256((size_t)NA_MAX_ITEMS * 4 * 8);
+constexpr size_t NA_CHUNK_ROWS = NA_MAX_ITEMS / FIN_CHUNK + 2;
+constexpr size_t NA_CHUNK = NA_COUNTS + al256((size_t)NA_MAX_ITEMS * 4 * 8);
+constexpr size_t NA_CHUNKCNT = NA_CHUNK + al256(NA_CHUNK_ROWS * 64 * 8);
+constexpr size_t NA_PROB = NA_CHUNKCNT + al256(NA_CHUNK_ROWS * 4 * 8);
 constexpr size_t NA_GRID = NA_PROB + al256(sizeof(ProbDev));
 constexpr size_t NA_EVAL = NA_GRID + al256(sizeof(GridDev));
-constexpr size_t NA_WORDS = NA_EVAL + al256(sizeof(EvalOut));   // work, n_items, lam, status, n_active
+constexpr size_t NA_WORDS = NA_EVAL + al256(sizeof(EvalOut));   // work, n_items, lam, status, n_active, n_chunks
 constexpr size_t NA_BYTES = NA_WORDS + 256;
-// 3 MiB of source records, 2 MiB of partials, 256 KiB of counters and 64 KiB
-// of work items: the 5.3 MiB the header documents
-static_assert(NA_BYTES >= size_t(5300) * 1048576 / 1000 && NA_BYTES <= size_t(5350) * 1048576 / 1000,
-              "the documented size of the static scratch (5.3 MiB)");
+// 4 MiB of source records and position tails, 2 MiB of partials, 256 KiB of
+// counters, 64 KiB of work items and 18 KiB of finalize chunk sums: the
+// 6.3 MiB the header documents
+static_assert(NA_BYTES >= size_t(6300) * 1048576 / 1000 && NA_BYTES <= size_t(6350) * 1048576 / 1000,
+              "the documented size of the static scratch (6.3 MiB)");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -111,6 +116,9 @@ __global__ void k_na_setup(NaSetup a, unsigned char *base) {
     P->iter = 0;
     P->w0 = 0;
     P->w1 = a.n_items;
+    P->c0 = 0;
+    P->c1 = (a.n_items + FIN_CHUNK - 1) / FIN_CHUNK;
+    P->lo = 1;   // r from double-float positions (no eigenvalue bounds here)
     const int le = words[2];
     const float lam_src = __int_as_float(le >= 0 ? le : le ^ 0x7fffffff);
     double c2 = a.cutoff * a.cutoff;
@@ -123,6 +131,7 @@ __global__ void k_na_setup(NaSetup a, unsigned char *base) {
     P->iso_inv = a.kernel_mode == 1 ? (float)(1.0 / (a.iso_ell * a.iso_ell)) : 0.f;
     words[1] = a.n_items;
     words[4] = 1;
+    words[5] = P->c1;
 }
 
 std::mutex g_na_mutex;
@@ -197,6 +206,9 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     fa.grids = reinterpret_cast<const GridDev *>(base + NA_GRID);
     fa.part = reinterpret_cast<const float *>(base + NA_PART);
     fa.counts = reinterpret_cast<const long long *>(base + NA_COUNTS);
+    fa.chunk = reinterpret_cast<double *>(base + NA_CHUNK);
+    fa.chunk_cnt = reinterpret_cast<long long *>(base + NA_CHUNKCNT);
+    fa.n_chunks = words + 5;
     fa.evalout = reinterpret_cast<EvalOut *>(base + NA_EVAL);
     fa.logs = nullptr;
     fa.n_active = words + 4;
@@ -209,7 +221,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     ta.spos = ta.tpos = reinterpret_cast<float4 *>(base + NA_SPOS);
     ta.sca = ta.tca = reinterpret_cast<float4 *>(base + NA_SCA);
     ta.scb = ta.tcb = reinterpret_cast<float4 *>(base + NA_SCB);
-    ta.tlo = nullptr;
+    ta.tlo = reinterpret_cast<float4 *>(base + NA_TLO);
     ta.sfx = nullptr;
     ta.tfx = nullptr;
     ta.pprob = nullptr;
@@ -221,7 +233,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     pa.tpos = ta.tpos;
     pa.tca = ta.tca;
     pa.tcb = ta.tcb;
-    pa.tlo = nullptr;
+    pa.tlo = ta.tlo;
     pa.tfx = nullptr;
     pa.items = reinterpret_cast<const int *>(base + NA_ITEMS);
     pa.item_prob = reinterpret_cast<const int *>(base + NA_IPROB);
@@ -239,6 +251,7 @@ extern "C" gcvo_status gcvo_eval_static(const gcvo_grid *target, const float *sr
     int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * sm));
     GCVO_CUDA(launch_pair(pa, PAIR_EVAL, iso, fd, NA_SUB, grid, s));
     fa.mode = FIN_EVAL;
+    fa.reduce_blocks = std::max(1, sm) * 8;
     GCVO_CUDA(launch_finalize(fa, s));
     EvalOut e;
     unsigned st = 0;

@@ -1,10 +1,12 @@
 // The FP64 side of the per-iteration hot path of Algorithm 1, the transform
 // of the source points, and the source packing done once per call:
-//   k_finalize  -- FP64 sum of the item partials of each problem, change of
-//                  frame, connection term (Eq. 12), the 6x6 solve of Eq. (13)
-//                  (or the G-CVO-E Newton step with the exact Hessian) and
-//                  the update T <- T exp(xi); the split pose constants the
-//                  transform reads.
+//   k_fin_reduce -- FP64 sums of the item partials over chunks of FIN_CHUNK
+//                  work items of one problem (all SMs, whatever the batch);
+//   k_fin_step  -- one warp per problem: the sum of its chunk rows, change
+//                  of frame, connection term (Eq. 12), the 6x6 solve of
+//                  Eq. (13) (or the G-CVO-E Newton step with the exact
+//                  Hessian) and the update T <- T exp(xi); the split pose
+//                  constants the transform reads.
 //   k_transform -- every source point of an active problem moved into the
 //                  target grid's frame at the current pose (Algorithm 1,
 //                  T^-1 z): p = R^T (z - t) - o in double-float arithmetic,
@@ -548,59 +550,94 @@ __device__ void refresh_pose(const FinalizeArgs &a, int prob, ProbDev *P) {
     }
 }
 
-constexpr int FIN_THREADS = 512;   // 16 parts x 32 slots of the partial sums
+constexpr int FIN_RED_THREADS = 256;   // 8 warps: item g goes to warp g % 8
+constexpr int FIN_STEP_WARPS = 4;      // problems per block of k_fin_step
 
-__global__ void __launch_bounds__(FIN_THREADS) k_finalize(FinalizeArgs a) {
-    const int prob = blockIdx.x;
+// The chunk rows: per chunk, per slot, a compensated FP32 sum of the (hi, lo)
+// partials over each warp's items (8 loads in flight per warp), the warps
+// added in FP64 in a fixed order; the pair counts likewise.  A persistent
+// grid walks the chunks; the problem of chunk c is the last one with c0 <= c.
+__global__ void __launch_bounds__(FIN_RED_THREADS) k_fin_reduce(FinalizeArgs a) {
+    __shared__ double red[FIN_RED_THREADS / 32][64];
+    __shared__ long long cred[FIN_RED_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // the G-CVO-E pass leaves slots 32..45 in a second partial row per item
+    // (its slots 46..63 are never written, and their sums never read)
+    const int rows = (a.mode == FIN_EXACT || a.mode == FIN_EXACT_EVAL) ? 2 : 1;
+    const int nch = *a.n_chunks;
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        int lo = 0, hi = a.n_problems - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.probs[mid].c0 <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const ProbDev *P = a.probs + lo;
+        if (P->status != 0) continue;   // the same for the whole block
+        const int i0 = P->w0 + (c - P->c0) * FIN_CHUNK, i1 = min(P->w1, i0 + FIN_CHUNK);
+        for (int row = 0; row < rows; ++row) {
+            const float *src = row == 0 ? a.part : a.part2;
+            float H = 0.f, Lo = 0.f;
+            long long cacc = 0;
+#pragma unroll 8
+            for (int g = i0 + w; g < i1; g += FIN_RED_THREADS / 32) {
+                const float *p = src + (size_t)g * 64;
+                const float h = p[lane], l = p[32 + lane];
+                const float sm = H + h;
+                const float bp = sm - H;
+                const float err = (H - (sm - bp)) + (h - bp);
+                H = sm;
+                Lo += l + err;
+                if (row == 0 && lane < 3) cacc += a.counts[(size_t)g * 4 + lane];
+            }
+            red[w][32 * row + lane] = (double)H + (double)Lo;
+            if (row == 0 && lane < 4) cred[w][lane] = cacc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32 * rows) {
+            double sm = 0.0;
+#pragma unroll
+            for (int q = 0; q < FIN_RED_THREADS / 32; ++q) sm += red[q][threadIdx.x];
+            a.chunk[(size_t)c * 64 + threadIdx.x] = sm;
+        }
+        if (threadIdx.x < 4) {
+            long long cs = 0;
+#pragma unroll
+            for (int q = 0; q < FIN_RED_THREADS / 32; ++q) cs += cred[q][threadIdx.x];
+            a.chunk_cnt[(size_t)c * 4 + threadIdx.x] = cs;
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per problem: the sums over its chunk rows in chunk order (FP64),
+// then the per-problem FP64 step on lane 0.
+__global__ void __launch_bounds__(FIN_STEP_WARPS * 32) k_fin_step(FinalizeArgs a) {
+    __shared__ double tot[FIN_STEP_WARPS][64];
+    __shared__ long long ctot[FIN_STEP_WARPS][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int prob = blockIdx.x * FIN_STEP_WARPS + w;
     if (prob >= a.n_problems) return;
     ProbDev *P = a.probs + prob;
     if (P->status != 0) return;
     if (a.mode == FIN_POSE) {
-        if (threadIdx.x == 0) refresh_pose(a, prob, P);
+        if (lane == 0) refresh_pose(a, prob, P);
         return;
     }
-    __shared__ double red[FIN_THREADS];
-    __shared__ long long cred[FIN_THREADS];
-    __shared__ double tot[64];
-    __shared__ long long ctot[4];
-    const int g0 = P->w0, g1 = P->w1;   // packed work items of this problem
-    const int slot = threadIdx.x & 31, part = threadIdx.x >> 5;
-    // the G-CVO-E pass leaves slots 32..45 in a second partial row per item
-    // (its slots 46..63 are never written, and their sums never read)
     const int rows = (a.mode == FIN_EXACT || a.mode == FIN_EXACT_EVAL) ? 2 : 1;
+    const int c0 = P->c0, c1 = P->c1;
     for (int row = 0; row < rows; ++row) {
-        const float *src = row == 0 ? a.part : a.part2;
-        // compensated FP32 sum of the (hi, lo) group partials, one FP64 combine
-        float H = 0.f, Lo = 0.f;
-        long long cacc = 0;
-#pragma unroll 4
-        for (int g = g0 + part; g < g1; g += FIN_THREADS / 32) {
-            const float *p = src + (size_t)g * 64;
-            float h = p[slot], l = p[32 + slot];
-            float sm = H + h;
-            float bp = sm - H;
-            float err = (H - (sm - bp)) + (h - bp);
-            H = sm;
-            Lo += l + err;
-            if (row == 0 && slot < 3) cacc += a.counts[(size_t)g * 4 + slot];
-        }
-        red[threadIdx.x] = (double)H + (double)Lo;
-        cred[threadIdx.x] = cacc;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double sm = 0.0;
-            long long cs = 0;
-#pragma unroll 8
-            for (int q = 0; q < FIN_THREADS / 32; ++q) {
-                sm += red[q * 32 + threadIdx.x];
-                cs += cred[q * 32 + threadIdx.x];
-            }
-            tot[32 * row + threadIdx.x] = sm;
-            if (row == 0 && threadIdx.x < 4) ctot[threadIdx.x] = cs;
-        }
-        __syncthreads();
+        double sm = 0.0;
+        for (int c = c0; c < c1; ++c) sm += a.chunk[(size_t)c * 64 + 32 * row + lane];
+        tot[w][32 * row + lane] = sm;
     }
-    if (threadIdx.x == 0 && finalize_thread0(a, prob, P, tot, ctot)) refresh_pose(a, prob, P);
+    if (lane < 4) {
+        long long cs = 0;
+        for (int c = c0; c < c1; ++c) cs += a.chunk_cnt[(size_t)c * 4 + lane];
+        ctot[w][lane] = cs;
+    }
+    __syncwarp();
+    if (lane == 0 && finalize_thread0(a, prob, P, tot[w], ctot[w])) refresh_pose(a, prob, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -651,6 +688,7 @@ __global__ void k_src_keys(SrcArgs a) {
         }
         float l = sym3_max_eig(s[0], s[1], s[2], s[3], s[4], s[5]);
         atomicMax(a.lam_enc + p, enc_f(l));
+        atomicMin(a.lam_min_enc + p, enc_f(sym3_min_eig(s[0], s[1], s[2], s[3], s[4], s[5])));
     }
     if (bad) atomicOr(a.status_word, DEV_ERR_NONFINITE);
 }
@@ -762,7 +800,11 @@ __global__ void k_transform(TransformArgs a) {
 // Host launchers.
 // ---------------------------------------------------------------------------
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s) {
-    k_finalize<<<a.n_problems, FIN_THREADS, 0, s>>>(a);
+    if (a.mode != FIN_POSE) {
+        k_fin_reduce<<<(unsigned)(a.reduce_blocks > 0 ? a.reduce_blocks : 1024), FIN_RED_THREADS, 0, s>>>(a);
+        count_launches(1);
+    }
+    k_fin_step<<<(unsigned)((a.n_problems + FIN_STEP_WARPS - 1) / FIN_STEP_WARPS), FIN_STEP_WARPS * 32, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }

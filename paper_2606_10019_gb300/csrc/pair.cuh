@@ -43,6 +43,8 @@ struct ProbDev {
     int status;        // 0 active, 1 converged, 2 k_max reached, < 0: -gcvo_status
     int iter;
     int w0, w1;        // range of packed work items
+    int c0, c1;        // range of finalize chunks (FIN_CHUNK work items each)
+    int lo;            // 1: the pair passes form r from double-float positions
     float rho2;        // Euclidean pre-test radius squared
     float c2;          // cutoff squared
     float sigma2;
@@ -75,12 +77,29 @@ struct PairArgs {
     int ls_literal;
 };
 
+// The finalize runs in two launches: k_fin_reduce sums the work items of
+// every chunk (FIN_CHUNK consecutive items of one problem) into one FP64 row,
+// then k_fin_step, one warp per problem, adds its chunks' rows in order and
+// takes the FP64 step.  The chunk rows depend only on the problem's own
+// items, so a problem's result does not depend on the rest of the batch.
+constexpr int FIN_CHUNK = 256;
+
+// Bytes of the chunk rows for at most n_items work items over np problems.
+inline size_t fin_chunk_bytes(int64_t n_items, int np) {
+    const size_t chunks = (size_t)(n_items / FIN_CHUNK) + (size_t)np + 1;
+    return chunks * (64 * sizeof(double) + 4 * sizeof(long long));
+}
+
 struct FinalizeArgs {
     ProbDev *probs;
     const GridDev *grids;
     const float *part;
     const float *part2;        // FIN_EXACT*: slots 32..
     const long long *counts;
+    double *chunk;             // per chunk: 64 FP64 slot sums
+    long long *chunk_cnt;      // per chunk: 4 count sums
+    const int *n_chunks;       // chunks of all problems (written when items are packed)
+    int reduce_blocks;         // grid of k_fin_reduce (a few blocks per SM)
     EvalOut *evalout;
     gcvo_iter_log *logs;
     int *n_active;
@@ -100,7 +119,8 @@ struct SrcArgs {
     const SrcDesc *desc;
     unsigned long long *keys;
     int *vals, *prob_of, *local;
-    int *lam_enc;
+    int *lam_enc;              // per problem: largest source covariance eigenvalue (ordered int)
+    int *lam_min_enc;          // per problem: smallest
     unsigned *status_word;
     float4 *spos, *sca, *scb;
     float4 *sfx;               // feature channels 3..6 (null when feat_dim <= 3)
@@ -139,6 +159,6 @@ cudaError_t launch_transform(const TransformArgs &a, cudaStream_t s);
 // tmp: 3 x round_up(n, 64) ints.
 gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, int level,
                        const int64_t *point_off, const int *n_pts, int *tmp, int *items, int *item_prob,
-                       int *d_nitems, ProbDev *probs, void *scan_tmp, cudaStream_t s);
+                       int *d_nitems, ProbDev *probs, int *n_chunks, void *scan_tmp, cudaStream_t s);
 
 }  // namespace gcvo

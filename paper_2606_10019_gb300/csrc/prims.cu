@@ -297,11 +297,12 @@ __global__ void bbox_init(int *out) {
     else if (threadIdx.x < 6) out[threadIdx.x] = enc(-INFINITY);
     else if (threadIdx.x == 6) out[6] = enc(0.0f);
     else if (threadIdx.x == 7) out[7] = 0;
+    else if (threadIdx.x == 8) out[8] = enc(INFINITY);
 }
 
 __global__ void bbox_kernel(const float *xyz, const float *cov, int64_t n, int *out) {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    float lam = 0.0f;
+    float lam = 0.0f, lmin = INFINITY;
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         for (int a = 0; a < 3; ++a) {
@@ -319,6 +320,7 @@ __global__ void bbox_kernel(const float *xyz, const float *cov, int64_t n, int *
             float l = sym3_max_eig(c[0], c[1], c[2], c[3], c[4], c[5]);
             if (c[0] <= 0.0f || c[3] <= 0.0f || c[5] <= 0.0f) bad |= 2;
             lam = fmaxf(lam, l);
+            lmin = fminf(lmin, sym3_min_eig(c[0], c[1], c[2], c[3], c[4], c[5]));
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -327,6 +329,7 @@ __global__ void bbox_kernel(const float *xyz, const float *cov, int64_t n, int *
             mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
         lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+        lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
@@ -335,6 +338,7 @@ __global__ void bbox_kernel(const float *xyz, const float *cov, int64_t n, int *
             atomicMax(out + 3 + a, enc(mx[a]));
         }
         atomicMax(out + 6, enc(lam));
+        atomicMin(out + 8, enc(lmin));
         if (bad) atomicOr(out + 7, bad);
     }
 }

@@ -41,11 +41,18 @@
 // SemanticCVO) in one more float4 stream staged beside the others.
 // The G-CVO-E pass (PAIR_EXACT) visits the same pairs and adds the sums of
 // the exact directional derivative of g (pair_exact); its 46 values per
-// sub-tile go to two partial rows.  The exact derivative is far more
-// sensitive to the positions than H_GN (its weight-change and Gauss-Newton
-// terms each reach several times its norm and cancel), so that pass forms
-// r from double-float positions on both sides: r = (x_hi - p_hi) +
-// (x_lo - p_lo), with the target grid's tails staged beside the points.
+// sub-tile go to two partial rows.
+// Every pass forms r from double-float positions on both sides:
+// r = (x_hi - p_hi) + (x_lo - p_lo), with the target grid's tails staged
+// beside the points.  Positions are relative to the target box centre, and
+// a LiDAR frame reaches 50-100 m from it, where FP32 rounds a position by
+// 3-6 um.  With the flattest clamped covariances (sigma about 3 cm) that
+// moves each pair's d^2 by about 1e-3 and the gradient sums by about 1e-5
+// of their scale, which is the tolerance itself.  The exact derivative is
+// more sensitive still: its weight-change and Gauss-Newton terms each reach
+// several times its norm and cancel.
+#include <type_traits>
+
 #include "common.cuh"
 #include "pair.cuh"
 #include "ptx.cuh"
@@ -71,6 +78,12 @@ struct __align__(16) WarpStage {
     unsigned short list[PAIR_WCAP];
     uint64_t bar;
 };
+
+// The stage of one warp in a pass of mode MODE with FD feature channels:
+// the kernel's layout and the launch's dynamic shared memory both come from
+// this one type.  Every pass stages the target tails (r in double-float).
+template <int MODE, int FD>
+using StageT = WarpStage<true, (FD > 3)>;
 
 // One anisotropic pair (Eq. 7), r = x_i - p_j, into the lane sums t[10].
 template <int FD>
@@ -258,21 +271,24 @@ __device__ __forceinline__ void ls_terms(float wgt, float kr1, float kr2, float 
 }
 
 template <int MODE, bool ISO, int FD, int SUB>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_tile(PairArgs a) {
+__global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_tile(PairArgs a) {
     static_assert(SUB == 4 || SUB == 8 || SUB == 16 || SUB == 32, "sub-tile of 4, 8, 16 or 32 points");
     static_assert(FD == 1 || FD == 3 || FD == 7, "1, up to 3 or up to 7 feature channels");
     constexpr int TQ = 32 / SUB;    // targets per warp step
     constexpr int NT = MODE == PAIR_EVAL ? 10 : MODE == PAIR_EXACT ? 25 : 5;
     constexpr int NSLOT = MODE == PAIR_EVAL ? PAIR_SLOTS : MODE == PAIR_EXACT ? PAIR_SLOTS_EXACT : 5;
-    constexpr bool LO = MODE == PAIR_EXACT;
+    // r from double-float positions in every pass (see the header comment)
+    constexpr bool LO = true;
     constexpr bool FX = FD > 3;
+    using Stage = StageT<MODE, FD>;
+    static_assert(std::is_same<Stage, WarpStage<LO, FX>>::value, "the stage type matches LO and FX");
     extern __shared__ __align__(16) unsigned char smem_raw[];   // PAIR_WARPS stages
-    WarpStage<LO, FX> *stage = reinterpret_cast<WarpStage<LO, FX> *>(smem_raw);
+    Stage *stage = reinterpret_cast<Stage *>(smem_raw);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qi = lane / SUB, si = lane % SUB;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    WarpStage<LO, FX> &S = stage[w];
+    Stage &S = stage[w];
     if (lane == 0) mbar_init(&S.bar, 1);
     __syncwarp();
     unsigned parity = 0;
@@ -309,6 +325,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         const unsigned word = (unsigned)__shfl_sync(FULL, my_word, src_lane);
         const ProbDev *P = a.probs + prob;
         const GridDev *G = a.grids + prob;
+        // double-float r for this problem (the same for the whole warp)
+        const bool dfr = MODE == PAIR_EXACT || P->lo != 0;
         // the sub-tile: first point << 6 | points
         const int j0 = (int)(word >> 6), cnt = (int)(word & 63u);
         const bool sval = si < cnt;
@@ -336,8 +354,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
         }
         float4 lf = make_float4(0.f, 0.f, 0.f, 0.f);   // sigma^2 l3..l6
         if (FX) lf = a.tfx[jj];
-        float plx = 0.f, ply = 0.f, plz = 0.f;   // tail of p (G-CVO-E pass)
-        if (LO) {
+        float plx = 0.f, ply = 0.f, plz = 0.f;   // tail of p
+        if (dfr) {
             const float4 L4 = a.tlo[jj];
             plx = L4.x;
             ply = L4.y;
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                 // ---- stage the chunk [base, base + m) (bulk copies)
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (48u + (LO ? 16u : 0u) + (FX ? 16u : 0u)));
+                if (lane == 0) mbar_arrive_expect_tx(&S.bar, (unsigned)m * (48u + (dfr ? 16u : 0u) + (FX ? 16u : 0u)));
                 __syncwarp();
                 {
                     const int s0 = max(off, base), s1 = min(off + rl, base + m);
@@ -446,7 +464,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                         bulk_g2s(S.pos + dst, G->pos + src, bytes, &S.bar);
                         bulk_g2s(S.ca + dst, G->ca + src, bytes, &S.bar);
                         bulk_g2s(S.cb + dst, G->cb + src, bytes, &S.bar);
-                        if (LO) bulk_g2s(S.lo + dst, G->plo + src, bytes, &S.bar);
+                        if (dfr) bulk_g2s(S.lo + dst, G->plo + src, bytes, &S.bar);
                         if (FX) bulk_g2s(S.fx + dst, G->fx + src, bytes, &S.bar);
                     }
                 }
@@ -491,7 +509,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 6 : 4) k_
                     const int k = S.list[min(idx, L - 1)];
                     const float4 x = S.pos[k];
                     float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
-                    if (LO) {
+                    if (dfr) {
                         // r = (x_hi - p_hi) + (x_lo - p_lo)
                         const float4 xl = S.lo[k];
                         r0 += xl.x - plx;
@@ -757,6 +775,32 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
     probs[p].w1 = sid[f + n_pts[p] - 1];
 }
 
+// One block: each problem's finalize chunks (FIN_CHUNK of its work items
+// each) get consecutive indices [c0, c1); *n_chunks receives the total.
+constexpr int CHUNK_THREADS = 1024;
+__global__ void __launch_bounds__(CHUNK_THREADS) k_chunk_ranges(int np, ProbDev *probs, int *n_chunks) {
+    __shared__ int sc[CHUNK_THREADS];
+    const int per = (np + CHUNK_THREADS - 1) / CHUNK_THREADS;
+    const int p0 = threadIdx.x * per, p1 = min(np, p0 + per);
+    int acc = 0;
+    for (int p = p0; p < p1; ++p) acc += (probs[p].w1 - probs[p].w0 + FIN_CHUNK - 1) / FIN_CHUNK;
+    sc[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 1; o < CHUNK_THREADS; o <<= 1) {
+        const int v = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+        __syncthreads();
+        sc[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int c = sc[threadIdx.x] - acc;
+    for (int p = p0; p < p1; ++p) {
+        probs[p].c0 = c;
+        c += (probs[p].w1 - probs[p].w0 + FIN_CHUNK - 1) / FIN_CHUNK;
+        probs[p].c1 = c;
+    }
+    if (threadIdx.x == CHUNK_THREADS - 1) *n_chunks = sc[threadIdx.x];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -766,7 +810,7 @@ __global__ void k_item_ranges(int np, const int64_t *point_off, const int *n_pts
 // above the 48 KB default made once per kernel instance.
 template <int MODE, int FD>
 constexpr size_t tile_smem_bytes() {
-    return PAIR_WARPS * sizeof(WarpStage<MODE == PAIR_EXACT, (FD > 3)>);
+    return PAIR_WARPS * sizeof(StageT<MODE, FD>);
 }
 
 template <int MODE, bool ISO, int FD, int SUB>
@@ -828,7 +872,7 @@ cudaError_t launch_pair(const PairArgs &a, int mode, bool iso, int fd, int sub, 
 
 gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int sub, int level,
                        const int64_t *point_off, const int *n_pts, int *tmp, int *items, int *item_prob,
-                       int *d_nitems, ProbDev *probs, void *scan_tmp, cudaStream_t s) {
+                       int *d_nitems, ProbDev *probs, int *n_chunks, void *scan_tmp, cudaStream_t s) {
     if (n >= (1LL << 26) || (sub != 4 && sub != 8 && sub != 16 && sub != 32) || level < 0 || level > 3)
         return GCVO_ERR_CAPACITY;
     const size_t stride = ((size_t)n + 63) / 64 * 64;
@@ -846,7 +890,8 @@ gcvo_status pack_items(int np, const unsigned long long *keys, int64_t n, int su
     k_sub_count<<<blocks, 256, 0, s>>>(sid, n, cnt);
     k_fill_items<<<blocks, 256, 0, s>>>(keys, sid, cnt, n, items, item_prob);
     k_item_ranges<<<(np + 127) / 128, 128, 0, s>>>(np, point_off, n_pts, sid, probs);
-    count_launches(3);
+    k_chunk_ranges<<<1, CHUNK_THREADS, 0, s>>>(np, probs, n_chunks);
+    count_launches(4);
     GCVO_CUDA(cudaGetLastError());
     GCVO_CUDA(cudaMemcpyAsync(d_nitems, sid + n - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
     return GCVO_OK;

@@ -23,6 +23,20 @@ def rel_g(g, go, gabs):
     return float(np.abs(np.asarray(g) - go).max() / max(np.abs(go).max(), np.asarray(gabs).max(), 1e-300))
 
 
+def rel_f_near(f, o):
+    """rel_f after taking off the terms of the pairs within 1e-4 c^2 of the
+    cutoff (the FP32 cutoff test of the kernel may decide them the other way
+    than the FP64 one of the oracle)."""
+    return max(0.0, abs(f - o.f) - o.f_near) / max(abs(o.f), 1e-300)
+
+
+def rel_g_near(g, o):
+    """rel_g after taking off, per component, the terms of the pairs within
+    1e-4 c^2 of the cutoff."""
+    d = np.maximum(np.abs(np.asarray(g) - o.g) - o.g_near, 0.0)
+    return float(d.max() / max(np.abs(o.g).max(), np.asarray(o.gabs).max(), 1e-300))
+
+
 def rel_H(H, Ho):
     return float(np.linalg.norm(np.asarray(H) - Ho) / max(np.linalg.norm(Ho), 1e-300))
 

@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import POSE_TOL, TOL, Case, rel_H, rel_f, rel_g, soa
+from helpers import POSE_TOL, TOL, Case, rel_H, rel_f, rel_f_near, rel_g, rel_g_near, soa
 from paper_2606_10019_gb300 import datagen as D
 
 pytestmark = pytest.mark.gpu
@@ -293,8 +293,10 @@ def test_register_first_order_lidar_long_run_steps_match_oracle(env):
     for k in (0, 1, 2, 5, 10, 25, 50, 100, 200, 300, K - 1):
         Tk = log[k]["T"]
         o = O.evaluate(case.prob, Tk, case.kp_o)
-        assert rel_f(log[k]["f"], o.f) <= TOL, k
-        assert rel_g(log[k]["g"], o.g, o.gabs) <= TOL, k
+        # a pair that lands within 1e-4 c^2 of the cutoff at an iterate may be
+        # kept by one side and not the other: its own terms are allowed for
+        assert rel_f_near(log[k]["f"], o) <= TOL, k
+        assert rel_g_near(log[k]["g"], o) <= TOL, (k, o.n_near_cut)
         c = O.linesearch_poly(case.prob, Tk, o.g, case.kp_o)
         mu_o = O.linesearch_step(c, 1e-10)
         mu_g = np.linalg.norm(log[k]["xi"]) / np.linalg.norm(log[k]["g"])

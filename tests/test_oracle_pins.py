@@ -647,3 +647,32 @@ def test_label_features_are_a_sum_over_classes(oracle_mod):
              for c in range(L)]
     assert soft.f == pytest.approx(sum(p.f for p in parts), rel=1e-12)
     assert np.allclose(soft.g, sum(p.g for p in parts), rtol=1e-11, atol=1e-12 * np.abs(soft.g).max())
+
+
+def test_near_cutoff_terms_single_pair(oracle_mod):
+    """The near-cutoff report on one isotropic pair (Remark 3: Sigma_ij =
+    ell^2 I, so d^2 = |r|^2 / ell^2), placed just inside, just outside and
+    well inside the cutoff c = 3 (Eq. 7: the pair is kept iff d^2 <= c^2):
+    f_near and g_near are that pair's own |f_ij| and |g^(ij)| whenever
+    |d^2 - c^2| < 1e-4 c^2, kept or not, and zero otherwise; f and g are the
+    pair's terms only when it is kept."""
+    O = oracle_mod
+    ell, c, s2 = 0.5, 3.0, 1.3
+    kp = O.KernelParams(kernel_mode=1, sigma2=s2, cutoff=c, iso_ell=ell)
+    u = np.array([2.0, -1.0, 2.0]) / 3.0            # unit direction
+    p = np.array([[0.4, 0.1, -0.2]])
+    lf = np.array([[0.6, 0.8, 0.0]])
+    for rel, near, kept in ((-5e-5, True, True), (5e-5, True, False), (-3e-4, False, True)):
+        d2 = c * c * (1.0 + rel)
+        x = p + ell * np.sqrt(d2) * u
+        prob = O.Problem.make(x, None, lf, p, None, lf)
+        r = O.evaluate(prob, np.eye(4), kp)
+        fij = s2 * 1.0 * np.exp(-0.5 * d2)           # c_ij = <l, l> = 1
+        w = (x - p)[0] / ell ** 2                     # Sigma^-1 r
+        g_terms = np.r_[-fij * np.cross(p[0], w), -fij * w]
+        assert r.n_near_cut == (1 if near else 0)
+        assert r.n_kept == (1 if kept else 0)
+        assert r.f == pytest.approx(fij if kept else 0.0, rel=1e-12, abs=1e-300)
+        assert np.allclose(r.g, g_terms if kept else 0.0, rtol=1e-12, atol=1e-300)
+        assert r.f_near == pytest.approx(fij if near else 0.0, rel=1e-12, abs=1e-300)
+        assert np.allclose(r.g_near, np.abs(g_terms) if near else 0.0, rtol=1e-12, atol=1e-300)
