@@ -558,7 +558,7 @@ __global__ void k_knn_cov(const GridDev *g, const KnnCloud *cl, const float4 *P,
 }  // namespace
 
 void launch_knn_far(const GridDev *gc, const KnnCloud *cl, const float4 *P, const int *list, const int *n_list,
-                    unsigned *status, int blocks, cudaStream_t s);
+                    int *next, unsigned *status, int sm_count, int64_t m_max, cudaStream_t s);
 
 size_t knn_meta_bytes(int64_t n_points, int n_clouds) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -665,10 +665,12 @@ gcvo_status knn_cov_group(gcvo_ctx *ctx, int n_clouds, const KnnJob *jobs) {
     int *list1 = ctx->knn_retry.as<int>();
     int *list2 = list1 + N;
     unsigned *stw = ctx->status_word.as<unsigned>();
-    int *n_list = reinterpret_cast<int *>(stw + 1);   // [0]: after the fine grid, [1]: after the middle grid
+    // [0]: points left after the fine grid, [1]: after the middle grid,
+    // [2]: work counter of the coarse pass
+    int *n_list = reinterpret_cast<int *>(stw + 1);
     GCVO_CUDA(cudaMemcpyAsync(d_cl, cl.data(), C * sizeof(KnnCloud), cudaMemcpyHostToDevice, s));
     GCVO_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-    GCVO_CUDA(cudaMemsetAsync(stw, 0, 3 * sizeof(unsigned), s));
+    GCVO_CUDA(cudaMemsetAsync(stw, 0, 4 * sizeof(unsigned), s));
 
     // gather, boxes, voxel sizes
     auto *hset = sb.hkeys.as<unsigned long long>();   // free until the middle grid is built
@@ -720,8 +722,7 @@ gcvo_status knn_cov_group(gcvo_ctx *ctx, int n_clouds, const KnnJob *jobs) {
 
     // pass 3: the rest, one warp per point on the coarse grids, no shell limit
     GCVO_TRY(kc_build(ctx, P, N, d_cl, d_g[2], tot[2], H, sa));
-    const int far_blocks = (int)std::min<int64_t>((m2 + 3) / 4, (int64_t)sm * 4);
-    launch_knn_far(d_g[2], d_cl, P, list2, n_list + 1, stw, far_blocks, s);
+    launch_knn_far(d_g[2], d_cl, P, list2, n_list + 1, n_list + 2, stw, sm, m2, s);
     count_launches(1);
     GCVO_CUDA(cudaGetLastError());
     unsigned hs = 0;

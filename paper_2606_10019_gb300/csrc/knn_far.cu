@@ -1,6 +1,8 @@
 // Pass 3 of the kNN covariances: the points whose neighbours lie beyond the
 // fine and middle grids' two shells (a separate translation unit so that it
 // compiles in parallel with grid.cu).
+#include <algorithm>
+
 #include "common.cuh"
 #include "knn.cuh"
 
@@ -14,13 +16,18 @@ using namespace knn;
 // private sorted lists; after every shell the warp merges them (repeated
 // warp-wide minimum over each lane's next entry) into the knn nearest so
 // far, and stops once the knn-th distance is within the shells' reach.
+// The searches differ in length by orders of magnitude (one shell or
+// dozens), so each warp takes its next point from a counter as it finishes.
 __global__ void k_knn_cov_far(const GridDev *gcs, const KnnCloud *cl, const float4 *P, const int *list,
-                              const int *n_list, unsigned *status) {
+                              const int *n_list, int *next, unsigned *status) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
     const int m = *n_list;
-    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < m; t += gridDim.x * wpb) {
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(next, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= m) break;
         const int j = list[t];
         const float4 q = P[j];
         const int cloud = cloud_of(q);
@@ -161,9 +168,18 @@ __global__ void k_knn_cov_far(const GridDev *gcs, const KnnCloud *cl, const floa
 
 }  // namespace
 
+// One resident wave: as many blocks of 4 warps as fit on the GPU, at most
+// one warp per queued point (m_max).  next: zeroed work counter.
 void launch_knn_far(const GridDev *gc, const KnnCloud *cl, const float4 *P, const int *list, const int *n_list,
-                    unsigned *status, int blocks, cudaStream_t s) {
-    k_knn_cov_far<<<blocks, 128, 0, s>>>(gc, cl, P, list, n_list, status);
+                    int *next, unsigned *status, int sm_count, int64_t m_max, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_knn_cov_far, 128, 0) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m_max + 3) / 4, (int64_t)per_sm * sm_count));
+    k_knn_cov_far<<<(unsigned)blocks, 128, 0, s>>>(gc, cl, P, list, n_list, next, status);
 }
 
 }  // namespace gcvo
