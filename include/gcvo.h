@@ -173,10 +173,12 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx);
  * clouds together count as its points, and it takes at most
  * 2 x max_problems clouds) and gcvo_build_grid / gcvo_rebuild_grid make no
  * device allocation for their scratch (a grid still owns its own storage),
- * and a call beyond the limits returns GCVO_ERR_WORKSPACE.  The calls that
- * build several grids concurrently (gcvo_build_grids_batched,
- * gcvo_register_clouds) use internal child contexts that allocate their own
- * scratch.  dev_ptr = NULL returns the context to library-owned
+ * and a call beyond the limits returns GCVO_ERR_WORKSPACE.
+ * gcvo_build_grids_batched and gcvo_register_clouds use the same scratch
+ * for all their clouds together: with a workspace set they fit when their
+ * clouds hold at most max_points points together (at most 2 x max_problems
+ * clouds) and only one of their grids reaches the 2^26-voxel limit, and
+ * return GCVO_ERR_WORKSPACE otherwise.  dev_ptr = NULL returns the context to library-owned
  * scratch.  gcvo_set_workspace synchronises the stream and may allocate
  * the context's small pinned host buffer.  The paper has no counterpart:
  * this is the memory ownership of the boundary. */
@@ -197,12 +199,14 @@ gcvo_status gcvo_estimate_covariances(gcvo_ctx *ctx, const float *xyz, int64_t n
 
 /* Build the voxel grid of a target cloud X (Eq. 5's x_i with Sigma(x_i; X)
  * and features l_i^X): points are keyed by voxel, sorted, copied into a
- * grid-owned packed layout relative to the box centre, and indexed by a
- * dense per-voxel prefix table over the box (the pair kernel's index;
- * voxels are coarsened while the box holds more than 2^26 of them) and an
- * open-addressing hash of the occupied voxels.  cov may be NULL in
- * kernel_mode 1.  The grid keeps the kernel parameters it was built with.
- * Synchronises the stream. */
+ * grid-owned packed layout relative to the box centre (FP32 heads and
+ * tails of x - o), and indexed by a dense per-voxel prefix table over the
+ * box (the pair kernel's index; voxels are coarsened while the box holds
+ * more than 2^26 of them).  cov may be NULL in kernel_mode 1.  The grid
+ * keeps the kernel parameters it was built with.  A non-finite coordinate,
+ * covariance or feature returns GCVO_ERR_NONFINITE, a covariance with a
+ * non-positive diagonal entry GCVO_ERR_INVALID_ARG.  Synchronises the
+ * stream. */
 gcvo_status gcvo_build_grid(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat,
                             int64_t n, const gcvo_kernel_params *params, gcvo_grid **grid_out);
 
@@ -233,11 +237,15 @@ gcvo_status gcvo_estimate_covariances_batched(gcvo_ctx *ctx, int n_clouds, const
                                               float *const *cov_out);
 
 /* gcvo_build_grid / gcvo_rebuild_grid for n_clouds target clouds in one
- * call, concurrently as in gcvo_estimate_covariances_batched: grids[k] ==
- * NULL builds a new grid into grids[k], otherwise grids[k] is rebuilt in
- * place.  Inputs as for gcvo_build_grid, per cloud, device memory only
- * (cov may be NULL in kernel_mode 1).  Returns the first failure; grids
- * built before it stay valid and belong to the caller. */
+ * call: grids[k] == NULL builds a new grid into grids[k], otherwise
+ * grids[k] is rebuilt in place.  Inputs as for gcvo_build_grid, per cloud,
+ * device memory only (cov may be NULL in kernel_mode 1).  All clouds share
+ * one set of launches on the context's stream (one box pass with one
+ * read-back, one sort of all points, one segmented scan of the voxel
+ * tables), and every grid equals the one gcvo_build_grid makes of its
+ * cloud.  On failure no new grid is returned (grids[k] is NULL again where
+ * it was NULL) and the grids given for a rebuild may only be destroyed or
+ * rebuilt.  Synchronises the stream. */
 gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *const *xyz,
                                      const float *const *cov, const float *const *feat, const int64_t *n,
                                      const gcvo_kernel_params *params, gcvo_grid **grids);

@@ -3,7 +3,6 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -696,56 +695,6 @@ gcvo_status run_register(gcvo_ctx *ctx, int np, const gcvo_problem *pr, const gc
     return GCVO_OK;
 }
 
-// Runs fn(child, k) for k = 0 .. n-1 on up to GCVO_LANES child contexts,
-// one host thread each, every child on its own stream.  The children's work
-// starts after everything already queued on ctx->stream and ctx->stream
-// waits for all of it, so the call is stream-ordered like the single-cloud
-// calls.  Returns the first failure.
-constexpr int GCVO_LANES = 8;
-
-template <class F>
-gcvo_status run_lanes(gcvo_ctx *ctx, int n, F fn) {
-    const int K = std::min(GCVO_LANES, n);
-    while ((int)ctx->lanes.size() < K) {
-        cudaStream_t ls;
-        GCVO_CUDA(cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking));
-        gcvo_ctx *c = nullptr;
-        gcvo_status st = gcvo_create(&c, ctx->device, ls);
-        if (st != GCVO_OK) {
-            cudaStreamDestroy(ls);
-            return st;
-        }
-        ctx->lanes.push_back(c);
-        ctx->lane_streams.push_back(ls);
-    }
-    cudaEvent_t start;
-    GCVO_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    GCVO_CUDA(cudaEventRecord(start, ctx->stream));
-    std::vector<gcvo_status> st(K, GCVO_OK);
-    std::vector<std::thread> th;
-    for (int j = 0; j < K; ++j) {
-        th.emplace_back([&, j]() {
-            gcvo_ctx *c = ctx->lanes[j];
-            if (cudaSetDevice(ctx->device) != cudaSuccess || cudaStreamWaitEvent(c->stream, start, 0) != cudaSuccess) {
-                st[j] = GCVO_ERR_CUDA;
-                return;
-            }
-            for (int k = j; k < n && st[j] == GCVO_OK; k += K) st[j] = fn(c, k);
-        });
-    }
-    for (auto &t : th) t.join();
-    gcvo_status out = GCVO_OK;
-    for (int j = 0; j < K; ++j) {
-        if (out == GCVO_OK) out = st[j];
-        cudaEvent_t done;
-        GCVO_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-        GCVO_CUDA(cudaEventRecord(done, ctx->lanes[j]->stream));
-        GCVO_CUDA(cudaStreamWaitEvent(ctx->stream, done, 0));
-        cudaEventDestroy(done);
-    }
-    cudaEventDestroy(start);
-    return out;
-}
 
 // ---------------------------------------------------------------------------
 // Caller-owned workspace: every scratch buffer of the single-stream calls
@@ -763,7 +712,7 @@ std::vector<DevBuf *> ws_bufs(gcvo_ctx *c) {
                                &c->src_fx,    &c->t_fx,
                                &c->items,     &c->item_prob, &c->pack_tmp, &c->partial,   &c->partial2,
                                &c->probs,     &c->grids,     &c->evalout,  &c->logs,      &c->status_word,
-                               &c->knn_retry,  &c->knn_meta,  &c->knn_grid.ca};
+                               &c->knn_retry,  &c->knn_meta,  &c->knn_grid.ca, &c->grid_meta, &c->grid_tiles};
     for (GridStore *g : {&c->knn_grid, &c->knn_grid2})
         for (DevBuf *b : {&g->pos, &g->orig, &g->cell_start, &g->hkeys, &g->hval}) v.push_back(b);
     return v;
@@ -798,7 +747,9 @@ std::vector<size_t> ws_sizes(int64_t N, int64_t np, int64_t rows) {
         256,                                                            // status_word
         2 * n * sizeof(int) + 256,                                      // knn_retry: two point lists
         knn_meta_bytes((int64_t)n, (int)std::min<int64_t>(2 * np, (int64_t)n)),   // knn_meta
-        n * sizeof(float4)};                                            // knn_grid.ca: gathered points
+        n * sizeof(float4),                                             // knn_grid.ca: gathered points
+        tgrid_meta_bytes((int)std::min<int64_t>(2 * np, (int64_t)n), (int64_t)n),   // grid_meta
+        tgrid_tile_bytes(tgrid_max_tiles(1) + 2 * np)};                 // grid_tiles: one grid of 2^26 voxels
     for (int g = 0; g < 2; ++g)
         for (size_t b : {n * sizeof(float4), n * sizeof(int), (n + 1) * sizeof(int), H * sizeof(unsigned long long),
                          H * sizeof(int)})
@@ -893,12 +844,12 @@ gcvo_status gcvo_destroy(gcvo_ctx *ctx) {
     }
     ctx->knn_retry.release();
     ctx->knn_meta.release();
+    ctx->grid_meta.release();
+    ctx->grid_tiles.release();
     ctx->clouds_stage.release();
     ctx->clouds_cov.release();
     for (gcvo_grid *g : ctx->clouds_grids)
         if (g) gcvo_grid_destroy(g);
-    for (gcvo_ctx *c : ctx->lanes) gcvo_destroy(c);
-    for (cudaStream_t ls : ctx->lane_streams) cudaStreamDestroy(ls);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -993,11 +944,9 @@ static gcvo_status build_into(gcvo_ctx *ctx, const float *xyz, const float *cov,
     GCVO_TRY(stage(ctx, xyz, 3 * (size_t)n, ctx->stage_xyz, off, &dx));
     if (params->kernel_mode == 0) GCVO_TRY(stage(ctx, cov, 6 * (size_t)n, ctx->stage_xyz, off, &dc));
     GCVO_TRY(stage(ctx, feat, (size_t)params->feat_dim * n, ctx->stage_xyz, off, &df));
-    g->kp = *params;
     g->device = ctx->device;
-    GCVO_TRY(build_grid_store(ctx, dx, dc, df, n, *params, false, params->cell_size, g->store));
-    GCVO_CUDA(cudaStreamSynchronize(s));
-    return GCVO_OK;
+    const TgJob job{dx, dc, df, n, params, g};
+    return build_target_grids(ctx, 1, &job);
 }
 
 gcvo_status gcvo_build_grid(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
@@ -1167,12 +1116,34 @@ gcvo_status gcvo_build_grids_batched(gcvo_ctx *ctx, int n_clouds, const float *c
         if (params->kernel_mode == 0 && (!cov[k] || !is_device_ptr(cov[k]))) return GCVO_ERR_INVALID_ARG;
         if (grids[k] && grids[k]->device != ctx->device) return GCVO_ERR_INVALID_ARG;
     }
+    if (!valid_kernel_params(params)) return GCVO_ERR_INVALID_ARG;
+    for (int k = 0; k < n_clouds; ++k)
+        if (n[k] < 1 || n[k] > (1 << 28)) return GCVO_ERR_INVALID_ARG;
     GCVO_CUDA(cudaSetDevice(ctx->device));
-    return run_lanes(ctx, n_clouds, [&](gcvo_ctx *c, int k) {
-        const float *ck = params->kernel_mode == 0 ? cov[k] : nullptr;
-        if (grids[k]) return gcvo_rebuild_grid(c, grids[k], xyz[k], ck, feat[k], n[k], params);
-        return gcvo_build_grid(c, xyz[k], ck, feat[k], n[k], params, &grids[k]);
-    });
+    // new grids for the empty slots; on failure they are released again
+    std::vector<TgJob> jobs(n_clouds);
+    std::vector<char> created(n_clouds, 0);
+    gcvo_status st = GCVO_OK;
+    for (int k = 0; k < n_clouds && st == GCVO_OK; ++k) {
+        if (!grids[k]) {
+            grids[k] = new (std::nothrow) gcvo_grid();
+            if (!grids[k]) {
+                st = GCVO_ERR_WORKSPACE;
+                break;
+            }
+            grids[k]->device = ctx->device;
+            created[k] = 1;
+        }
+        jobs[k] = TgJob{xyz[k], params->kernel_mode == 0 ? cov[k] : nullptr, feat[k], n[k], params, grids[k]};
+    }
+    if (st == GCVO_OK) st = build_target_grids(ctx, n_clouds, jobs.data());
+    if (st != GCVO_OK)
+        for (int k = 0; k < n_clouds; ++k)
+            if (created[k]) {
+                gcvo_grid_destroy(grids[k]);
+                grids[k] = nullptr;
+            }
+    return st;
 }
 
 gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pair *pairs,
@@ -1237,14 +1208,23 @@ gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pa
         GCVO_TRY(knn_covariances(ctx, nc, jobs.data()));
     }
     if (ph[1]) GCVO_CUDA(cudaEventRecord(ph[1], s));
-    // the target grids, kept by the context and rebuilt in place next call
+    // the target grids, kept by the context and rebuilt in place next call,
+    // all in one batch
     if ((int)ctx->clouds_grids.size() < n_pairs) ctx->clouds_grids.resize(n_pairs, nullptr);
-    GCVO_TRY(run_lanes(ctx, n_pairs, [&](gcvo_ctx *c, int k) {
-        const float *ck = kp[k]->kernel_mode == 0 ? cov + cov_off[2 * k] : nullptr;
-        gcvo_grid *&g = ctx->clouds_grids[k];
-        if (g) return gcvo_rebuild_grid(c, g, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k]);
-        return gcvo_build_grid(c, dx[2 * k], ck, df[2 * k], n[2 * k], kp[k], &g);
-    }));
+    {
+        std::vector<TgJob> jobs(n_pairs);
+        for (int k = 0; k < n_pairs; ++k) {
+            gcvo_grid *&g = ctx->clouds_grids[k];
+            if (!g) {
+                g = new (std::nothrow) gcvo_grid();
+                if (!g) return GCVO_ERR_WORKSPACE;
+                g->device = ctx->device;
+            }
+            jobs[k] = TgJob{dx[2 * k], kp[k]->kernel_mode == 0 ? cov + cov_off[2 * k] : nullptr, df[2 * k],
+                            n[2 * k], kp[k], g};
+        }
+        GCVO_TRY(build_target_grids(ctx, n_pairs, jobs.data()));
+    }
     if (ph[2]) {
         GCVO_CUDA(cudaEventRecord(ph[2], s));
         GCVO_CUDA(cudaEventSynchronize(ph[2]));

@@ -139,11 +139,6 @@ size_t scan_scratch_bytes(int64_t n);
 gcvo_status scan_inclusive_sum(int *data, int64_t n, void *scratch, cudaStream_t s);
 gcvo_status scan_inclusive_max(int *data, int64_t n, void *scratch, cudaStream_t s);
 
-// Bounding box of a 3 x n SoA cloud and the largest and smallest
-// eigenvalues of a 6 x n SoA covariance array (cov may be null).  out: 9
-// floats (min xyz, max xyz, lam_max, flags, lam_min).
-gcvo_status bbox_lammax(const float *xyz, const float *cov, int64_t n, float *out_dev, cudaStream_t s);
-
 // Largest eigenvalue of a symmetric 3x3 (closed form, float).
 __host__ __device__ inline float sym3_max_eig(float a00, float a01, float a02, float a11, float a12, float a22) {
     float p1 = a01 * a01 + a02 * a02 + a12 * a12;
@@ -186,11 +181,21 @@ struct GridStore {
     DevBuf pos, ca, cb, plo, fx, orig, cell_start, hkeys, hval, vox_first;
 };
 
-// Build a grid from SoA inputs.  absolute: keep absolute coordinates and no
-// origin shift (kNN grid); otherwise coordinates are relative to the box
-// centre.  cell <= 0 picks cutoff * sqrt(2 lam_max) (or cutoff * iso_ell).
-gcvo_status build_grid_store(gcvo_ctx *ctx, const float *xyz, const float *cov, const float *feat, int64_t n,
-                             const gcvo_kernel_params &kp, bool absolute, double cell, GridStore &out);
+// Target grids of a batch of clouds in one set of launches (tgrid.cu):
+// cloud k (device SoA xyz, cov (null in kernel mode 1), feat; n points)
+// into grid k with its kernel parameters kp (the same kernel mode and
+// feature count for all).  The voxel edge is kp->cell_size, or half the
+// kernel range when that is <= 0.
+struct TgJob {
+    const float *xyz, *cov, *feat;
+    int64_t n;
+    const gcvo_kernel_params *kp;
+    gcvo_grid *grid;
+};
+gcvo_status build_target_grids(gcvo_ctx *ctx, int n_clouds, const TgJob *jobs);
+size_t tgrid_meta_bytes(int n_clouds, int64_t n_points);
+size_t tgrid_tile_bytes(int64_t n_tiles);
+int64_t tgrid_max_tiles(int n_clouds);
 
 // kNN covariances of a batch of clouds in one set of launches: cloud k has
 // n[k] points at xyz[k] (3 x n SoA, device) and its own parameters kp[k];
@@ -228,6 +233,7 @@ struct gcvo_ctx {
     gcvo::DevBuf partial2;                           // second partial row of the G-CVO-E pass
     gcvo::GridStore knn_grid, knn_grid2;             // reused by gcvo_estimate_covariances
     gcvo::DevBuf knn_meta;                           // its per-cloud descriptors and grids
+    gcvo::DevBuf grid_meta, grid_tiles;              // target-grid builds: per-cloud data, scan tiles
     // gcvo_register_clouds: staged host clouds, covariances and target grids
     gcvo::DevBuf clouds_stage, clouds_cov;
     std::vector<gcvo_grid *> clouds_grids;
@@ -247,9 +253,6 @@ struct gcvo_ctx {
     long long fin_launches = 0;
     double fin_ms = 0.0, transform_ms = 0.0;
     double clouds_cov_ms = 0.0, clouds_grid_ms = 0.0;   // gcvo_register_clouds phases
-    // child contexts with their own streams for the *_batched calls
-    std::vector<gcvo_ctx *> lanes;
-    std::vector<cudaStream_t> lane_streams;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     // caller-owned workspace (gcvo_set_workspace): null when the library
     // allocates its own scratch

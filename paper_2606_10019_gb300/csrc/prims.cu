@@ -282,79 +282,4 @@ gcvo_status radix_sort_pairs(unsigned long long *keys, int *vals, int64_t n, int
     return GCVO_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Bounding box and largest covariance eigenvalue.
-// ---------------------------------------------------------------------------
-namespace {
-
-__device__ inline int enc(float f) {
-    int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7fffffff;
-}
-
-__global__ void bbox_init(int *out) {
-    if (threadIdx.x < 3) out[threadIdx.x] = enc(INFINITY);
-    else if (threadIdx.x < 6) out[threadIdx.x] = enc(-INFINITY);
-    else if (threadIdx.x == 6) out[6] = enc(0.0f);
-    else if (threadIdx.x == 7) out[7] = 0;
-    else if (threadIdx.x == 8) out[8] = enc(INFINITY);
-}
-
-__global__ void bbox_kernel(const float *xyz, const float *cov, int64_t n, int *out) {
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    float lam = 0.0f, lmin = INFINITY;
-    int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        for (int a = 0; a < 3; ++a) {
-            float v = xyz[a * n + i];
-            if (!isfinite(v)) bad = 1;
-            mn[a] = fminf(mn[a], v);
-            mx[a] = fmaxf(mx[a], v);
-        }
-        if (cov) {
-            float c[6];
-            for (int q = 0; q < 6; ++q) {
-                c[q] = cov[q * n + i];
-                if (!isfinite(c[q])) bad = 1;
-            }
-            float l = sym3_max_eig(c[0], c[1], c[2], c[3], c[4], c[5]);
-            if (c[0] <= 0.0f || c[3] <= 0.0f || c[5] <= 0.0f) bad |= 2;
-            lam = fmaxf(lam, l);
-            lmin = fminf(lmin, sym3_min_eig(c[0], c[1], c[2], c[3], c[4], c[5]));
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-        lam = fmaxf(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-        lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(out + a, enc(mn[a]));
-            atomicMax(out + 3 + a, enc(mx[a]));
-        }
-        atomicMax(out + 6, enc(lam));
-        atomicMin(out + 8, enc(lmin));
-        if (bad) atomicOr(out + 7, bad);
-    }
-}
-
-}  // namespace
-
-gcvo_status bbox_lammax(const float *xyz, const float *cov, int64_t n, float *out_dev, cudaStream_t s) {
-    int *o = reinterpret_cast<int *>(out_dev);
-    bbox_init<<<1, 32, 0, s>>>(o);
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    if (blocks < 1) blocks = 1;
-    bbox_kernel<<<blocks, 256, 0, s>>>(xyz, cov, n, o);
-    count_launches(2);
-    GCVO_CUDA(cudaGetLastError());
-    return GCVO_OK;
-}
-
 }  // namespace gcvo

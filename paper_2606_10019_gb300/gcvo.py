@@ -268,7 +268,7 @@ def _ptr_array(arrs):
 
 
 def gcvo_estimate_covariances_batched(ctx: Context, xyz_list, params: gcvo_kernel_params, cov_list) -> None:
-    """Covariances of several device clouds in one call (concurrent)."""
+    """Covariances of several device clouds in one call (one set of launches)."""
     n = (ctypes.c_int64 * len(xyz_list))(*[_n(x) for x in xyz_list])
     _check(lib().gcvo_estimate_covariances_batched(ctx.handle, len(xyz_list), _ptr_array(xyz_list), n,
                                                    ctypes.byref(params), _ptr_array(cov_list)),
@@ -278,7 +278,7 @@ def gcvo_estimate_covariances_batched(ctx: Context, xyz_list, params: gcvo_kerne
 def gcvo_build_grids_batched(ctx: Context, xyz_list, cov_list, feat_list, params: gcvo_kernel_params,
                              grids=None) -> list:
     """Build (grids[k] None) or rebuild grids for several device clouds in one
-    call (concurrent).  Returns the list of Grid objects."""
+    call (one set of launches).  Returns the list of Grid objects."""
     m = len(xyz_list)
     grids = list(grids) if grids is not None else [None] * m
     h = (ctypes.c_void_p * m)(*[g.handle if g is not None else None for g in grids])
