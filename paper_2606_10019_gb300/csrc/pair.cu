@@ -551,7 +551,9 @@ __device__ void refresh_pose(const FinalizeArgs &a, int prob, ProbDev *P) {
 }
 
 constexpr int FIN_RED_THREADS = 256;   // 8 warps: item g goes to warp g % 8
-constexpr int FIN_STEP_WARPS = 4;      // problems per block of k_fin_step
+// problems per block of k_fin_step: one, so that problems spread over the
+// SMs and their serial FP64 steps do not share one SM's FP64 units
+constexpr int FIN_STEP_WARPS = 1;
 
 // The chunk rows: per chunk, per slot, a compensated FP32 sum of the (hi, lo)
 // partials over each warp's items (8 loads in flight per warp), the warps
