@@ -40,11 +40,16 @@ METRIC = "G-CVO kernel pair-evals/s & registrations/s at equal pose error vs pla
 UNIT = "pair-evals/s"
 FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
 FLOP_PER_PAIR_EXACT = 232   # the G-CVO-E pass: the 76 above plus y, Sigma'y, u, K and the S_yy, S_B sums
-# DRAM bytes per pair-eval of the pair kernel's evaluation pass on this
-# workload, measured by one ncu capture of the kernel whose source hashes to
-# PAIR_KERNEL_SHA; the traffic is reported only while the source still matches
-PAIR_DRAM_BYTES_PER_PAIR = None
-PAIR_KERNEL_SHA = None
+# DRAM bytes per active point (source + target) of one launch of the pair
+# kernel's evaluation pass: 113.38 MB over 1,201,176 points in one ncu
+# capture of the first iteration of the 64-problem batch (4 points per
+# sub-tile in that capture), from the kernel whose source hashes to
+# PAIR_KERNEL_SHA.  The pass reads every point of an active
+# problem once and writes one partial row per sub-tile, so its traffic grows
+# with the active points; the traffic is reported only while the source
+# still matches.
+PAIR_DRAM_BYTES_PER_POINT = 113.383168e6 / 1201176
+PAIR_KERNEL_SHA = "5fe050fc55d7ff0a"
 EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
 
 
@@ -306,7 +311,10 @@ def run_gcvo(args, rank, world):
     import hashlib
     src = os.path.join(ROOT, "paper_2606_10019_gb300", "csrc", "tile.cu")
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == PAIR_KERNEL_SHA
-    traffic = PAIR_DRAM_BYTES_PER_PAIR * pair_evals / n_launch if same_kernel and PAIR_DRAM_BYTES_PER_PAIR else None
+    # points of the active problems, summed over the launches of the timed steps
+    active_points = args.steps * sum(int(n_iter[k]) * (q["sx"].shape[0] + q["tx"].shape[0])
+                                     for k, q in enumerate(batch))
+    traffic = PAIR_DRAM_BYTES_PER_POINT * active_points / n_launch if same_kernel else None
     t_pair = prof["pair_kernel_ms"] / 1e3
     achieved = pair_evals * FLOP_PER_PAIR / t_pair / 1e12 if t_pair > 0 else 0.0
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -314,8 +322,10 @@ def run_gcvo(args, rank, world):
     peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "traffic_basis": "DRAM bytes per pair-eval from an ncu capture of this pass on this workload x mean "
-                                 "pair-evals per launch; null if the kernel source changed since the capture",
+                "traffic_basis": "DRAM bytes per active point (94.4 B, ncu capture of the first iteration of the "
+                                 "64-problem batch) x mean active points per launch; null if the kernel source "
+                                 "changed since the capture",
+                "active_points_per_launch": active_points / n_launch,
                 "kernel": "k_tile (evaluation pass)", "launches": prof["n_pair_launches"],
                 "points_per_subtile": schedule,
                 "avg_launch_ms": prof["pair_kernel_ms"] / n_launch,
