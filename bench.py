@@ -369,7 +369,7 @@ def run_gcvo(args, rank, world):
                        "lidar_points_per_frame_mean": float(np.mean([len(x) for x, _ in frames])),
                        "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, eig clamp "
                                  f"[eig_max/100, eig_max], eig_max 0.01 (corner) / {EIG_MAX} (LiDAR)",
-                       "precision": "FP32 pair kernel, compensated FP32 partials, FP64 reduction/solve/exp",
+                       "precision": "FP32 pair kernel (r from double-float positions for the problems whose FP32 positions would miss 1e-5), compensated FP32 partials, FP64 reduction/solve/exp",
                        "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
                        "parallelism": f"{world} independent replica(s), no collective"},
             "registrations_per_s": regs_all / t_dev,
