@@ -51,6 +51,7 @@
 // of their scale, which is the tolerance itself.  The exact derivative is
 // more sensitive still: its weight-change and Gauss-Newton terms each reach
 // several times its norm and cancel.
+#include <cstddef>
 #include <type_traits>
 
 #include "common.cuh"
@@ -62,7 +63,7 @@ namespace {
 
 static_assert(PAIR_WCAP <= 65535, "target list entries are 16-bit");
 static_assert(PAIR_SLOTS * 33 * 4 <= PAIR_WCAP * 32, "epilogue transpose fits in a warp's staged pos, ca");
-static_assert(PAIR_WARPS * (PAIR_WCAP * 80 + PAIR_WCAP * 2 + 64) <= 227 * 1024, "the largest block stage fits");
+static_assert(PAIR_WARPS * (PAIR_WCAP * 80 + PAIR_WCAP * 4 + 64) <= 227 * 1024, "the largest block stage fits");
 static_assert(PAIR_SLOTS_EXACT * 33 * 4 <= PAIR_WCAP * 48, "exact epilogue transpose fits in pos, ca, cb");
 
 // Per warp: staged target points (with their coordinate tails when LO and
@@ -75,7 +76,8 @@ struct __align__(16) WarpStage {
     float4 cb[PAIR_WCAP];
     float4 lo[LO ? PAIR_WCAP : 1];
     float4 fx[FX ? PAIR_WCAP : 1];   // feature channels 3..6
-    unsigned short list[PAIR_WCAP];
+    unsigned short list[PAIR_WCAP];    // staged targets within rho of the sub-tile box
+    unsigned short listB[PAIR_WCAP];   // those of them within the per-pair bound
     uint64_t bar;
 };
 
@@ -84,6 +86,11 @@ struct __align__(16) WarpStage {
 // this one type.  Every pass stages the target tails (r in double-float).
 template <int MODE, int FD>
 using StageT = WarpStage<true, (FD > 3)>;
+using Stage3 = WarpStage<true, false>;
+using Stage7 = WarpStage<true, true>;
+static_assert(offsetof(Stage3, listB) == offsetof(Stage3, list) + PAIR_WCAP * sizeof(unsigned short) &&
+                  offsetof(Stage7, listB) == offsetof(Stage7, list) + PAIR_WCAP * sizeof(unsigned short),
+              "listB follows list: the evaluation indexes both from list");
 
 // One anisotropic pair (Eq. 7), r = x_i - p_j, into the lane sums t[10].
 template <int FD>
@@ -362,6 +369,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
             plz = L4.z;
         }
         const float rho2 = P->rho2, c2 = P->c2, iso_inv = P->iso_inv;
+        // Two target lists per sub-tile (anisotropic kernel with a cutoff):
+        // every pair within rho is counted (the pair-eval unit), but a pair
+        // can only pass d^2 <= c^2 if |r|^2 <= c^2 lambda_max(Sigma_ij) <=
+        // c^2 (|Sigma'_i|_F + |Sigma_j|_F), so only the targets within that
+        // bound of the sub-tile's box are evaluated.
+        const bool two_lists = !ISO && c2 < INFINITY;
+        float lam_i = 0.f;   // |Sigma'_i|_F, an upper bound of its largest eigenvalue
+        if (two_lists && sval)
+            lam_i = sqrtf(qv[0] * qv[0] + qv[3] * qv[3] + qv[5] * qv[5] +
+                          2.f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[4] * qv[4]));
 
         // G-CVO-1 second pass: a_k = (xi^)^k p, xi the search direction
         float b1[3], b2[3], b3[3], b4[3];
@@ -390,6 +407,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                 bmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
             }
         }
+        const float lam_sub = two_lists ? ord_dec(__reduce_max_sync(FULL, ord_enc(lam_i))) : 0.f;
         const float rho = sqrtf(rho2);
         const float h = G->h, ih = G->inv_h;
         // culling radius: rho plus a margin for the float voxel assignment
@@ -414,6 +432,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
 #pragma unroll
         for (int k = 0; k < NT; ++k) t[k] = 0.f;
         int n_pairs = 0, n_kept = 0, n_cand = 0;
+        int npe = 0;   // pairs within rho counted by the evaluation loop
         const int dy = G->dims[1], dzs = G->dims[2];
 
         for (int cb0 = 0; cb0 < n_cols; cb0 += 32) {
@@ -484,29 +503,67 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                 }
 
                 // ---- 3. the staged targets within rho of the sub-tile box
-                int L = 0;
+                // (list), and those of them within the per-pair bound
+                // c^2 (lam_sub + |Sigma_j|_F) of it (listB; a small margin
+                // covers the rounding of the box test)
+                int L = 0, LB = 0;
                 for (int t0 = 0; t0 < m; t0 += 32) {
                     const int tt = t0 + lane;
-                    bool hit = false;
+                    bool hit = false, near = false;
                     if (tt < m) {
                         const float4 x = S.pos[tt];
                         const float dx = fmaxf(0.f, fmaxf(bmin[0] - x.x, x.x - bmax[0]));
                         const float dyy = fmaxf(0.f, fmaxf(bmin[1] - x.y, x.y - bmax[1]));
                         const float dz = fmaxf(0.f, fmaxf(bmin[2] - x.z, x.z - bmax[2]));
-                        hit = dx * dx + dyy * dyy + dz * dz <= rc2;
+                        const float db2 = dx * dx + dyy * dyy + dz * dz;
+                        hit = db2 <= rc2;
+                        if (two_lists && hit) {
+                            const float4 ca = S.ca[tt], cbv = S.cb[tt];
+                            const float lam_j = sqrtf(ca.x * ca.x + ca.w * ca.w + cbv.y * cbv.y +
+                                                      2.f * (ca.y * ca.y + ca.z * ca.z + cbv.x * cbv.x));
+                            near = db2 <= c2 * (lam_sub + lam_j) * 1.001f + 1e-12f;
+                        }
                     }
                     const unsigned bal = __ballot_sync(FULL, hit);
                     if (hit) S.list[L + __popc(bal & lt_mask)] = (unsigned short)tt;
                     L += __popc(bal);
+                    if (two_lists) {
+                        const unsigned balB = __ballot_sync(FULL, near);
+                        if (near) S.listB[LB + __popc(balB & lt_mask)] = (unsigned short)tt;
+                        LB += __popc(balB);
+                    }
                 }
                 __syncwarp();
                 if (qi == 0 && sval) n_cand += L;
+                // the counting pass pays off when it removes a fifth or more
+                // of the evaluations; otherwise the evaluation counts
+                const bool split = two_lists && LB * 5 < L * 4;
+                // the evaluated list: listB follows list in the stage
+                const int eoff = split ? PAIR_WCAP : 0;
+                const int EL = split ? LB : L;
+                if (split) {
+                    // every pair within rho of the sub-tile, counted with the
+                    // same r as the evaluation forms
+                    for (int j = 0; j < L; j += TQ) {
+                        const int idx = j + qi;
+                        const int k = S.list[min(idx, L - 1)];
+                        const float4 x = S.pos[k];
+                        float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
+                        if (dfr) {
+                            const float4 xl = S.lo[k];
+                            r0 += xl.x - plx;
+                            r1 += xl.y - ply;
+                            r2 += xl.z - plz;
+                        }
+                        n_pairs += (sval && idx < L && r0 * r0 + r1 * r1 + r2 * r2 <= rho2) ? 1 : 0;
+                    }
+                }
 
                 // ---- 4. TQ targets per step, one per group of lanes
-                for (int j = 0; j < L; j += TQ) {
+                for (int j = 0; j < EL; j += TQ) {
                     const int idx = j + qi;
-                    const bool act = sval && idx < L;
-                    const int k = S.list[min(idx, L - 1)];
+                    const bool act = sval && idx < EL;
+                    const int k = S.list[eoff + min(idx, EL - 1)];
                     const float4 x = S.pos[k];
                     float r0 = x.x - px, r1 = x.y - py, r2 = x.z - pz;
                     if (dfr) {
@@ -519,12 +576,12 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                     const float4 xf = FX ? S.fx[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                     if (MODE == PAIR_EVAL && !ISO) {
                         pair_aniso<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], xf, lf, l0, l1, l2, qv, rho2, c2, act, t,
-                                       n_pairs, n_kept);
+                                       npe, n_kept);
                         continue;
                     }
                     if constexpr (MODE == PAIR_EXACT && !ISO) {
                         pair_exact<FD>(r0, r1, r2, x, S.ca[k], S.cb[k], xf, lf, l0, l1, l2, qv, rho2, c2, act, t,
-                                       n_pairs, n_kept);
+                                       npe, n_kept);
                         continue;
                     }
                     const float rr = r0 * r0 + r1 * r1 + r2 * r2;
@@ -539,7 +596,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                         const float d2 = rr * iso_inv;
                         const bool keep = in && d2 <= c2;
                         const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                        n_pairs += in;
+                        npe += in;
                         n_kept += keep;
                         if constexpr (MODE == PAIR_EVAL || MODE == PAIR_EXACT) {
                             t[0] += wgt;
@@ -588,7 +645,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                         const float d2 = qf * rdet;
                         const bool keep = in && d2 <= c2;
                         const float wgt = keep ? cij * ex2_approx(d2 * NEG_HALF_LOG2E) : 0.f;
-                        n_pairs += in;
+                        npe += in;
                         n_kept += keep;
                         // bilinear forms of A = adj / det with r and a_k
                         const float kr1 = (b1[0] * y0 + b1[1] * y1 + b1[2] * y2) * rdet;
@@ -608,6 +665,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                         ls_terms(wgt, kr1, kr2, kr3, kr4, a11, a12, a13, a22, a.ls_literal, t);
                     }
                 }
+                if (!split) n_pairs += npe;
+                npe = 0;
                 __syncwarp();   // the list and staged points are reused by the next chunk
             }
         }

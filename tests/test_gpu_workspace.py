@@ -1,6 +1,7 @@
 """Caller-owned scratch through the C ABI (gcvo_workspace_size /
-gcvo_set_workspace): with a workspace set, covariances, grid rebuilds,
-evaluations and registrations make no device allocation for their scratch,
+gcvo_set_workspace): with a workspace set, covariances, grid rebuilds (one
+at a time and batched), evaluations and registrations make no device
+allocation for their scratch,
 give the same results bit for bit as a context with library-owned scratch,
 and refuse calls beyond the workspace's limits."""
 import numpy as np
@@ -46,6 +47,10 @@ def test_workspace_backed_calls_allocate_nothing(oracle_mod):
             G.gcvo_estimate_covariances(ctx, c[0], kp, c[1])
             G.gcvo_estimate_covariances(ctx, c[3], kp, c[4])
             G.gcvo_rebuild_grid(ctx, g, c[0], c[1], c[2], kp)
+        # the batched forms: both target clouds (3400 points) in one call each
+        G.gcvo_estimate_covariances_batched(ctx, [c[0] for c in clouds], kp, [c[1] for c in clouds])
+        G.gcvo_build_grids_batched(ctx, [c[0] for c in clouds], [c[1] for c in clouds], [c[2] for c in clouds],
+                                   kp, grids)
         ev = [G.gcvo_eval(ctx, g, c[3], c[4], c[5], np.eye(4)) for c, g in zip(clouds, grids)]
         ex = G.gcvo_eval_exact(ctx, grids[0], clouds[0][3], clouds[0][4], clouds[0][5], np.eye(4))
         one = G.gcvo_register(ctx, grids[0], clouds[0][3], clouds[0][4], clouds[0][5], np.eye(4), sp)
@@ -67,6 +72,11 @@ def test_workspace_backed_calls_allocate_nothing(oracle_mod):
     sc = torch.empty((6, sx.shape[1]), device=dev)
     with pytest.raises(G.GcvoError) as e:
         G.gcvo_estimate_covariances(ws_ctx, sx, kp, sc)
+    assert e.value.status == G.GCVO_ERR_WORKSPACE
+    # a batched call whose clouds together exceed the limit
+    with pytest.raises(G.GcvoError) as e:
+        G.gcvo_estimate_covariances_batched(ws_ctx, [clouds[0][0], clouds[1][0], clouds[0][3]], kp,
+                                            [clouds[0][1], clouds[1][1], clouds[0][4]])
     assert e.value.status == G.GCVO_ERR_WORKSPACE
     # library-owned scratch again: the same call runs
     G.gcvo_set_workspace(ws_ctx, None)
