@@ -41,15 +41,15 @@ UNIT = "pair-evals/s"
 FLOP_PER_PAIR = 76          # FP32 flops (FMA = 2) of one pair evaluation
 FLOP_PER_PAIR_EXACT = 232   # the G-CVO-E pass: the 76 above plus y, Sigma'y, u, K and the S_yy, S_B sums
 # DRAM bytes per active point (source + target) of one launch of the pair
-# kernel's evaluation pass: 113.38 MB over 1,201,176 points in one ncu
+# kernel's evaluation pass: 112.75 MB over 1,201,176 points in one ncu
 # capture of the first iteration of the 64-problem batch (4 points per
 # sub-tile in that capture), from the kernel whose source hashes to
 # PAIR_KERNEL_SHA.  The pass reads every point of an active
 # problem once and writes one partial row per sub-tile, so its traffic grows
 # with the active points; the traffic is reported only while the source
 # still matches.
-PAIR_DRAM_BYTES_PER_POINT = 113.383168e6 / 1201176
-PAIR_KERNEL_SHA = "5fe050fc55d7ff0a"
+PAIR_DRAM_BYTES_PER_POINT = 112.750848e6 / 1201176
+PAIR_KERNEL_SHA = "7b263fa72408aff8"
 EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel scans
 
 
@@ -322,7 +322,7 @@ def run_gcvo(args, rank, world):
     peak = sm_count * 128 * 2 * clock_ghz / 1e3      # FP32 TFLOP/s at the maximum SM clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "traffic_basis": "DRAM bytes per active point (94.4 B, ncu capture of the first iteration of the "
+                "traffic_basis": "DRAM bytes per active point (93.9 B, ncu capture of the first iteration of the "
                                  "64-problem batch) x mean active points per launch; null if the kernel source "
                                  "changed since the capture",
                 "active_points_per_launch": active_points / n_launch,
