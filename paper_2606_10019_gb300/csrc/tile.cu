@@ -374,9 +374,9 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
         // can only pass d^2 <= c^2 if |r|^2 <= c^2 lambda_max(Sigma_ij) <=
         // c^2 (|Sigma'_i|_F + |Sigma_j|_F), so only the targets within that
         // bound of the sub-tile's box are evaluated.
-        const bool two_lists = !ISO && c2 < INFINITY;
+        const bool bounded = !ISO && c2 < INFINITY;
         float lam_i = 0.f;   // |Sigma'_i|_F, an upper bound of its largest eigenvalue
-        if (two_lists && sval)
+        if (bounded && sval)
             lam_i = sqrtf(qv[0] * qv[0] + qv[3] * qv[3] + qv[5] * qv[5] +
                           2.f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[4] * qv[4]));
 
@@ -407,12 +407,16 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MODE == PAIR_EVAL ? 5 : 4) k_
                 bmax[k] = ord_dec(__reduce_max_sync(FULL, ord_enc(sval ? pp[k] : -INFINITY)));
             }
         }
-        const float lam_sub = two_lists ? ord_dec(__reduce_max_sync(FULL, ord_enc(lam_i))) : 0.f;
+        const float lam_sub = bounded ? ord_dec(__reduce_max_sync(FULL, ord_enc(lam_i))) : 0.f;
         const float rho = sqrtf(rho2);
         const float h = G->h, ih = G->inv_h;
         // culling radius: rho plus a margin for the float voxel assignment
         const float rc = rho * 1.0001f + 1e-5f * h;
         const float rc2 = rc * rc;
+        // the second list only where it can be much shorter: a sub-tile whose
+        // own covariances are about as large as the largest (sparse LiDAR)
+        // meets targets whose bound is about rho as well
+        const bool two_lists = bounded && 2.f * c2 * lam_sub < 0.64f * rc2;
         int lo[3], hi[3];
         bool empty = !(bmin[0] <= bmax[0]);
 #pragma unroll
