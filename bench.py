@@ -788,7 +788,7 @@ def learned_proposal_block(G, ctx, dev, frames, T_true_frames, n_train=100_000, 
     sp = G.solver_params(k_max=200, eps_tol=1e-6)
     arms = {}
 
-    def judge(name, T, iters, t):
+    def score(name, T, iters, t):
         e = PD.pose_errors(list(T), T_true)
         ok = (e[:, 0] < 2.0) & (e[:, 1] < 0.05)
         arms[name] = {"registrations_per_s": n_eval / t, "success": float(ok.mean()),
@@ -807,11 +807,11 @@ def learned_proposal_block(G, ctx, dev, frames, T_true_frames, n_train=100_000, 
         Ts.append(T1)
         its.append(n1)
     torch.cuda.synchronize(dev)
-    judge("plain_single_from_identity", Ts, its, time.perf_counter() - ts)
+    score("plain_single_from_identity", Ts, its, time.perf_counter() - ts)
     ts = time.perf_counter()
     Tb, _, itb, _ = G.gcvo_register_batched(ctx, probs_id, sp)
     torch.cuda.synchronize(dev)
-    judge("batched_from_identity", Tb, itb, time.perf_counter() - ts)
+    score("batched_from_identity", Tb, itb, time.perf_counter() - ts)
     ts = time.perf_counter()
     _, T0p = net.infer(*batch)
     probs_p = [(g, x, c, f, T0p[k]) for k, (g, x, c, f, _) in enumerate(probs_id)]
@@ -826,12 +826,12 @@ def learned_proposal_block(G, ctx, dev, frames, T_true_frames, n_train=100_000, 
                 Tp[k] = Tf[j]
                 itp[k] += itf[j]
     torch.cuda.synchronize(dev)
-    judge("batched_with_proposal", Tp, itp, time.perf_counter() - ts)
+    score("batched_with_proposal", Tp, itp, time.perf_counter() - ts)
     arms["batched_with_proposal"]["fallbacks"] = len(bad)
     net.close()
     for _, _, _, g in keep:
         g.close()
-    return {"workload": f"config 5: {N} training pairs of {n} points (half corner scenes, half LiDAR frame pairs), "
+    return {"workload": f"learned proposal: {N} training pairs of {n} points (half corner scenes, half LiDAR frame pairs), "
                         f"misaligned up to 30 deg / 0.5 m, labelled by G-CVO-2 from the truth; {n_eval} held-out pairs "
                         "of the same mix",
             "train": {"pairs": N, "steps": steps, "batch": batch_size, "seconds": t_train,

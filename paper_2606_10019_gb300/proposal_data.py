@@ -1,7 +1,7 @@
 """Training and evaluation pairs for the learned initial-pose proposal.
 
-Pairs are drawn from the seeded scene generators (the corner scene of
-config 1 and, optionally, voxelised LiDAR frames of config 2), misaligned by
+Pairs are drawn from the seeded scene generators (the synthetic corner scene
+and, optionally, voxelised frames of the synthetic 64-beam LiDAR trajectory), misaligned by
 a random rigid motion (rotation up to max_deg about a random axis,
 translation up to max_t), and labelled with the pose plain G-CVO-2 converges
 to when started from the true pose (the library does the labelling).
