@@ -19,6 +19,11 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   exp_se3             : scipy.linalg.expm of the 4x4 twist matrix.
   register            : exact recovery in the isotropic and sphere cases.
   linesearch          : polynomial vs direct evaluation of G(t) to O(t^5).
+                        The printed-coefficient variant (literal=True) is
+                        parity unpinned: it is kept only to show the printed
+                        form, and nothing on the CUDA side follows it.
+  f_near / g_near     : one pair placed just inside, just outside and well
+                        inside the cutoff.
   grad_derivative     : central finite differences of g; its fourth term is
                         -M; isotropic D(g) + Gamma is self-adjoint; Newton on
                         it reaches the G-CVO-2 stationary point.

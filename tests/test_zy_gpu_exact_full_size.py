@@ -44,7 +44,7 @@ def test_eval_exact_dense_no_cutoff(env):
 @pytest.mark.slow
 def test_exact_lidar_frame_pair_full_size(env):
     """Full size: one voxelised LiDAR frame pair of the bench's trajectory
-    (about 14k points each, anisotropic, cutoff 3).  f, g, D(g) and H_E of
+    (about 22k points each, anisotropic, cutoff 3).  f, g, D(g) and H_E of
     the exact pass against the oracle's C loops over every pair, at the
     identity and at the true pose."""
     O, G, ctx, dev = env
