@@ -676,3 +676,28 @@ def test_near_cutoff_terms_single_pair(oracle_mod):
         assert np.allclose(r.g, g_terms if kept else 0.0, rtol=1e-12, atol=1e-300)
         assert r.f_near == pytest.approx(fij if near else 0.0, rel=1e-12, abs=1e-300)
         assert np.allclose(r.g_near, np.abs(g_terms) if near else 0.0, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("aniso", [False, True])
+def test_pair_counts_brute_force(oracle_mod, aniso):
+    """The pair-eval unit: n_rho counts the pairs with |r_ij| <= rho (the
+    Euclidean gate before the Mahalanobis test of Eq. 7), for any rho; with
+    the isotropic kernel (Remark 3, d^2 = |r|^2 / ell^2) n_kept counts
+    |r| <= c ell, and the dense objective (cutoff 0) keeps every pair.
+    Counted here by scipy cdist over the source moved by T^-1, so a wrong
+    transform direction, a strict inequality or a dropped rho would show."""
+    O = oracle_mod
+    prob = _small_problem(O, n_t=70, n_s=65, seed=13, aniso=aniso)
+    rng = np.random.default_rng(14)
+    T = D.rigid(_rand_rot(rng, 25), rng.normal(size=3) * 0.1)
+    p = (prob.src - T[:3, 3]) @ T[:3, :3]
+    dist = cdist(prob.tgt, p)
+    for rho in (0.05, 0.2, float(np.quantile(dist, 0.3)), 2.0):
+        mode = dict(kernel_mode=0) if aniso else dict(kernel_mode=1, iso_ell=0.07)
+        r = O.evaluate(prob, T, O.KernelParams(cutoff=3.0, rho=rho, **mode))
+        assert r.n_rho == np.count_nonzero(dist <= rho)
+        if not aniso:
+            assert r.n_kept == np.count_nonzero(dist <= 3.0 * 0.07)
+        dense = O.evaluate(prob, T, O.KernelParams(cutoff=0.0, rho=rho, **mode))
+        assert dense.n_kept == 70 * 65
+        assert dense.n_rho == r.n_rho
