@@ -92,9 +92,9 @@ def parse():
 # ---------------------------------------------------------------------------
 
 def _frame_job(args):
-    config, n_frames, k = args
+    stream, n_frames, k = args
     from paper_2606_10019_gb300 import datagen as D
-    seq = D.LidarSequence(n_frames=n_frames, config=config)
+    seq = D.LidarSequence(n_frames=n_frames, stream=stream)
     return seq.frame(k)
 
 
@@ -104,11 +104,11 @@ def make_frames(n_frames: int, rank: int):
     import multiprocessing as mp
     from paper_2606_10019_gb300 import datagen as D
     from paper_2606_10019_gb300 import replicas as R
-    config = R.rank_config(2, rank)
-    seq = D.LidarSequence(n_frames=n_frames, config=config)
+    stream = R.rank_stream(2, rank)
+    seq = D.LidarSequence(n_frames=n_frames, stream=stream)
     nproc = max(1, min(16, os.cpu_count() or 1))
     with mp.get_context("spawn").Pool(nproc) as pool:
-        frames = pool.map(_frame_job, [(config, n_frames, k) for k in range(n_frames)])
+        frames = pool.map(_frame_job, [(stream, n_frames, k) for k in range(n_frames)])
     T_true = [D.inv_rigid(seq.poses[k + 1]) @ seq.poses[k] for k in range(n_frames - 1)]
     return frames, T_true
 
@@ -183,7 +183,7 @@ class Clocks:
 # ---------------------------------------------------------------------------
 
 def batch_problems(frames, T_true_frames, n_problems=256, n_min=1000, n_max=40000):
-    """The config-4 batch as host arrays: sizes log-uniform in [n_min, n_max];
+    """The uneven headline batch as host arrays: sizes log-uniform in [n_min, n_max];
     even problems are corner scenes of that size (eigenvalue bound 0.01 m^2),
     odd ones LiDAR frame pairs subsampled to it (at most a whole frame,
     bound 0.09 m^2); every initial pose is the truth perturbed by up to 30
@@ -455,7 +455,7 @@ def plain_vs_batched(G, ctx, dev, dpairs, batch, kp, sp):
 
 
 def lidar_tracking_block(G, ctx, dev, frames, T_true, args, steps=3):
-    """LiDAR frame-to-frame tracking (the config-2 workload): covariances of
+    """LiDAR frame-to-frame tracking (100 street frames of about 22k points): covariances of
     every frame, the grid of every target frame and batched G-CVO-2 over the
     consecutive frame pairs from the identity; pair-evals/s, registrations/s,
     phase times and pose errors."""

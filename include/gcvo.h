@@ -105,7 +105,7 @@ typedef struct {
     double xi[6];       /* step xi^(k) */
     double xi_l1;       /* ||xi^(k)||_1 */
     double T[16];       /* T^(k), row-major */
-    int64_t n_pairs;    /* pairs with |r_ij| <= rho examined by the kernel */
+    int64_t n_pairs;    /* pairs with |r_ij| <= rho, counted by the kernel */
     int64_t n_kept;     /* pairs with d^2 <= cutoff^2 */
 } gcvo_iter_log;
 
@@ -113,7 +113,8 @@ typedef struct {
 typedef struct {
     int64_t n_pairs;      /* pairs with |r_ij| <= rho (pair-evals) */
     int64_t n_kept;       /* pairs with d^2 <= cutoff^2 */
-    int64_t n_candidates; /* target points scanned in the voxel neighbourhoods */
+    int64_t n_candidates; /* candidate pairs: each source point times the targets
+                             within rho of its sub-tile's box */
     double rho;           /* Euclidean radius that bounds the cutoff ellipsoids */
 } gcvo_eval_stats;
 
@@ -291,7 +292,8 @@ gcvo_status gcvo_register(gcvo_ctx *ctx, const gcvo_grid *target, const float *s
 
 /* Algorithm 1 for n_problems independent problems in one set of launches:
  * every iteration evaluates all still-active problems in one pair-kernel
- * launch and updates them in one solver launch; a problem that converged
+ * launch and updates them in one reduction and one solver launch; a
+ * problem that converged
  * or failed is masked out.  T_out: n_problems x 16 (host); logs: n_problems
  * x k_max rows (host, may be NULL); n_iter and status: n_problems (host).
  * The call returns GCVO_OK when every problem ran (per-problem outcomes
@@ -323,9 +325,11 @@ typedef struct {
  * stream.  The covariances and grids live in buffers the context keeps
  * and reuses on the next call.  Outputs as gcvo_register_batched: T_out
  * n_pairs x 16 (host), logs n_pairs x k_max rows (host, may be NULL),
- * n_iter and status n_pairs (host, may be NULL).  Covariances and grids
- * of different clouds are computed concurrently on the context's internal
- * streams.  Synchronises the stream. */
+ * n_iter and status n_pairs (host, may be NULL).  The covariances of all
+ * clouds take one batched set of launches and the grids of all targets
+ * another (as gcvo_estimate_covariances_batched and
+ * gcvo_build_grids_batched), on the context's stream.  Synchronises the
+ * stream. */
 gcvo_status gcvo_register_clouds(gcvo_ctx *ctx, int n_pairs, const gcvo_cloud_pair *pairs,
                                  const gcvo_kernel_params *params, const gcvo_solver_params *solver, double *T_out,
                                  gcvo_iter_log *logs, int *n_iter, int *status);
@@ -396,9 +400,11 @@ gcvo_status gcvo_proposal_get_params(gcvo_ctx *ctx, const gcvo_proposal *prop, f
  * state (host or device, 3 x n_params floats) holds the FP32 master
  * parameters, then Adam's first and second moment estimates, in the flat
  * parameter order; step is the number of Adam steps taken (it sets Adam's
- * bias corrections).  set_state also refreshes the BF16 weights.  After
- * set_state(get_state()) further training steps give the same parameters,
- * bit for bit, as if training had not been interrupted.  Both synchronise
+ * bias corrections).  set_state also refreshes the BF16 weights.  The
+ * round trip set_state(get_state()) is exact, and further training steps
+ * then give the parameters of uninterrupted training to float rounding
+ * (the backward sums gradients across blocks with float atomics, so two
+ * runs of the same steps may differ in the last bits).  Both synchronise
  * the stream. */
 gcvo_status gcvo_proposal_get_state(gcvo_ctx *ctx, const gcvo_proposal *prop, float *state_out, int64_t *step_out);
 gcvo_status gcvo_proposal_set_state(gcvo_ctx *ctx, gcvo_proposal *prop, const float *state, int64_t step);

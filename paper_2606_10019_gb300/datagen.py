@@ -10,7 +10,9 @@ cloud, and a pose T acts as T x = R x + t.  The registration objective (Eq. 5)
 is maximised when T^{-1} z_j lands on the target surface, so every generator
 returns ``T_true`` with ``T_true^{-1} z ~ x``.
 
-Seeds: NumPy PCG64, seed = 20260601 + 1000 * config + frame.
+Seeds: NumPy PCG64, seed = 20260601 + 1000 * stream + frame, with one seed
+stream per workload: 1 corner scenes, 2 LiDAR street, 3 RGB-D room, 4 uneven
+batches (rank r of a multi-rank run adds 100 r).
 
 The scenes stand in for the paper's datasets (KITTI LiDAR, ETH3D RGB-D,
 ModelNet40 and a private racing set), none of which is available here; no item
@@ -27,8 +29,8 @@ from scipy.spatial.transform import Rotation
 SEED_BASE = 20260601
 
 
-def rng_for(config: int, frame: int = 0) -> np.random.Generator:
-    return np.random.Generator(np.random.PCG64(SEED_BASE + 1000 * config + frame))
+def rng_for(stream: int, frame: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + 1000 * stream + frame))
 
 
 def rigid(R: np.ndarray, t: np.ndarray) -> np.ndarray:
@@ -74,7 +76,7 @@ class Pair:
 
 
 # ----------------------------------------------------------------------------
-# Config 1: three orthogonal 2 m x 2 m planes forming a corner plus a sphere.
+# Corner scene: three orthogonal 2 m x 2 m planes forming a corner plus a sphere.
 # ----------------------------------------------------------------------------
 
 def sample_corner_scene(rng, n: int, scale: float = 1.0) -> np.ndarray:
@@ -101,10 +103,10 @@ def sample_corner_scene(rng, n: int, scale: float = 1.0) -> np.ndarray:
 
 def make_corner_pair(frame: int = 0, n_src: int = 2000, n_tgt: int = 2000,
                      noise: float = 0.01, angle_deg: float = 5.0, trans: float = 0.2,
-                     config: int = 1, scale: float = 1.0) -> Pair:
-    """Config-1 problem: source = scene sample + noise; target = G (independent
+                     stream: int = 1, scale: float = 1.0) -> Pair:
+    """Corner-scene problem: source = scene sample + noise; target = G (independent
     resample) + fresh noise; T_true = G^{-1}."""
-    rng = rng_for(config, frame)
+    rng = rng_for(stream, frame)
     G = random_motion(rng, angle_deg, trans)
     s_a = sample_corner_scene(rng, n_src, scale)
     s_b = sample_corner_scene(rng, n_tgt, scale)
@@ -137,7 +139,7 @@ def voxel_downsample(xyz: np.ndarray, feat: np.ndarray, voxel: float):
 
 
 # ----------------------------------------------------------------------------
-# Config 2: 64-beam spinning LiDAR in a procedural street.
+# LiDAR street: 64-beam spinning LiDAR in a procedural street.
 # ----------------------------------------------------------------------------
 
 @dataclass
@@ -320,20 +322,20 @@ def lidar_trajectory(rng, n_frames: int) -> list[np.ndarray]:
 
 
 class LidarSequence:
-    """Config 2: a seeded street and a 100-frame trajectory; frames are
+    """A seeded street and a 100-frame trajectory; frames are
     ray-cast and voxel-downsampled (0.3 m) on demand and cached."""
 
-    def __init__(self, n_frames: int = 100, voxel: float = 0.3, config: int = 2):
-        rng = rng_for(config, 0)
+    def __init__(self, n_frames: int = 100, voxel: float = 0.3, stream: int = 2):
+        rng = rng_for(stream, 0)
         self.street = make_street(rng)
         self.poses = lidar_trajectory(rng, n_frames)
         self.voxel = voxel
-        self.config = config
+        self.stream = stream
         self._cache: dict[int, tuple[np.ndarray, np.ndarray]] = {}
 
     def frame(self, k: int):
         if k not in self._cache:
-            rng = rng_for(self.config, 1 + k)
+            rng = rng_for(self.stream, 1 + k)
             pts, inten = lidar_scan(self.street, self.poses[k], rng)
             xyz, f = voxel_downsample(pts, inten, self.voxel)
             self._cache[k] = (xyz.astype(np.float32), f.astype(np.float32))
@@ -348,7 +350,7 @@ class LidarSequence:
 
 
 # ----------------------------------------------------------------------------
-# Config 3: RGB-D frames of a procedural room.
+# RGB-D room: RGB-D frames of a procedural room.
 # ----------------------------------------------------------------------------
 
 @dataclass
@@ -399,14 +401,14 @@ def depth_frame(room: Room, pose: np.ndarray, rng, w: int = 640, h: int = 480,
 
 
 class RgbdSequence:
-    """Config 3: camera inside the room moving <= 5 cm and <= 4 degrees per
+    """Camera inside the room moving <= 5 cm and <= 4 degrees per
     frame; 2 cm voxel downsampling."""
 
-    def __init__(self, n_frames: int = 20, voxel: float = 0.02, config: int = 3):
-        rng = rng_for(config, 0)
+    def __init__(self, n_frames: int = 20, voxel: float = 0.02, stream: int = 3):
+        rng = rng_for(stream, 0)
         self.room = make_room(rng)
         self.voxel = voxel
-        self.config = config
+        self.stream = stream
         yaw = 0.0
         pos = np.array([1.0, 1.2, 1.4])
         R0 = Rotation.from_euler("xyz", [-math.pi / 2 - 0.3, 0.0, -math.pi / 2 + 0.5]).as_matrix()
@@ -422,7 +424,7 @@ class RgbdSequence:
 
     def frame(self, k: int):
         if k not in self._cache:
-            rng = rng_for(self.config, 1 + k)
+            rng = rng_for(self.stream, 1 + k)
             pts, col = depth_frame(self.room, self.poses[k], rng)
             xyz, f = voxel_downsample(pts, col, self.voxel)
             self._cache[k] = (xyz.astype(np.float32), f.astype(np.float32))
@@ -436,7 +438,7 @@ class RgbdSequence:
 
 
 # ----------------------------------------------------------------------------
-# Config 4 / 5: batches of problems of uneven size with large perturbations.
+# Batches of problems of uneven size with large perturbations.
 # ----------------------------------------------------------------------------
 
 def perturb(rng, max_deg: float = 30.0, max_trans: float = 0.5) -> np.ndarray:

@@ -124,7 +124,7 @@ def _lidar_job(args):
 
 def mixed_pairs(frames, T_true_frames, n_pairs: int, seed: int, n: int = 4096, max_deg: float = 30.0,
                 max_t: float = 0.5, pool=None):
-    """The config-5 data: n_pairs pairs of n points, alternately a corner
+    """The proposal training data: n_pairs pairs of n points, alternately a corner
     scene and a consecutive LiDAR frame pair (frames: list of (xyz, l) with
     the true relative poses T_true_frames) subsampled to n points, each
     misaligned by a random motion up to max_deg / max_t.  Returns (pairs,

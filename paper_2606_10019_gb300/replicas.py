@@ -4,9 +4,10 @@ units all ranks processed divided by the slowest rank's time."""
 from __future__ import annotations
 
 
-def rank_config(base_config: int, rank: int) -> int:
-    """Scene/trajectory seed family of a rank: independent problems per rank."""
-    return base_config + 100 * rank
+def rank_stream(base_stream: int, rank: int) -> int:
+    """Seed stream of a rank's scenes and trajectory: independent problems
+    per rank."""
+    return base_stream + 100 * rank
 
 
 def combine(units: float, seconds: float, device=None) -> tuple[float, float]:

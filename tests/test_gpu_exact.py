@@ -203,7 +203,7 @@ def test_register_exact_batched_equals_single(env):
 @pytest.mark.slow
 def test_exact_isotropic_lidar_frame_pair_is_self_adjoint(env):
     """Full size (one voxelised LiDAR frame pair of the bench's trajectory,
-    about 14k points each) with the isotropic kernel, where Lemma 1's g is
+    about 22k points each) with the isotropic kernel, where Lemma 1's g is
     the true gradient: the GPU's H_E = D(g) + Gamma is symmetric at any pose
     (the self-adjointness pinned in the oracle tests), while D(g) alone is
     not (checked at the identity; near the optimum g, and with it D's skew

@@ -44,7 +44,7 @@ def _check_eval(O, G, ctx, case, T, tol=TOL):
 
 @pytest.mark.parametrize("n", [2000, 333, 37])
 def test_eval_corner_anisotropic(env, n):
-    """Config-1 scene; sizes with a ragged last group (333, 37 points)."""
+    """Corner scene; sizes with a ragged last group (333, 37 points)."""
     O, G, ctx, dev = env
     pair = D.make_corner_pair(n_src=n, n_tgt=n)
     case = Case(O, pair, O.KernelParams(cutoff=3.0)).gpu(G, ctx, dev, G.kernel_params(eig_max=0.01))
@@ -251,7 +251,7 @@ def test_covariances_match_oracle(env):
 
 
 def test_register_corner_matches_oracle(env):
-    """Alg. 1 (G-CVO-2) on the config-1 problem from the identity: the oracle
+    """Alg. 1 (G-CVO-2) on the corner-scene problem from the identity: the oracle
     evaluated at each GPU iterate T^(k) matches the logged f and g, and the
     final poses agree within 1e-5 rad / 1e-5 m."""
     O, G, ctx, dev = env
@@ -444,8 +444,8 @@ def test_batched_lidar_launch_configuration_sampled(env):
 
 @pytest.mark.slow
 def test_rgbd_frame_pair_full_size(env):
-    """Config 3: an RGB-D frame pair (2 cm voxels, RGB features, c_ij the dot
-    product) subsampled to the configured ~20k points, evaluated at the
+    """An RGB-D frame pair of the synthetic room (2 cm voxels, RGB features, c_ij the dot
+    product) subsampled to about 20k points, evaluated at the
     identity and at the true pose against the oracle."""
     O, G, ctx, dev = env
     seq = D.RgbdSequence(n_frames=2)
@@ -463,7 +463,7 @@ def test_rgbd_frame_pair_full_size(env):
 
 @pytest.mark.slow
 def test_uneven_batch_sampled(env):
-    """Config 4 style: problems of uneven size (1k to 20k points; corner
+    """Problems of uneven size (1k to 20k points; corner
     scenes and a LiDAR pair) from perturbed starts in one batched call; the
     first two iterations of sampled problems against the oracle at the GPU's
     iterates."""
@@ -495,7 +495,7 @@ def test_uneven_batch_sampled(env):
 
 @pytest.mark.slow
 def test_register_lidar_frame_pair(env):
-    """Config 2 at full size (one voxelised LiDAR frame pair, ~14k points):
+    """A LiDAR street pair at full size (one voxelised frame pair, ~22k points):
     GPU vs oracle at sampled iterates and at the final pose."""
     O, G, ctx, dev = env
     seq = D.LidarSequence(n_frames=2)

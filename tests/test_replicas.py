@@ -12,7 +12,7 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     units, secs = R.combine(100.0 * (rank + 1), 1.5 + rank)
-    out[rank] = (units, secs, R.rank_config(2, rank))
+    out[rank] = (units, secs, R.rank_stream(2, rank))
     dist.barrier()
     dist.destroy_process_group()
 
