@@ -24,7 +24,7 @@ namespace gcvo {
 namespace {
 
 // ---------------------------------------------------------------------------
-// FP64 finalize, one block per problem.
+// FP64 finalize: the device-side math of the per-problem step (k_fin_step).
 // ---------------------------------------------------------------------------
 
 __device__ void hat3d(const double w[3], double W[9]) {

@@ -5,7 +5,8 @@
 //
 // The source points of a problem are sorted by Morton code and cut into
 // sub-tiles: runs of at most SUB points inside one Morton voxel of edge rho
-// (or 2 rho, the coarser cut the autotuner may pick).  Every warp works alone
+// (or rho / 2 or 2 rho, the finer and coarser cuts the autotuner may pick).
+// Every warp works alone
 // on one sub-tile at a time (a work item); it takes up to PAIR_GRAB items per
 // atomic on the global counter (two: a larger grab of heavy items leaves a
 // few warps working long after the rest), and no warp waits for another.
@@ -26,6 +27,15 @@
 //     a time: lane (q, i) pairs target q of the step with point i.  A target
 //     is read by SUB lanes at once (a broadcast), a point stays in
 //     registers, and no lane waits on another's branch.
+//     With a finite cutoff, lambda_max(Sigma_ij) <= |Sigma_i|_F +
+//     |Sigma'_j|_F bounds every pair that can pass d^2 <= c^2 to
+//     |r|^2 <= c^2 (|Sigma_i|_F + |Sigma'_j|_F).  A sub-tile whose own
+//     covariances are well below the problem's largest also lists the
+//     targets within that bound of its box (with its points' largest norm).
+//     When the second list is at most four fifths of the first, the warp
+//     counts the pairs within rho over the first list (the pair-eval unit,
+//     a distance test per pair) and evaluates only the second; otherwise
+//     it evaluates the first list and counts as it goes.
 //  4. Per pair (Eq. 7): Sigma_ij = Sigma_i + Sigma'_j, its adjugate and
 //     determinant, d^2 = r^T Sigma_ij^-1 r, w = c_ij sigma^2 exp(-d^2 / 2)
 //     for d^2 <= c^2 and |r| <= rho, else 0; the lane sums
@@ -42,15 +52,19 @@
 // The G-CVO-E pass (PAIR_EXACT) visits the same pairs and adds the sums of
 // the exact directional derivative of g (pair_exact); its 46 values per
 // sub-tile go to two partial rows.
-// Every pass forms r from double-float positions on both sides:
-// r = (x_hi - p_hi) + (x_lo - p_lo), with the target grid's tails staged
-// beside the points.  Positions are relative to the target box centre, and
-// a LiDAR frame reaches 50-100 m from it, where FP32 rounds a position by
-// 3-6 um.  With the flattest clamped covariances (sigma about 3 cm) that
-// moves each pair's d^2 by about 1e-3 and the gradient sums by about 1e-5
-// of their scale, which is the tolerance itself.  The exact derivative is
-// more sensitive still: its weight-change and Gauss-Newton terms each reach
-// several times its norm and cancel.
+// r from double-float positions: r = (x_hi - p_hi) + (x_lo - p_lo), with
+// the target grid's tails staged beside the points.  Positions are relative
+// to the target box centre, and a LiDAR frame reaches 50-100 m from it,
+// where FP32 rounds a position by 3-6 um.  With the flattest clamped
+// covariances (sigma about 3 cm) that moves each pair's d^2 by about 1e-3
+// and the gradient sums by about 1e-5 of their scale, which is the
+// tolerance itself.  The host marks the problems whose bound
+// 4 c R 2^-24 / sigma_min on that shift exceeds 3e-4 (P->lo); only their
+// work items take the tails in the evaluation and line-search passes, and
+// the others form r = x_hi - p_hi.  The G-CVO-E pass always takes them: the
+// exact derivative is more sensitive still, since its weight-change and
+// Gauss-Newton terms each reach several times its norm and cancel.  Every
+// stage has room for the tails, so one layout serves all passes.
 #include <cstddef>
 #include <type_traits>
 
