@@ -236,8 +236,6 @@ def run_gcvo(args, rank, world):
     dclouds = [tuple(torch.from_numpy(_soa(q[key])).to(dev) for key in ("tx", "tf", "sx", "sf")) for q in batch]
     kps = [kp_c if q["kind"] == "corner" else kp_l for q in batch]
     dpairs = [(*c, q["T0"], kp) for c, q, kp in zip(dclouds, batch, kps)]
-    n_src_total = sum(q["sx"].shape[0] for q in batch)
-    n_tgt_total = sum(q["tx"].shape[0] for q in batch)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(pairs):
@@ -361,17 +359,7 @@ def run_gcvo(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched multi-problem refinement: {n_prob} problems, cloud sizes log-uniform in "
-                                   f"[1000, 40000] points (corner scenes and voxelised LiDAR frame pairs subsampled), "
-                                   "initial poses perturbed up to 30 deg / 0.5 m; covariances, grids and G-CVO-2 "
-                                   "in one gcvo_register_clouds call",
-                       "problems": n_prob, "source_points": n_src_total, "target_points": n_tgt_total,
-                       "lidar_points_per_frame_mean": float(np.mean([len(x) for x, _ in frames])),
-                       "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, eig clamp "
-                                 f"[eig_max/100, eig_max], eig_max 0.01 (corner) / {EIG_MAX} (LiDAR)",
-                       "precision": "FP32 pair kernel (r from double-float positions for the problems whose FP32 positions would miss 1e-5), compensated FP32 partials, FP64 reduction/solve/exp",
-                       "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
-                       "parallelism": f"{world} independent replica(s), no collective"},
+            "config": headline_config(args, batch, frames, world),
             "registrations_per_s": regs_all / t_dev,
             "phase_ms_per_step": {
                 "covariances": prof["clouds_covariance_ms"] / args.steps,
@@ -895,6 +883,23 @@ def cpu_baseline(batch, min_seconds=10.0):
             "seconds": tot_t}
 
 
+def headline_config(args, batch, frames, world):
+    """The headline workload as both arms name it in their JSON line."""
+    return {"workload": f"batched multi-problem refinement: {len(batch)} problems, cloud sizes log-uniform in "
+                        f"[1000, 40000] points (corner scenes and voxelised LiDAR frame pairs subsampled), "
+                        "initial poses perturbed up to 30 deg / 0.5 m; covariances, grids and G-CVO-2 "
+                        "in one gcvo_register_clouds call",
+            "problems": len(batch), "source_points": int(sum(q["sx"].shape[0] for q in batch)),
+            "target_points": int(sum(q["tx"].shape[0] for q in batch)),
+            "lidar_points_per_frame_mean": float(np.mean([len(x) for x, _ in frames])),
+            "solver": f"G-CVO-2, eps_tol {args.eps}, k_max {args.k_max}, cutoff 3, knn {KNN}, eig clamp "
+                      f"[eig_max/100, eig_max], eig_max 0.01 (corner) / {EIG_MAX} (LiDAR)",
+            "precision": "FP32 pair kernel (r from double-float positions for the problems whose FP32 positions "
+                         "would miss 1e-5), compensated FP32 partials, FP64 reduction/solve/exp",
+            "l2": "256 MB flush between timed steps; per-step inputs and grids exceed L2",
+            "parallelism": f"{world} independent replica(s), no collective"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -924,8 +929,7 @@ def run_reference(args, rank, world):
     res = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"batched multi-problem refinement: {len(batch)} problems, cloud sizes log-uniform "
-                                  "in [1000, 40000] points; each step a bounded sample of three problems"},
+           "config": headline_config(args, batch, frames, world),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                             "sample": f"per step: {per_step} problems of the batch with at most 8000 points per "
                                       "cloud, kNN covariances of both clouds and one all-pairs FP64 evaluation each"},
