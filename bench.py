@@ -267,6 +267,8 @@ def run_gcvo(args, rank, world):
         regs += len(T_est)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
     schedule = G.gcvo_pair_schedule(ctx)     # the autotuner's choice for this workload
     clk = clocks.stop()
     prof = G.gcvo_profile_read(ctx)
@@ -296,6 +298,8 @@ def run_gcvo(args, rank, world):
     if not args.no_e2e:
         step(hpairs)                         # staging buffers sized outside the timed loop
         torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for s in range(args.steps):
             flush.zero_()
@@ -303,6 +307,8 @@ def run_gcvo(args, rank, world):
             e2e_pairs += sum(int(lg["n_pairs"].sum()) for lg in logs_e)
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
+        # whole job: pairs of every rank over the slowest rank's time
+        e2e_pairs, t_e2e = R.combine(e2e_pairs, t_e2e, dev)
 
     # ---- roofline of the pair kernel's evaluation pass over the batch
     n_launch = max(1, prof["n_pair_launches"])
