@@ -54,7 +54,7 @@ EIG_MAX = 0.09              # (0.3 m)^2: eigenvalue bound for the 0.3 m voxel sc
 
 
 def _measured_bf16_peak():
-    """The dense bf16 GEMM peak measured on this GPU pool (MEASURED_PEAKS.json,
+    """The dense bf16 GEMM peak measured on GB300s of this kind (MEASURED_PEAKS.json,
     sustained figure: the training loop runs for seconds), else the
     documented fallback of 1.7 PFLOP/s."""
     try:
